@@ -1,0 +1,166 @@
+"""Seeded synthetic workloads: surface profiles, incidences, accelerator parameters and densities.
+
+This module is shared by the CUDA path's tests/bench and by the CPU oracle. It holds no arithmetic
+of the scattering method itself: it only builds profile Fourier coefficients, picks the numerical
+parameters of a run (cell grid, shift h, windows, ...) by the rules stated below, and draws random
+complex densities. Both sides receive the resulting dictionary as input.
+
+Profile convention: f(x) = a[0] + sum_{m>=1} a[m] cos(2 pi m x / d) + b[m] sin(2 pi m x / d).
+
+Parameter rules (readings of the paper where it prints no value):
+  * nodes x_l = l*dx, l = 1..N, dx = d/N (Section 4.2: x_0 = 0, x_N = d);
+  * singular window a = floor(0.75 L / dx) dx (a < L, Remark a_cond), gamma = a/2, large window
+    flat fraction c = 1/2 and A = n_per * d (Section 4.2.2);
+  * shift h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p the finest grid lag in Y: every shifted
+    pole m h (1 <= m <= j) then stays at least dg/(j+1) away from a lag of the equivalent-source
+    grids (Section 3.1 poles P_j); a half-integer offset would put 2h, 4h, ... on the grid;
+  * spectral/spatial switch distance delta_min = d/64 (Section 3.2, estimate of the spectral decay);
+  * eta = 1e-3 for the mode completion M^eta (Section 3.1).
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+DIRICHLET = 0
+NEUMANN = 1
+
+
+def profile_eval_host(prof, x):
+    """f, f', f'' of a Fourier profile at points x (used only to choose the cell box)."""
+    d = prof["d"]
+    a = np.asarray(prof["a"], float)
+    b = np.asarray(prof["b"], float)
+    x = np.asarray(x, float)
+    f = np.full_like(x, a[0])
+    for m in range(1, len(a)):
+        w = 2 * math.pi * m / d
+        f += a[m] * np.cos(w * x) + b[m] * np.sin(w * x)
+    return f
+
+
+def sinusoid(d, amp, phase="cos"):
+    a = np.zeros(2)
+    b = np.zeros(2)
+    if phase == "cos":
+        a[1] = amp
+    else:
+        b[1] = amp
+    return {"d": float(d), "a": a, "b": b}
+
+
+def gaussian_surface(d, rms, corr_len, seed):
+    """Gaussian random periodic surface with correlation exp(-x^2/lc^2).
+
+    Spectrum W(K) = rms^2 lc /(2 sqrt(pi)) exp(-K^2 lc^2/4); complex amplitudes
+    F_m = sqrt(pi W(K_m)/d) (g1 + i g2), F_{-m} = conj(F_m), F_0 = 0, |m| <= ceil(6 d /(pi lc)).
+    Returned as cosine/sine coefficients a_m = 2 Re F_m, b_m = -2 Im F_m.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = int(math.ceil(6 * d / (math.pi * corr_len)))
+    m = np.arange(1, M + 1)
+    K = 2 * math.pi * m / d
+    W = rms**2 * corr_len / (2 * math.sqrt(math.pi)) * np.exp(-(K**2) * corr_len**2 / 4)
+    g = rng.standard_normal((M, 2))
+    F = np.sqrt(math.pi * W / d) * (g[:, 0] + 1j * g[:, 1])
+    a = np.zeros(M + 1)
+    b = np.zeros(M + 1)
+    a[1:] = 2 * F.real
+    b[1:] = -2 * F.imag
+    return {"d": float(d), "a": a, "b": b}
+
+
+def harmonic_surface(d, n_harm, scale, seed):
+    """sum_{m=1..n_harm} c_m cos + s_m sin with c_m, s_m ~ N(0, (scale/m)^2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = np.arange(1, n_harm + 1)
+    g = rng.standard_normal((n_harm, 2))
+    a = np.zeros(n_harm + 1)
+    b = np.zeros(n_harm + 1)
+    a[1:] = g[:, 0] * scale / m
+    b[1:] = g[:, 1] * scale / m
+    return {"d": float(d), "a": a, "b": b}
+
+
+def make_params(prof, k, theta_deg, bc, N, *, j=8, h0=0.5, n_per=40, nx, ny=None, hmin=None,
+                p=8, e=1, n_coll=200, n_fb=12, eta=1e-3, delta_min=None, spec_exp=40.0,
+                c_win=0.5, precision=64):
+    """Assemble the full parameter record of one scattering problem."""
+    d = prof["d"]
+    dx = d / N
+    L = d / nx
+    xs = dx * np.arange(1, N + 1)
+    f = profile_eval_host(prof, xs)
+    fmin, fmax = float(f.min()), float(f.max())
+    if hmin is None:
+        hmin = fmin - 0.5 * L
+    if ny is None:
+        ny = int(math.floor((fmax - hmin) / L)) + 1
+    assert hmin < fmin and hmin + ny * L >= fmax, "cell box does not contain the profile"
+    Ma = int(math.floor(0.75 * L / dx + 1e-9))
+    a_s = Ma * dx
+    dg = L / p
+    h = (round(h0 / dg) + 1.0 / (j + 1)) * dg
+    if delta_min is None:
+        delta_min = d / 64.0
+    theta = math.radians(theta_deg)
+    return {
+        "d": d, "a": np.asarray(prof["a"], float), "b": np.asarray(prof["b"], float),
+        "k": float(k), "theta": theta, "bc": int(bc), "N": int(N),
+        "j": int(j), "h": float(h), "n_per": int(n_per), "c_win": float(c_win),
+        "Ma": Ma, "a_s": float(a_s), "gamma": 0.5 * a_s, "eta": float(eta),
+        "nx": int(nx), "ny": int(ny), "L": float(L), "hmin": float(hmin),
+        "p": int(p), "e": int(e), "n_coll": int(n_coll), "n_fb": int(n_fb),
+        "delta_min": float(delta_min), "spec_exp": float(spec_exp), "precision": int(precision),
+    }
+
+
+# --------------------------------------------------------------------------------------------
+# Named workloads (sizes and shapes of the paper's test problems; all synthetic)
+# --------------------------------------------------------------------------------------------
+
+def wl_sinusoid_dirichlet(N=512, nx=16, **kw):
+    """Perfectly conducting sinusoid y = 0.25 cos(pi x), d = 2, k = 2 pi, theta = 30 deg
+    (double Wood anomaly: alpha_n = pi (1 + n), beta_1 = beta_-3 = 0), 16x16 cells on [-1, 1)."""
+    prof = sinusoid(2.0, 0.25)
+    ny = kw.pop("ny", nx)
+    hmin = kw.pop("hmin", -1.0)
+    return make_params(prof, 2 * math.pi, 30.0, DIRICHLET, N, nx=nx, ny=ny, hmin=hmin, **kw)
+
+
+def wl_deep_corrugation_neumann(N=16384, nx=128, **kw):
+    """Deep sinusoidal corrugation, depth/period = 2, period 10 (wavelength 1), TM (Neumann),
+    theta = 45 deg, 128 cell columns (L = 10/128); one extra cell row so that half-open cells hold
+    both the crest and the trough node."""
+    prof = sinusoid(10.0, 10.0)
+    return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
+
+
+def wl_deep_corrugation_neumann_small(N=1024, nx=32, **kw):
+    """Same shape as the deep corrugation (depth/period = 2) at period 2: the small parity case."""
+    prof = sinusoid(2.0, 2.0)
+    return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
+
+
+def wl_gaussian_wood(N=8192, nx=40, seed=2, **kw):
+    """Gaussian rough surface rms 0.5, correlation length 2, period 40, theta = 85 deg at the
+    Wood wavenumber k = 2 pi 80 /(40 (1 + sin 85 deg)) (alpha_-80 = -k)."""
+    prof = gaussian_surface(40.0, 0.5, 2.0, seed)
+    th = 85.0
+    k = 2 * math.pi * 80 / (40.0 * (1 + math.sin(math.radians(th))))
+    return make_params(prof, k, th, DIRICHLET, N, nx=nx, **kw)
+
+
+def flat(N=64, d=1.0, k=2 * math.pi, theta_deg=20.0, bc=DIRICHLET, nx=8, **kw):
+    prof = {"d": float(d), "a": np.zeros(1), "b": np.zeros(1)}
+    kw.setdefault("hmin", -0.5 * d / nx)
+    kw.setdefault("ny", 1)
+    return make_params(prof, k, theta_deg, bc, N, nx=nx, **kw)
+
+
+def random_density(N, seed, dtype=np.complex128):
+    """Complex normal density vector, normalised to unit 2-norm."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    v /= np.linalg.norm(v)
+    return v.astype(dtype)
