@@ -1,0 +1,133 @@
+/*
+ * sgf.h -- C ABI of the GB300 library for the FFT-accelerated, shifted-Green-function Nystrom
+ * operator of Bruno & Maas, "Shifted equivalent sources and FFT acceleration for periodic
+ * scattering problems, including Wood anomalies" (arXiv:1707.04950).
+ *
+ * Conventions shared by every entry point
+ *  - Profile f(x) = a[0] + sum_{m=1..M} a[m] cos(2 pi m x/d) + b[m] sin(2 pi m x/d), period d.
+ *  - Nystrom nodes x_l = l d/N, l = 1..N (Section 4.2); vectors are length N, index l-1.
+ *  - Complex vectors are interleaved (re, im) pairs of double (complex128) in DEVICE memory unless
+ *    an entry point says "host". The caller owns every buffer it passes; the library never frees
+ *    or retains caller pointers beyond the call.
+ *  - All work is enqueued on the stream given to sgf_create; calls that return results to host
+ *    memory synchronise that stream before returning. Device-output calls do not synchronise.
+ *  - Every call returns sgf_status; SGF_OK is 0. On failure sgf_last_error() holds a message.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SGF_H
+#define SGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgf_ctx sgf_ctx;
+
+typedef enum {
+  SGF_OK = 0,
+  SGF_EINVAL = 1,          /* bad argument or parameter combination                          */
+  SGF_ERESONANT_CELL = 2,  /* -k^2 is (close to) a Dirichlet eigenvalue of the cell (Remark non-resonant) */
+  SGF_EPOLE_ON_GRID = 3,   /* a shifted pole (0, -m h) falls on a lag of an equivalent-source grid */
+  SGF_EWINDOW = 4,         /* window constraints violated: a >= L, or h <= a max|f'| (Remark a_cond) */
+  SGF_ENOCONV = 5,         /* GMRES did not reach the tolerance within maxit                  */
+  SGF_EBREAKDOWN = 6,      /* Krylov breakdown                                                 */
+  SGF_ENONFINITE = 7,      /* a non-finite value was produced                                   */
+  SGF_ETIMEOUT = 8,        /* a bounded device wait gave up                                     */
+  SGF_ECUDA = 9,           /* a CUDA runtime call failed                                        */
+  SGF_ESTATE = 10          /* call order violated (e.g. apply before build)                    */
+} sgf_status;
+
+/* Numerical parameters of one problem (Sections 3-5). Lengths in the units of d and 1/k. */
+typedef struct {
+  int N;            /* Nystrom nodes per period                                                 */
+  int j;            /* number of shifts of the multipolar Green function (eq. shifted_green_function) */
+  double h;         /* shift length h (poles at (0, -m h), 1 <= m <= j)                          */
+  int n_per;        /* smooth truncation A = n_per d of the spatial lattice sum (eq. Gq_limit)      */
+  double c_win;     /* flat fraction c of the window S_{cA,A}                                   */
+  int Ma;           /* singular window a = Ma dx (eq. dsing_def); gamma = a/2                     */
+  double eta;       /* mode-completion threshold (eq. M_eta)                                      */
+  int nx, ny;       /* cells: d = nx L, cell box [hmin, hmin + ny L) (eq. L_constr)               */
+  double hmin;      /* bottom of the reference periodicity domain                                 */
+  int p, e;         /* equivalent sources: spacing L/p, e extra points per side end (eq. eq_mesh)  */
+  int n_coll;       /* collocation points on the boundary of S_q (eq. eq_source_point)           */
+  int n_fb;         /* order of the cell reconstruction basis, 2 n_fb + 1 functions (eq. planewave) */
+  double delta_min; /* spectral series used where min_m |Y + m h| >= delta_min (Section 3.2)     */
+  double spec_exp;  /* spectral series truncated where |e^{i beta_n delta}| < e^{-spec_exp}       */
+  int precision;    /* 64: all stages FP64; 32: projection, FFT and interpolation in FP32 complex  */
+  double ls_reg;    /* Tikhonov weight of the equivalent-source least squares: minimise
+                       |A xi - psi|^2 + (ls_reg |A|_F)^2 |xi|^2 (0 = plain QR solution)           */
+} sgf_params;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL = legacy default). */
+sgf_status sgf_create(sgf_ctx** out, int device, void* cuda_stream);
+void sgf_destroy(sgf_ctx* ctx);
+const char* sgf_last_error(const sgf_ctx* ctx);
+
+/* Surface profile (Section 2): period d, M+1 cosine coefficients a[0..M] and sine coefficients
+ * b[0..M] (b[0] ignored), host arrays copied by the call. */
+sgf_status sgf_set_profile_fourier(sgf_ctx* ctx, double d, int M, const double* a, const double* b);
+
+/* Incidence e^{i(alpha x - beta y)}, alpha = k sin(theta), beta = k cos(theta) (eq. fist_eq);
+ * bc = 0 Dirichlet (TE, double layer), 1 Neumann (TM, single layer). */
+sgf_status sgf_set_wave(sgf_ctx* ctx, double k, double theta_rad, int bc);
+
+/* Numerical parameters (copied). Validated by sgf_build_operator. */
+sgf_status sgf_set_params(sgf_ctx* ctx, const sgf_params* p);
+
+/* Algorithm 2 (initialisation) on the device: geometry and cells, least-squares factors, the
+ * periodised kernel table on the lag grids (hybrid spectral/spatial, Remark large_FFT_eval) and its
+ * spectra, per-cell projection and reconstruction matrices, the block-sparse near-field operator
+ * (exact intersecting part, singular quadrature of eq. local_mat, local equivalent-source
+ * subtraction folded in) and the mode factors of eq. D_M_deltax. Synchronises the stream. */
+sgf_status sgf_build_operator(sgf_ctx* ctx);
+
+/* Algorithm 3: out = (sigma/2 I + D^dx) mu for nrhs right-hand sides stored one after another
+ * (column stride N). sigma = +1 Dirichlet, -1 Neumann. mu_dev/out_dev: device complex128.
+ * transpose_conj must be 0 (the adjoint is not available). Enqueued on the context stream. */
+sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj);
+
+/* Same as sgf_apply with HOST complex128 buffers: copies mu to the device, applies, copies back,
+ * synchronises. */
+sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* out_host, int nrhs);
+
+/* Right-hand side of eq. discrete_eq at the nodes into out_dev (device complex128, length N). */
+sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev);
+
+/* Algorithm 1: GMRES (restart 200, zero initial guess, CGS2 Arnoldi in FP64) on the system with
+ * the right-hand side of sgf_rhs; with precision 32 an FP64 residual-refinement loop wraps inner
+ * GMRES solves on the mixed operator. Writes the solution to mu_dev; *iters = operator
+ * applications, *relres = final ||b - A mu|| / ||b|| with the FP64 operator. Synchronises. */
+sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres);
+
+/* Rayleigh coefficients B_n for n = n_lo..n_hi (eq. rayexp) from the solution mu (device), into
+ * host B[2*(n_hi-n_lo+1)] (interleaved complex); host eff[n_hi-n_lo+1] gets e_n = beta_n/beta |B_n|^2
+ * for propagating n (0 otherwise) and *energy_err = 1 - sum over propagating n in the range
+ * (eq. energy_error). Synchronises. */
+sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
+                        double* energy_err);
+
+/* Introspection: fills host info[0..15] with N, number of occupied cells, near-field entries,
+ * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
+ * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec. */
+sgf_status sgf_info(const sgf_ctx* ctx, double* info);
+
+/* Device time of the stages of the last sgf_apply when profiling is switched on with
+ * sgf_set_profiling(ctx, 1): host times_ms[0..7] = project, forward X-FFT, Y convolution, inverse
+ * X-FFT, interpolation + near field + modes, total. */
+sgf_status sgf_set_profiling(sgf_ctx* ctx, int on);
+sgf_status sgf_stage_times(const sgf_ctx* ctx, double* times_ms);
+
+/* Testing hook: restrict sgf_apply to a subset of its terms. Bit 0 the FFT far field
+ * (interpolated phi^all), bit 1 the block-sparse near operator, bit 2 the mode completion D_M,
+ * bit 3 the sigma/2 identity. Default 15 (all). */
+sgf_status sgf_debug_mask(sgf_ctx* ctx, int mask);
+
+/* Copy of internal tables for testing: which = 0 twisted kernel table of orientation lam
+ * (0 = H, 1 = V) before the Y transform, [P_x][P_y] complex128 with kind 0 monopole, 1 dipole.
+ * Host buffer of P_x*P_y complex128. Synchronises. */
+sgf_status sgf_debug_table(const sgf_ctx* ctx, int lam, int kind, void* host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGF_H */

@@ -8,7 +8,10 @@ Readings (where the paper prints no detail):
     b = 0, 1 (sides extended by e points per end, ~20% more points for p = 8, e = 1); dipole
     normals (0, 1) for H and (1, 0) for V; n_eq = 2 (p + 1 + 2e) sources per orientation;
   * n_coll collocation points equispaced on the boundary of S_q (3L x 3L), offset by half a
-    spacing from its lower-left corner; least squares by Householder QR (eq. eq_source_point);
+    spacing from its lower-left corner; least squares by Householder QR (eq. eq_source_point) with a
+    Tikhonov term ls_reg |A|_F |xi|: the collocation matrix has condition ~1e13 for the layouts
+    used, so the plain solution's near-null components are set by rounding and, carried through the
+    local subtraction, make the operator depend on rounding at the 1e-5 level;
   * punctured Green functions drop only the m = 0 (and, for the periodised kernel, p = 0) self
     term at coincident points, in both Phi~_j^qper and Phi_j, so phi^all - phi^int removes the
     local cells' equivalent sources exactly (eqs. phi_def, phi_jq_def, psi_na_sum);
@@ -35,10 +38,14 @@ from . import green as gr
 from . import direct as dr
 
 
-def _qr_pinv(A):
-    """Least-squares solution operator R^{-1} Q^H of a full-column-rank A (Householder QR)."""
+def _qr_pinv(A, reg=0.0):
+    """Least-squares solution operator of A by Householder QR; with reg > 0 the Tikhonov-regularised
+    problem min |A x - b|^2 + (reg |A|_F)^2 |x|^2, i.e. QR of [A; reg |A|_F I] restricted to b."""
+    m, n = A.shape
+    if reg > 0:
+        A = np.concatenate([A, reg * np.linalg.norm(A) * np.eye(n)], axis=0)
     Q, R = np.linalg.qr(A, mode="reduced")
-    return solve_triangular(R, Q.conj().T)
+    return solve_triangular(R, Q.conj().T)[:, :m]
 
 
 class Accel:
@@ -157,7 +164,7 @@ class Accel:
             gx, gy = gr.gradG0(k, X, Y)
             nu = self.nu[lam]
             A = np.concatenate([gr.G0(k, X, Y), -(nu[0] * gx + nu[1] * gy)], axis=1)
-            self.pinv_eq[lam] = _qr_pinv(A)
+            self.pinv_eq[lam] = _qr_pinv(A, self.par.get("ls_reg", 0.0))
 
     def fb_basis(self, rel, nu=None):
         """Fourier-Bessel functions about the cell centre at points rel (relative to the centre),

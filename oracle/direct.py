@@ -99,15 +99,16 @@ def _kernel_dnu(par, gx, gy, f1_src, f1_tgt, s_src, s_tgt):
     return (-f1_tgt * gx + gy) / s_tgt * s_src
 
 
-def reg_matrix(par):
-    """Dense N x N matrix of D~_reg (eqs. D_ns, G_jq_s)."""
+def reg_matrix(par, rows=None):
+    """Dense matrix of D~_reg (eqs. D_ns, G_jq_s): all N rows, or the target rows given."""
     N, d, k, j, h = par["N"], par["d"], par["k"], par["j"], par["h"]
     dx = d / N
     al, _ = wave(par)
     x, f, f1, f2 = nodes(par)
     s = np.sqrt(1 + f1 * f1)
     a_s, gam = par["a_s"], par["gamma"]
-    I, K = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    I, K = np.meshgrid(rows, np.arange(N), indexing="ij")
     X = (x[I] - x[K]).ravel()
     Y = (f[I] - f[K]).ravel()
     diag = (I == K).ravel()
@@ -131,7 +132,22 @@ def reg_matrix(par):
         gx = gx - ph * sf * ax
         gy = gy - ph * sf * ay
     kreg = _kernel_dnu(par, gx, gy, f1[K].ravel(), f1[I].ravel(), s[K].ravel(), s[I].ravel())
-    return (dx * kreg).reshape(N, N)
+    return (dx * kreg).reshape(len(rows), N)
+
+
+def apply_rows(par, mu, rows):
+    """Rows `rows` of (sigma/2 I + D^dx) mu of the exact system, without assembling the matrix."""
+    rows = np.asarray(rows)
+    y = reg_matrix(par, rows) @ mu
+    r, c, v = sing_triplets(par)
+    pos = {int(t): n for n, t in enumerate(rows)}
+    for rr, cc, vv in zip(r, c, v):
+        if int(rr) in pos:
+            y[pos[int(rr)]] += vv * mu[cc]
+    T, S = modes_factors(par)
+    y += T[rows] @ (S @ mu)
+    sigma = 0.5 if par["bc"] == 0 else -0.5
+    return y + sigma * mu[rows]
 
 
 def sing_triplets(par):

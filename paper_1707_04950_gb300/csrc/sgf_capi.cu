@@ -1,0 +1,858 @@
+// Host side of the sgf library: the C ABI of include/sgf.h, parameter validation, the cell and
+// index bookkeeping of Section 5.1 (binning, occupied cells, local sets L(q), grid indices of the
+// equivalent sources and samples), the orchestration of Algorithm 2 and Algorithm 3, restarted
+// GMRES with CGS2 Arnoldi (Algorithm 1), and Rayleigh extraction.
+#include <complex>
+#include <cmath>
+#include <cstring>
+#include <set>
+#include <cstdlib>
+
+#include "sgf_internal.h"
+
+typedef std::complex<double> cd;
+
+sgf_status set_err(sgf_ctx* ctx, sgf_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+template <typename T>
+static sgf_status dalloc(sgf_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess)
+    return set_err(ctx, SGF_ECUDA, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  ctx->allocs.push_back((void*)*p);
+  return SGF_OK;
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    sgf_status st__ = (x);             \
+    if (st__ != SGF_OK) return st__;   \
+  } while (0)
+
+#define CU(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e__ = (call);                                                                         \
+    if (e__ != cudaSuccess)                                                                           \
+      return set_err(ctx, SGF_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e__)); \
+  } while (0)
+
+static void free_all(sgf_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->o64 = OpData<double>();
+  ctx->o32 = OpData<float>();
+  ctx->built = false;
+}
+
+static int ilog2_exact(long n) {
+  int l = 0;
+  while ((1L << l) < n) ++l;
+  return ((1L << l) == n) ? l : -1;
+}
+static int next_pow2_log(long n) {
+  int l = 0;
+  while ((1L << l) < n) ++l;
+  return l;
+}
+
+extern "C" {
+
+sgf_status sgf_create(sgf_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SGF_EINVAL;
+  *out = nullptr;
+  sgf_ctx* ctx = new sgf_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    set_err(ctx, SGF_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+    *out = ctx;
+    return SGF_ECUDA;
+  }
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&ctx->ev[i]);
+  *out = ctx;
+  return SGF_OK;
+}
+
+void sgf_destroy(sgf_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  for (int i = 0; i < 8; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+}
+
+const char* sgf_last_error(const sgf_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+sgf_status sgf_set_profile_fourier(sgf_ctx* ctx, double d, int M, const double* a, const double* b) {
+  if (!ctx) return SGF_EINVAL;
+  if (!(d > 0) || M < 0 || !a || !b) return set_err(ctx, SGF_EINVAL, "bad profile (d=%g, M=%d)", d, M);
+  ctx->d = d;
+  ctx->fa.assign(a, a + M + 1);
+  ctx->fb.assign(b, b + M + 1);
+  ctx->fb[0] = 0;
+  ctx->have_profile = true;
+  ctx->built = false;
+  return SGF_OK;
+}
+
+sgf_status sgf_set_wave(sgf_ctx* ctx, double k, double theta, int bc) {
+  if (!ctx) return SGF_EINVAL;
+  if (!(k > 0) || !(fabs(theta) < 0.5 * SGF_PI) || (bc != 0 && bc != 1))
+    return set_err(ctx, SGF_EINVAL, "bad wave (k=%g, theta=%g, bc=%d)", k, theta, bc);
+  ctx->k = k;
+  ctx->theta = theta;
+  ctx->alpha = k * sin(theta);
+  ctx->beta = k * cos(theta);
+  ctx->bc = bc;
+  ctx->have_wave = true;
+  ctx->built = false;
+  return SGF_OK;
+}
+
+sgf_status sgf_set_params(sgf_ctx* ctx, const sgf_params* p) {
+  if (!ctx || !p) return SGF_EINVAL;
+  ctx->prm = *p;
+  ctx->have_params = true;
+  ctx->built = false;
+  return SGF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Relative layouts of one cell (lower-left corner at the origin), Section 5.1-5.2 readings:
+// H sources (s dL, b L), V sources (b L, s dL), s = -e..p+e, b = 0,1; collocation points on the
+// boundary of [-L, 2L]^2 at arc lengths (t + 1/2) 12L/n_coll; samples: H bottom, H top (s dL, b L),
+// V left, V right (b L, s dL), s = 0..p.
+static void layouts(sgf_ctx* c, std::vector<double>& src_rel, std::vector<double>& coll_rel,
+                    std::vector<double>& samp_rel, std::vector<int>& src_off) {
+  const int p = c->prm.p, e = c->prm.e, neq = c->neq;
+  const double L = c->L, dL = L / p;
+  src_rel.assign(2 * neq * 2, 0.0);
+  src_off.assign(2 * neq * 2, 0);  // integer (o1, o2) offsets per orientation and source
+  for (int lam = 0; lam < 2; ++lam) {
+    int t = 0;
+    for (int b = 0; b < 2; ++b)
+      for (int s = -e; s <= p + e; ++s, ++t) {
+        double* r = &src_rel[(lam * neq + t) * 2];
+        int* o = &src_off[(lam * neq + t) * 2];
+        if (lam == 0) {
+          r[0] = s * dL; r[1] = b * L; o[0] = s; o[1] = b;
+        } else {
+          r[0] = b * L; r[1] = s * dL; o[0] = b; o[1] = s;
+        }
+      }
+  }
+  const int nc = c->prm.n_coll;
+  coll_rel.assign(2 * nc, 0.0);
+  for (int t = 0; t < nc; ++t) {
+    double tt = (t + 0.5) * 12 * L / nc;
+    int side = std::min((int)floor(tt / (3 * L)), 3);
+    double u = tt - side * 3 * L;
+    double X, Y;
+    if (side == 0) { X = -L + u; Y = -L; }
+    else if (side == 1) { X = 2 * L; Y = -L + u; }
+    else if (side == 2) { X = 2 * L - u; Y = 2 * L; }
+    else { X = -L; Y = 2 * L - u; }
+    coll_rel[2 * t] = X;
+    coll_rel[2 * t + 1] = Y;
+  }
+  samp_rel.assign(2 * c->nfit, 0.0);
+  int t = 0;
+  for (int b = 0; b < 2; ++b)
+    for (int s = 0; s <= p; ++s, ++t) { samp_rel[2 * t] = s * dL; samp_rel[2 * t + 1] = b * L; }
+  for (int b = 0; b < 2; ++b)
+    for (int s = 0; s <= p; ++s, ++t) { samp_rel[2 * t] = b * L; samp_rel[2 * t + 1] = s * dL; }
+}
+
+// Rows c of cells meeting S^r - m h e_2 for some 0 <= m <= j (half-open cells, Section 5.3).
+static std::set<int> rows_of_Sj(int cy_r, int j, double h, double L) {
+  std::set<int> rows;
+  for (int m = 0; m <= j; ++m) {
+    double sh = m * h / L;
+    double lo = cy_r - 2 - sh, hi = cy_r + 2 - sh;
+    for (int cc = (int)floor(lo) + 1; cc < (int)ceil(hi); ++cc)
+      if (lo < cc && cc < hi) rows.insert(cc);
+  }
+  return rows;
+}
+
+static cd Qj_host(cd beta, double h, int j) {
+  if (j == 0) return 1.0 / beta;
+  cd half = 0.5 * h * beta;
+  cd sn = std::sin(half);
+  cd sinc = std::abs(half) < 1e-3 ? 1.0 - half * half / 6.0 + std::pow(half, 4) / 120.0 : std::sin(half) / half;
+  cd acc = 0.5 * h * sinc;
+  for (int m = 1; m < j; ++m) acc *= sn;
+  return std::pow(cd(0, -2), j) * std::exp(cd(0, 1) * (double)j * half) * acc;
+}
+static cd beta_host(double k, double an) {
+  double q = k * k - an * an;
+  return q >= 0 ? cd(std::sqrt(q), 0) : cd(0, std::sqrt(-q));
+}
+// U^eta (eq. M_eta) restricted to |beta_n| <= k.
+static std::vector<int> ueta_set(sgf_ctx* c) {
+  std::vector<int> out;
+  double k = c->k, d = c->d;
+  int nlo = (int)floor((-sqrt(2.0) * k - c->alpha) * d / (2 * SGF_PI)) - 1;
+  int nhi = (int)ceil((sqrt(2.0) * k - c->alpha) * d / (2 * SGF_PI)) + 1;
+  for (int n = nlo; n <= nhi; ++n) {
+    double an = c->alpha + 2 * SGF_PI * n / d;
+    cd bn = beta_host(k, an);
+    if (std::abs(Qj_host(bn, c->prm.h, c->prm.j)) < c->prm.eta && std::abs(bn) <= k) out.push_back(n);
+  }
+  return out;
+}
+
+static sgf_status validate(sgf_ctx* ctx) {
+  if (!ctx->have_profile || !ctx->have_wave || !ctx->have_params)
+    return set_err(ctx, SGF_ESTATE, "profile, wave and params must be set before build");
+  const sgf_params& p = ctx->prm;
+  if (p.N < 8 || p.j < 0 || p.j > 24 || !(p.h > 0) || p.n_per < 1 || p.nx < 3 || p.ny < 1 || p.p < 1 || p.e < 0 ||
+      p.n_coll < 8 || p.n_coll + 4 * (p.p + 1 + 2 * p.e) > 256 || p.n_fb < 0 || !(p.ls_reg >= 0) || p.Ma < 2 || !(p.c_win > 0 && p.c_win < 1) ||
+      !(p.delta_min > 0) || !(p.spec_exp > 0))
+    return set_err(ctx, SGF_EINVAL, "parameter out of range");
+  if (p.precision != 64 && p.precision != 32) return set_err(ctx, SGF_EINVAL, "precision must be 64 or 32");
+  if (p.N % p.nx != 0) return set_err(ctx, SGF_EINVAL, "N must be a multiple of nx");
+  if (ilog2_exact((long)p.nx * p.p) < 0 || ilog2_exact(p.nx) < 0)
+    return set_err(ctx, SGF_EINVAL, "nx and nx*p must be powers of two (cyclic FFT along X)");
+  int nfit = 4 * (p.p + 1), nb = 2 * p.n_fb + 1;
+  if (nb > 63 || nb > 2 * (p.p + 1) + 2 * (p.p - 1)) return set_err(ctx, SGF_EINVAL, "n_fb too large for the samples");
+  if (2 * (p.p + 1 + 2 * p.e) * 2 > p.n_coll) return set_err(ctx, SGF_EINVAL, "n_coll below the number of unknowns");
+  (void)nfit;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
+  if (!ctx) return SGF_EINVAL;
+  TRY(validate(ctx));
+  CU(cudaSetDevice(ctx->device));
+  free_all(ctx);
+  sgf_ctx* c = ctx;
+  const sgf_params& P = c->prm;
+  c->N = P.N;
+  c->dx = c->d / P.N;
+  c->L = c->d / P.nx;
+  c->a_s = P.Ma * c->dx;
+  c->gam = 0.5 * c->a_s;
+  c->neq = 2 * (P.p + 1 + 2 * P.e);
+  c->nfit = 4 * (P.p + 1);
+  c->nb = 2 * P.n_fb + 1;
+  if (!(c->a_s < c->L)) return set_err(ctx, SGF_EWINDOW, "singular window a = %g must be below the cell side %g", c->a_s, c->L);
+  // grids
+  Orient& H = c->og[0];
+  Orient& V = c->og[1];
+  H.Px = P.nx * P.p; H.logPx = ilog2_exact(H.Px); H.nrow = P.ny + 1; H.dxg = c->L / P.p; H.dyg = c->L;
+  V.Px = P.nx; V.logPx = ilog2_exact(V.Px); V.nrow = P.ny * P.p + 1 + 2 * P.e; V.dxg = c->L; V.dyg = c->L / P.p;
+  for (int l = 0; l < 2; ++l) {
+    c->og[l].logPy = next_pow2_log(2L * c->og[l].nrow - 1);
+    c->og[l].Py = 1 << c->og[l].logPy;
+  }
+  c->twlog = std::max(std::max(H.logPx, V.logPx), std::max(H.logPy, V.logPy));
+  if (V.Py > 16384 || H.Px > 8192) return set_err(ctx, SGF_EINVAL, "FFT length above the shared-memory limit");
+  // shifted poles must stay off the finest grid lag (0, -m h)
+  for (int m = 1; m <= P.j; ++m) {
+    double r = m * P.h / V.dyg;
+    if (fabs(r - std::round(r)) < 1e-6)
+      return set_err(ctx, SGF_EPOLE_ON_GRID, "shifted pole %d h lies on a grid lag", m);
+  }
+  {  // non-resonant cell: (kL/pi)^2 != m^2 + n^2, m, n >= 1
+    double t = c->k * c->L / SGF_PI;
+    t *= t;
+    for (int m = 1; m * m < t + 1; ++m)
+      for (int n = 1; m * m + n * n < t + 1; ++n)
+        if (fabs(t - (m * m + n * n)) < 1e-3) return set_err(ctx, SGF_ERESONANT_CELL, "cell side resonant");
+  }
+
+  // ---------------- nodes and profile (device), copied back for the cell bookkeeping
+  int M = (int)c->fa.size() - 1;
+  TRY(dalloc(ctx, &c->d_coef, 2 * (M + 1)));
+  CU(cudaMemcpyAsync(c->d_coef, c->fa.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_coef + M + 1, c->fb.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TRY(dalloc(ctx, &c->d_x, c->N));
+  TRY(dalloc(ctx, &c->d_f, c->N));
+  TRY(dalloc(ctx, &c->d_f1, c->N));
+  TRY(dalloc(ctx, &c->d_f2, c->N));
+  CU(launch_profile(c));
+  c->hx.resize(c->N); c->hf.resize(c->N); c->hf1.resize(c->N); c->hf2.resize(c->N);
+  CU(cudaMemcpyAsync(c->hx.data(), c->d_x, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(c->hf.data(), c->d_f, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(c->hf1.data(), c->d_f1, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  double maxslope = 0;
+  for (int i = 0; i < c->N; ++i) maxslope = std::max(maxslope, fabs(c->hf1[i]));
+  if (!(P.h > c->a_s * maxslope))
+    return set_err(ctx, SGF_EWINDOW, "shift h = %g must exceed a max|f'| = %g", P.h, c->a_s * maxslope);
+
+  // ---------------- binning (Remark cell_def: half-open cells)
+  std::vector<int> ncx(c->N), ncy(c->N);
+  for (int i = 0; i < c->N; ++i) {
+    ncx[i] = (int)(((long)(i + 1) * P.nx + c->N - 1) / c->N) - 1;
+    ncy[i] = (int)ceil((c->hf[i] - P.hmin) / c->L) - 1;
+    if (ncy[i] < 0 || ncy[i] >= P.ny) return set_err(ctx, SGF_EINVAL, "node %d outside the cell box", i);
+  }
+  std::vector<int> occ_id((size_t)P.nx * P.ny, -1);
+  std::vector<std::vector<int>> members;
+  c->occ_cx.clear(); c->occ_cy.clear();
+  // occupied cells ordered by (cy, cx)
+  {
+    std::vector<char> used((size_t)P.nx * P.ny, 0);
+    for (int i = 0; i < c->N; ++i) used[(size_t)ncy[i] * P.nx + ncx[i]] = 1;
+    for (int cy = 0; cy < P.ny; ++cy)
+      for (int cx = 0; cx < P.nx; ++cx)
+        if (used[(size_t)cy * P.nx + cx]) {
+          occ_id[(size_t)cy * P.nx + cx] = (int)c->occ_cx.size();
+          c->occ_cx.push_back(cx);
+          c->occ_cy.push_back(cy);
+        }
+  }
+  c->n_occ = (int)c->occ_cx.size();
+  members.assign(c->n_occ, {});
+  for (int i = 0; i < c->N; ++i) members[occ_id[(size_t)ncy[i] * P.nx + ncx[i]]].push_back(i);
+  c->cell_start.assign(c->n_occ + 1, 0);
+  c->node_idx.clear();
+  std::vector<int> node_cell;
+  int maxnq = 0;
+  for (int q = 0; q < c->n_occ; ++q) {
+    c->cell_start[q] = (int)c->node_idx.size();
+    for (int i : members[q]) { c->node_idx.push_back(i); node_cell.push_back(q); }
+    maxnq = std::max(maxnq, (int)members[q].size());
+  }
+  c->cell_start[c->n_occ] = c->N;
+  if ((size_t)c->nfit * maxnq * sizeof(zd) > 200 * 1024)
+    return set_err(ctx, SGF_EINVAL, "too many nodes (%d) in one cell for the near-field kernel", maxnq);
+  TRY(dalloc(ctx, &c->d_cell_start, c->n_occ + 1));
+  TRY(dalloc(ctx, &c->d_node_idx, c->N));
+  TRY(dalloc(ctx, &c->d_node_cell, c->N));
+  TRY(dalloc(ctx, &c->d_occ_cx, c->n_occ));
+  TRY(dalloc(ctx, &c->d_occ_cy, c->n_occ));
+  CU(cudaMemcpy(c->d_cell_start, c->cell_start.data(), (c->n_occ + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_node_idx, c->node_idx.data(), c->N * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_node_cell, node_cell.data(), c->N * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_occ_cx, c->occ_cx.data(), c->n_occ * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_occ_cy, c->occ_cy.data(), c->n_occ * sizeof(int), cudaMemcpyHostToDevice));
+
+  // ---------------- layouts, grid indices and twists
+  std::vector<double> src_rel, coll_rel, samp_rel;
+  std::vector<int> src_off;
+  layouts(c, src_rel, coll_rel, samp_rel, src_off);
+  const int neq = c->neq, nfit = c->nfit;
+  std::vector<int> src_gidx((size_t)c->n_occ * 2 * neq), samp_gidx((size_t)c->n_occ * nfit);
+  std::vector<zd> src_tw((size_t)c->n_occ * 2 * neq);
+  for (int q = 0; q < c->n_occ; ++q) {
+    int cx = c->occ_cx[q], cy = c->occ_cy[q];
+    for (int lam = 0; lam < 2; ++lam) {
+      const Orient& o = c->og[lam];
+      for (int s = 0; s < neq; ++s) {
+        int o1 = src_off[(lam * neq + s) * 2], o2 = src_off[(lam * neq + s) * 2 + 1];
+        long ixr, iy;
+        if (lam == 0) { ixr = (long)cx * P.p + o1; iy = cy + o2; }
+        else { ixr = cx + o1; iy = (long)cy * P.p + o2 + P.e; }
+        long ixref = ((ixr % o.Px) + o.Px) % o.Px;
+        src_gidx[((size_t)q * 2 + lam) * neq + s] = (int)(ixref * o.nrow + iy);
+        double xs = ixr * o.dxg;
+        src_tw[((size_t)q * 2 + lam) * neq + s] = zd(cos(-c->alpha * xs), sin(-c->alpha * xs));
+      }
+    }
+    for (int t = 0; t < nfit; ++t) {
+      int lam = t < 2 * (P.p + 1) ? 0 : 1;
+      const Orient& o = c->og[lam];
+      int tt = lam == 0 ? t : t - 2 * (P.p + 1);
+      int b = tt / (P.p + 1), s = tt % (P.p + 1);
+      long ixr, iy;
+      if (lam == 0) { ixr = (long)cx * P.p + s; iy = cy + b; }
+      else { ixr = cx + b; iy = (long)cy * P.p + s + P.e; }
+      long ixref = ((ixr % o.Px) + o.Px) % o.Px;
+      samp_gidx[(size_t)q * nfit + t] = (int)(ixref * o.nrow + iy);
+    }
+  }
+  TRY(dalloc(ctx, &c->d_src_gidx, src_gidx.size()));
+  TRY(dalloc(ctx, &c->d_samp_gidx, samp_gidx.size()));
+  TRY(dalloc(ctx, &c->o64.src_tw, src_tw.size()));
+  CU(cudaMemcpy(c->d_src_gidx, src_gidx.data(), src_gidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->d_samp_gidx, samp_gidx.data(), samp_gidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(c->o64.src_tw, src_tw.data(), src_tw.size() * sizeof(zd), cudaMemcpyHostToDevice));
+  double *d_src_rel, *d_coll_rel, *d_samp_rel, *d_kress;
+  TRY(dalloc(ctx, &d_src_rel, src_rel.size()));
+  TRY(dalloc(ctx, &d_coll_rel, coll_rel.size()));
+  TRY(dalloc(ctx, &d_samp_rel, samp_rel.size()));
+  CU(cudaMemcpy(d_src_rel, src_rel.data(), src_rel.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(d_coll_rel, coll_rel.data(), coll_rel.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(d_samp_rel, samp_rel.data(), samp_rel.size() * sizeof(double), cudaMemcpyHostToDevice));
+  // binomial weights and log-quadrature weights R_s, s = -(Ma-1)..(Ma-1)
+  std::vector<double> binw(P.j + 1);
+  for (int m = 0; m <= P.j; ++m) {
+    double cb = 1;
+    for (int i = 0; i < m; ++i) cb = cb * (P.j - i) / (i + 1);
+    binw[m] = (m % 2 ? -1.0 : 1.0) * cb;
+  }
+  TRY(dalloc(ctx, &c->d_binw, binw.size()));
+  CU(cudaMemcpy(c->d_binw, binw.data(), binw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<double> kress(2 * P.Ma - 1);
+  for (int s = -(P.Ma - 1); s <= P.Ma - 1; ++s) {
+    double acc = 0;
+    for (int m = 1; m < P.Ma; ++m) acc += cos(SGF_PI * m * s / P.Ma) / m;
+    kress[s + P.Ma - 1] = -2 * c->dx * acc - c->dx / P.Ma * ((s & 1) ? -1.0 : 1.0);
+  }
+  TRY(dalloc(ctx, &d_kress, kress.size()));
+  CU(cudaMemcpy(d_kress, kress.data(), kress.size() * sizeof(double), cudaMemcpyHostToDevice));
+
+  // ---------------- least-squares operators (Algorithm 2, first step)
+  const int nc = P.n_coll;
+  zd *d_Acoll, *d_Bfb, *d_pinv_eq, *d_pinv_fb, *d_qrs;
+  const long lda = nc + 2 * neq;
+  TRY(dalloc(ctx, &d_Acoll, (size_t)2 * lda * 2 * neq));
+  TRY(dalloc(ctx, &d_Bfb, (size_t)nfit * c->nb));
+  TRY(dalloc(ctx, &d_pinv_eq, (size_t)2 * 2 * neq * nc));
+  TRY(dalloc(ctx, &d_pinv_fb, (size_t)c->nb * nfit));
+  TRY(dalloc(ctx, &d_qrs, (size_t)(2 * neq) * (2 * neq) + 2 * neq + (size_t)lda * lda + 64));
+  CU(launch_build_matrices(c, d_Acoll, d_Bfb, d_coll_rel, d_src_rel, d_samp_rel));
+  for (int lam = 0; lam < 2; ++lam)
+    CU(launch_qr_pinv(c, d_Acoll + (size_t)lam * lda * 2 * neq, nc, 2 * neq, true, P.ls_reg,
+                      d_pinv_eq + (size_t)lam * 2 * neq * nc, d_qrs));
+  CU(launch_qr_pinv(c, d_Bfb, nfit, c->nb, false, 0.0, d_pinv_fb, d_qrs));
+
+  // ---------------- projection and reconstruction matrices
+  TRY(dalloc(ctx, &c->o64.P, (size_t)4 * neq * c->N));
+  CU(launch_build_P(c, d_pinv_eq, d_coll_rel));
+  zd* d_Iplain;
+  TRY(dalloc(ctx, &d_Iplain, (size_t)nfit * c->N));
+  TRY(dalloc(ctx, &c->o64.Ip, (size_t)nfit * c->N));
+  CU(launch_build_I(c, d_pinv_fb, d_Iplain, d_samp_rel));
+
+  // ---------------- kernel tables and spectra
+  TRY(dalloc(ctx, &c->o64.tw, (size_t)1 << (c->twlog - 1)));
+  bool mixed = P.precision == 32;
+  if (mixed) TRY(dalloc(ctx, &c->o32.tw, (size_t)1 << (c->twlog - 1)));
+  CU(launch_twiddles(c));
+  for (int lam = 0; lam < 2; ++lam) {
+    long n = (long)c->og[lam].Px * c->og[lam].Py;
+    for (int kd = 0; kd < 2; ++kd) {
+      TRY(dalloc(ctx, &c->o64.Khat[lam][kd], n));
+      TRY(dalloc(ctx, &c->d_Tx[lam][kd], n));
+      if (mixed) TRY(dalloc(ctx, &c->o32.Khat[lam][kd], n));
+    }
+  }
+  TRY(dalloc(ctx, &c->d_msum, 64));
+  CU(launch_tables(c));
+
+  // ---------------- local sets L(q) and the near-field block list
+  std::vector<int> pq, pr, pw, pdcx;
+  std::vector<long> poff;
+  std::vector<int> blk_start(c->n_occ + 1, 0);
+  std::vector<std::set<int>> rowsS(P.ny);
+  for (int cy = 0; cy < P.ny; ++cy) rowsS[cy] = rows_of_Sj(cy, P.j, P.h, c->L);
+  long off = 0;
+  int dcy_min = 1 << 30, dcy_max = -(1 << 30);
+  for (int q = 0; q < c->n_occ; ++q) {
+    blk_start[q] = (int)pq.size();
+    int cxq = c->occ_cx[q], cyq = c->occ_cy[q];
+    int nq = c->cell_start[q + 1] - c->cell_start[q];
+    for (int dcx = -1; dcx <= 1; ++dcx) {
+      int cxr = cxq + dcx;
+      int ref = ((cxr % P.nx) + P.nx) % P.nx;
+      int wrap = (cxr - ref) / P.nx;
+      for (int cyr = 0; cyr < P.ny; ++cyr) {
+        int r = occ_id[(size_t)cyr * P.nx + ref];
+        if (r < 0) continue;
+        if (!rowsS[cyr].count(cyq)) continue;
+        int nr = c->cell_start[r + 1] - c->cell_start[r];
+        pq.push_back(q); pr.push_back(r); pw.push_back(wrap); pdcx.push_back(dcx); poff.push_back(off);
+        off += (long)nq * nr;
+        dcy_min = std::min(dcy_min, cyr - cyq);
+        dcy_max = std::max(dcy_max, cyr - cyq);
+      }
+    }
+  }
+  blk_start[c->n_occ] = (int)pq.size();
+  c->n_blk = (int)pq.size();
+  c->nnz = off;
+  int n_dcy = dcy_max - dcy_min + 1;
+  NearPairs pp;
+  pp.n = c->n_blk;
+  TRY(dalloc(ctx, &pp.q, pp.n));
+  TRY(dalloc(ctx, &pp.r, pp.n));
+  TRY(dalloc(ctx, &pp.wrap, pp.n));
+  TRY(dalloc(ctx, &pp.dcx, pp.n));
+  TRY(dalloc(ctx, &pp.off, pp.n));
+  CU(cudaMemcpy(pp.q, pq.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(pp.r, pr.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(pp.wrap, pw.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(pp.dcx, pdcx.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(pp.off, poff.data(), pp.n * sizeof(long), cudaMemcpyHostToDevice));
+  TRY(dalloc(ctx, &c->d_blk_start, c->n_occ + 1));
+  CU(cudaMemcpy(c->d_blk_start, blk_start.data(), (c->n_occ + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  c->d_blk_r = pp.r;
+  c->d_blk_off = pp.off;
+  TRY(dalloc(ctx, &c->d_C, c->nnz));
+  zd* d_phi;
+  TRY(dalloc(ctx, &d_phi, (size_t)3 * n_dcy * nfit * 2 * neq));
+  CU(launch_phi_off(c, d_phi, dcy_min, n_dcy, d_samp_rel, d_src_rel));
+  CU(launch_near(c, d_phi, dcy_min, n_dcy, d_Iplain, pp, d_kress));
+
+  // ---------------- modes
+  std::vector<int> ue = ueta_set(c);
+  c->nm = (int)ue.size();
+  std::vector<double> mn(3 * std::max(1, c->nm));
+  for (int t = 0; t < c->nm; ++t) {
+    double an = c->alpha + 2 * SGF_PI * ue[t] / c->d;
+    cd bn = beta_host(c->k, an);
+    mn[3 * t] = an; mn[3 * t + 1] = bn.real(); mn[3 * t + 2] = bn.imag();
+  }
+  double* d_mn;
+  TRY(dalloc(ctx, &d_mn, mn.size()));
+  CU(cudaMemcpy(d_mn, mn.data(), mn.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY(dalloc(ctx, &c->d_MT, (size_t)c->N * std::max(1, c->nm)));
+  TRY(dalloc(ctx, &c->d_MS, (size_t)c->N * std::max(1, c->nm)));
+  CU(launch_modes(c, d_mn));
+
+  // ---------------- grids and FP32 copies
+  for (int lam = 0; lam < 2; ++lam) {
+    long sz = 2L * c->og[lam].Px * c->og[lam].nrow;
+    TRY(dalloc(ctx, &c->o64.grid[lam], sz));
+    if (mixed) TRY(dalloc(ctx, &c->o32.grid[lam], sz));
+  }
+  if (mixed) {
+    TRY(dalloc(ctx, &c->o32.P, (size_t)4 * neq * c->N));
+    TRY(dalloc(ctx, &c->o32.Ip, (size_t)nfit * c->N));
+    TRY(dalloc(ctx, &c->o32.src_tw, src_tw.size()));
+    CU(launch_to_f32(c->o64.P, c->o32.P, (long)4 * neq * c->N, c->stream));
+    CU(launch_to_f32(c->o64.Ip, c->o32.Ip, (long)nfit * c->N, c->stream));
+    CU(launch_to_f32(c->o64.src_tw, c->o32.src_tw, (long)src_tw.size(), c->stream));
+  }
+  TRY(dalloc(ctx, &c->d_mu_tmp, (size_t)c->N * 2));
+  TRY(dalloc(ctx, &c->d_out_tmp, (size_t)c->N * 2));
+  CU(cudaStreamSynchronize(c->stream));
+  CU(cudaGetLastError());
+
+  // algorithmic bytes of one matvec (compulsory traffic; s bytes per complex of the far field)
+  for (int prec = 0; prec < 2; ++prec) {
+    double s = prec == 0 ? 16.0 : 8.0;
+    double b = s * (4.0 * neq * c->N + (double)nfit * c->N) + 16.0 * c->nnz + 32.0 * c->N;
+    for (int lam = 0; lam < 2; ++lam) {
+      double Pk = (double)c->og[lam].Px * c->og[lam].Py, Mg = (double)c->og[lam].Px * c->og[lam].nrow;
+      b += s * (2 * Pk + 2 * Mg + Mg);
+    }
+    if (prec == 0) c->bytes64 = b; else c->bytes32 = b;
+  }
+  c->launches_per_apply = 9;
+  c->built = true;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (transpose_conj) return set_err(ctx, SGF_EINVAL, "adjoint application is not available");
+  if (nrhs < 1 || !mu_dev || !out_dev) return set_err(ctx, SGF_EINVAL, "bad apply arguments");
+  for (int r = 0; r < nrhs; ++r) {
+    const zd* mu = (const zd*)mu_dev + (size_t)r * ctx->N;
+    zd* out = (zd*)out_dev + (size_t)r * ctx->N;
+    cudaError_t e = ctx->prm.precision == 64 ? launch_apply64(ctx, mu, out) : launch_apply32(ctx, mu, out);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "apply: %s", cudaGetErrorString(e));
+  }
+  if (ctx->profiling) {
+    cudaEventSynchronize(ctx->ev[5]);
+    float ms;
+    for (int i = 0; i < 5; ++i) {
+      cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
+      ctx->stage_ms[i] = ms;
+    }
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+    ctx->stage_ms[5] = ms;
+  }
+  return SGF_OK;
+}
+
+static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec) {
+  cudaError_t e = prec == 64 ? launch_apply64(ctx, mu, out) : launch_apply32(ctx, mu, out);
+  if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "apply: %s", cudaGetErrorString(e));
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* out_host, int nrhs) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  size_t nb = (size_t)ctx->N * sizeof(zd);
+  for (int r = 0; r < nrhs; ++r) {
+    CU(cudaMemcpyAsync(ctx->d_mu_tmp, (const char*)mu_host + r * nb, nb, cudaMemcpyHostToDevice, ctx->stream));
+    TRY(apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision));
+    CU(cudaMemcpyAsync((char*)out_host + r * nb, ctx->d_out_tmp, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  CU(launch_rhs(ctx, (zd*)out_dev));
+  return SGF_OK;
+}
+
+// ------------------------------------------------------------------ GMRES (restarted, CGS2)
+struct Krylov {
+  zd *V = nullptr, *w = nullptr, *h = nullptr, *partial = nullptr, *r = nullptr, *tmp = nullptr;
+  int m = 0, nblk = 32;
+};
+
+static sgf_status dot_host(sgf_ctx* ctx, Krylov& K, const zd* V, int m, const zd* w, std::vector<cd>& out) {
+  CU(launch_dots(V, m, ctx->N, w, ctx->N, K.partial, K.nblk, K.h, ctx->stream));
+  out.resize(m);
+  CU(cudaMemcpyAsync(out.data(), K.h, m * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return SGF_OK;
+}
+
+// Solves A x = b from x = 0 with operator precision prec; returns applications in *its.
+static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, double tol, int maxit, int* its,
+                        double* relres) {
+  const long N = ctx->N;
+  const int m = K.m;
+  std::vector<cd> tmp;
+  TRY(dot_host(ctx, K, b, 1, b, tmp));
+  double bn = std::sqrt(tmp[0].real());
+  CU(cudaMemsetAsync(x, 0, N * sizeof(zd), ctx->stream));
+  if (bn == 0) { *relres = 0; return SGF_OK; }
+  int total = 0;
+  double res = bn;
+  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  while (total < maxit) {
+    // r = b - A x
+    TRY(apply_prec(ctx, x, K.r, prec));
+    CU(launch_axpby(K.r, zd(1, 0), b, zd(-1, 0), N, ctx->stream));
+    TRY(dot_host(ctx, K, K.r, 1, K.r, tmp));
+    double beta = std::sqrt(tmp[0].real());
+    res = beta;
+    if (beta / bn <= tol) break;
+    CU(cudaMemcpyAsync(K.V, K.r, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(launch_axpby(K.V, zd(0, 0), K.V, zd(1.0 / beta, 0), N, ctx->stream));
+    std::fill(g.begin(), g.end(), cd(0));
+    g[0] = beta;
+    int jdone = 0;
+    for (int jj = 0; jj < m && total < maxit; ++jj) {
+      zd* vj = K.V + (size_t)jj * N;
+      zd* w = K.V + (size_t)(jj + 1) * N;
+      TRY(apply_prec(ctx, vj, w, prec));
+      ++total;
+      std::vector<cd> h1, h2;
+      TRY(dot_host(ctx, K, K.V, jj + 1, w, h1));
+      CU(cudaMemcpyAsync(K.h, h1.data(), (jj + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+      CU(launch_update(w, K.V, jj + 1, N, K.h, N, ctx->stream));
+      TRY(dot_host(ctx, K, K.V, jj + 1, w, h2));
+      CU(cudaMemcpyAsync(K.h, h2.data(), (jj + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+      CU(launch_update(w, K.V, jj + 1, N, K.h, N, ctx->stream));
+      for (int i = 0; i <= jj; ++i) H[(size_t)i * m + jj] = h1[i] + h2[i];
+      TRY(dot_host(ctx, K, w, 1, w, tmp));
+      double hn = std::sqrt(tmp[0].real());
+      H[(size_t)(jj + 1) * m + jj] = hn;
+      if (!(hn > 0) || !std::isfinite(hn)) {
+        if (!std::isfinite(hn)) return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
+      } else {
+        CU(launch_axpby(w, zd(0, 0), w, zd(1.0 / hn, 0), N, ctx->stream));
+      }
+      for (int i = 0; i < jj; ++i) {
+        cd a = H[(size_t)i * m + jj], bb = H[(size_t)(i + 1) * m + jj];
+        H[(size_t)i * m + jj] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
+        H[(size_t)(i + 1) * m + jj] = -sn[i] * a + cs[i] * bb;
+      }
+      cd a = H[(size_t)jj * m + jj], bb = H[(size_t)(jj + 1) * m + jj];
+      double den = std::sqrt(std::norm(a) + std::norm(bb));
+      cs[jj] = den > 0 ? a / den : cd(1);
+      sn[jj] = den > 0 ? bb / den : cd(0);
+      H[(size_t)jj * m + jj] = den;
+      H[(size_t)(jj + 1) * m + jj] = 0;
+      g[jj + 1] = -sn[jj] * g[jj];
+      g[jj] = std::conj(cs[jj]) * g[jj];
+      jdone = jj + 1;
+      res = std::abs(g[jj + 1]);
+      if (getenv("SGF_VERBOSE"))
+        fprintf(stderr, "gmres prec %d it %d j %d hn %.3e h00 %.3e res %.3e\n", prec, total, jj, hn,
+                std::abs(H[0]), res / bn);
+      if (res / bn <= tol || !(hn > 0)) break;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      cd s = g[i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) s -= H[(size_t)i * m + k2] * y[k2];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    std::vector<cd> ny(jdone);
+    for (int i = 0; i < jdone; ++i) ny[i] = -y[i];
+    CU(cudaMemcpyAsync(K.h, ny.data(), jdone * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_update(x, K.V, jdone, N, K.h, N, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (res / bn <= tol) break;
+  }
+  // true residual
+  TRY(apply_prec(ctx, x, K.r, prec));
+  CU(launch_axpby(K.r, zd(1, 0), b, zd(-1, 0), N, ctx->stream));
+  TRY(dot_host(ctx, K, K.r, 1, K.r, tmp));
+  *relres = std::sqrt(tmp[0].real()) / bn;
+  *its = total;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!(tol > 0) || maxit < 1 || !mu_dev) return set_err(ctx, SGF_EINVAL, "bad solve arguments");
+  const long N = ctx->N;
+  Krylov K;
+  K.m = std::min(200, maxit);
+  std::vector<void*> mine;
+  auto al = [&](zd** p, size_t n) -> sgf_status {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(zd));
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    mine.push_back(*p);
+    return SGF_OK;
+  };
+  sgf_status st = SGF_OK;
+  zd *b, *x, *dlt;
+  if ((st = al(&K.V, (size_t)(K.m + 1) * N)) || (st = al(&K.h, 256)) || (st = al(&K.partial, 256 * 32)) ||
+      (st = al(&K.r, N)) || (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
+    for (void* p : mine) cudaFree(p);
+    return st;
+  }
+  int its = 0;
+  double rr = 1;
+  launch_rhs(ctx, b);
+  if (ctx->prm.precision == 64) {
+    st = gmres(ctx, K, 64, b, x, tol, maxit, &its, &rr);
+  } else {
+    // FP64 residual refinement around inner mixed-precision GMRES solves
+    std::vector<cd> tmp;
+    cudaMemsetAsync(x, 0, N * sizeof(zd), ctx->stream);
+    cudaMemcpyAsync(K.r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
+    st = dot_host(ctx, K, b, 1, b, tmp);
+    double bn = std::sqrt(tmp[0].real());
+    zd* r = nullptr;
+    if (st == SGF_OK) st = al(&r, N);
+    if (st == SGF_OK) cudaMemcpyAsync(r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
+    for (int outer = 0; outer < 30 && st == SGF_OK; ++outer) {
+      int it_in = 0;
+      double rr_in = 1;
+      st = gmres(ctx, K, 32, r, dlt, 1e-6, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in);
+      if (st != SGF_OK) break;
+      its += it_in;
+      launch_axpby(x, zd(1, 0), dlt, zd(1, 0), N, ctx->stream);
+      st = apply_prec(ctx, x, r, 64);
+      ++its;
+      if (st != SGF_OK) break;
+      launch_axpby(r, zd(1, 0), b, zd(-1, 0), N, ctx->stream);
+      st = dot_host(ctx, K, r, 1, r, tmp);
+      rr = std::sqrt(tmp[0].real()) / bn;
+      if (rr <= tol || its >= maxit) break;
+    }
+  }
+  if (st == SGF_OK) {
+    cudaMemcpyAsync(mu_dev, x, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+  }
+  for (void* p : mine) cudaFree(p);
+  if (iters) *iters = its;
+  if (relres) *relres = rr;
+  if (st != SGF_OK) return st;
+  if (!(rr <= tol)) return set_err(ctx, SGF_ENOCONV, "GMRES stopped at relative residual %g after %d applications", rr, its);
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
+                                   double* energy_err) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (n_hi < n_lo || n_hi - n_lo > 100000) return set_err(ctx, SGF_EINVAL, "bad mode range");
+  int nmod = n_hi - n_lo + 1;
+  std::vector<int> ue = ueta_set(ctx);
+  std::vector<double> mp(6 * nmod);
+  std::vector<cd> bns(nmod);
+  for (int t = 0; t < nmod; ++t) {
+    int n = n_lo + t;
+    double an = ctx->alpha + 2 * SGF_PI * n / ctx->d;
+    cd bn = beta_host(ctx->k, an);
+    cd Q = Qj_host(bn, ctx->prm.h, ctx->prm.j);
+    bool in = std::find(ue.begin(), ue.end(), n) != ue.end();
+    mp[6 * t] = an; mp[6 * t + 1] = bn.real(); mp[6 * t + 2] = bn.imag();
+    mp[6 * t + 3] = Q.real(); mp[6 * t + 4] = Q.imag(); mp[6 * t + 5] = in ? 1.0 : 0.0;
+    bns[t] = bn;
+  }
+  double* d_mp;
+  zd* d_B;
+  CU(cudaMalloc(&d_mp, mp.size() * sizeof(double)));
+  CU(cudaMalloc(&d_B, nmod * sizeof(zd)));
+  cudaMemcpyAsync(d_mp, mp.data(), mp.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e = launch_rayleigh_mp(ctx, (const zd*)mu_dev, nmod, d_mp, d_B);
+  std::vector<zd> hB(nmod);
+  cudaMemcpyAsync(hB.data(), d_B, nmod * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(d_mp);
+  cudaFree(d_B);
+  if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "rayleigh: %s", cudaGetErrorString(e));
+  double sum = 0;
+  for (int t = 0; t < nmod; ++t) {
+    if (B) { B[2 * t] = hB[t].re; B[2 * t + 1] = hB[t].im; }
+    double an = ctx->alpha + 2 * SGF_PI * (n_lo + t) / ctx->d;
+    bool prop = ctx->k * ctx->k - an * an > 0;
+    double en = prop ? bns[t].real() / ctx->beta * abs2(hB[t]) : 0.0;
+    if (eff) eff[t] = en;
+    sum += en;
+  }
+  if (energy_err) *energy_err = 1.0 - sum;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_info(const sgf_ctx* ctx, double* info) {
+  if (!ctx || !info) return SGF_EINVAL;
+  if (!ctx->built) return SGF_ESTATE;
+  double v[16] = {(double)ctx->N, (double)ctx->n_occ, (double)ctx->nnz, (double)ctx->og[0].Px,
+                  (double)ctx->og[0].nrow, (double)ctx->og[0].Py, (double)ctx->og[1].Px, (double)ctx->og[1].nrow,
+                  (double)ctx->og[1].Py, (double)ctx->neq, (double)ctx->nfit, (double)ctx->nb,
+                  (double)ctx->nm, ctx->bytes64, ctx->bytes32, (double)ctx->launches_per_apply};
+  memcpy(info, v, sizeof(v));
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_set_profiling(sgf_ctx* ctx, int on) {
+  if (!ctx) return SGF_EINVAL;
+  ctx->profiling = on != 0;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_debug_mask(sgf_ctx* ctx, int mask) {
+  if (!ctx || mask < 0 || mask > 15) return SGF_EINVAL;
+  ctx->debug_mask = mask;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_stage_times(const sgf_ctx* ctx, double* t) {
+  if (!ctx || !t) return SGF_EINVAL;
+  for (int i = 0; i < 8; ++i) t[i] = ctx->stage_ms[i];
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_debug_table(const sgf_ctx* ctx_, int lam, int kind, void* host_out) {
+  sgf_ctx* ctx = const_cast<sgf_ctx*>(ctx_);
+  if (!ctx || !host_out || lam < 0 || lam > 1 || kind < 0 || kind > 1) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  long n = (long)ctx->og[lam].Px * ctx->og[lam].Py;
+  zd* tmp;
+  CU(cudaMalloc(&tmp, n * sizeof(zd)));
+  cudaError_t e = launch_debug_table(ctx, lam, kind, tmp);
+  cudaMemcpyAsync(host_out, tmp, n * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "debug table: %s", cudaGetErrorString(e));
+  return SGF_OK;
+}

@@ -1,0 +1,141 @@
+// Shared device helpers of the sgf library: complex arithmetic, free-space and shifted Green
+// functions (Bruno & Maas, eqs. free_space, shifted_green_function), the smooth windows of
+// eq. S_def, and launch/error helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define SGF_PI 3.14159265358979323846
+
+template <typename T>
+struct cplx {
+  T re, im;
+  __host__ __device__ cplx() : re(0), im(0) {}
+  __host__ __device__ cplx(T r, T i = 0) : re(r), im(i) {}
+  template <typename U>
+  __host__ __device__ explicit cplx(const cplx<U>& o) : re((T)o.re), im((T)o.im) {}
+};
+
+template <typename T>
+__host__ __device__ inline cplx<T> operator+(cplx<T> a, cplx<T> b) { return cplx<T>(a.re + b.re, a.im + b.im); }
+template <typename T>
+__host__ __device__ inline cplx<T> operator-(cplx<T> a, cplx<T> b) { return cplx<T>(a.re - b.re, a.im - b.im); }
+template <typename T>
+__host__ __device__ inline cplx<T> operator-(cplx<T> a) { return cplx<T>(-a.re, -a.im); }
+template <typename T>
+__host__ __device__ inline cplx<T> operator*(cplx<T> a, cplx<T> b) {
+  return cplx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ inline cplx<T> operator*(T s, cplx<T> a) { return cplx<T>(s * a.re, s * a.im); }
+template <typename T>
+__host__ __device__ inline cplx<T> operator*(cplx<T> a, T s) { return cplx<T>(s * a.re, s * a.im); }
+template <typename T>
+__host__ __device__ inline cplx<T>& operator+=(cplx<T>& a, cplx<T> b) { a.re += b.re; a.im += b.im; return a; }
+template <typename T>
+__host__ __device__ inline cplx<T>& operator-=(cplx<T>& a, cplx<T> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <typename T>
+__host__ __device__ inline cplx<T> conj(cplx<T> a) { return cplx<T>(a.re, -a.im); }
+template <typename T>
+__host__ __device__ inline T abs2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+// a * conj(b)
+template <typename T>
+__host__ __device__ inline cplx<T> mulc(cplx<T> a, cplx<T> b) {
+  return cplx<T>(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+template <typename T>
+__device__ inline cplx<T> fma_c(cplx<T> a, cplx<T> b, cplx<T> c) {  // a*b + c
+  return cplx<T>(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
+}
+
+typedef cplx<double> zd;
+typedef cplx<float> zf;
+
+__host__ __device__ inline zd cdiv(zd a, zd b) {
+  double s = b.re * b.re + b.im * b.im;
+  return zd((a.re * b.re + a.im * b.im) / s, (a.im * b.re - a.re * b.im) / s);
+}
+
+// e^{i t}
+__device__ inline zd expi(double t) {
+  double s, c;
+  sincos(t, &s, &c);
+  return zd(c, s);
+}
+// e^{z} for complex z
+__device__ inline zd cexpz(zd z) {
+  double m = exp(z.re), s, c;
+  sincos(z.im, &s, &c);
+  return zd(m * c, m * s);
+}
+// sin(z), complex
+__device__ inline zd csin(zd z) {
+  double s, c;
+  sincos(z.re, &s, &c);
+  return zd(s * cosh(z.im), c * sinh(z.im));
+}
+// sin(z)/z with the series 1 - z^2/6 + z^4/120 for |z| < 1e-3
+__device__ inline zd csinc(zd z) {
+  double a2 = z.re * z.re + z.im * z.im;
+  if (a2 < 1e-6) {
+    zd z2 = z * z;
+    return zd(1.0, 0.0) - (1.0 / 6.0) * z2 + (1.0 / 120.0) * (z2 * z2);
+  }
+  return cdiv(csin(z), z);
+}
+
+// H0^(1)(x), H1^(1)(x) for real x > 0 from the CUDA Bessel functions of the first and second kind.
+__device__ inline zd hankel0(double x) { return zd(j0(x), y0(x)); }
+__device__ inline zd hankel1(double x) { return zd(j1(x), y1(x)); }
+
+// Free-space G = (i/4) H0(k r) and its gradient (dG/dX, dG/dY) = (i/4)(-k H1(k r)) (X, Y)/r.
+struct GreenVal {
+  zd g, gx, gy;
+};
+__device__ inline void green0_add(double k, double X, double Y, double w, bool want_val, GreenVal& acc) {
+  double r = hypot(X, Y);
+  double kr = k * r;
+  if (want_val) {
+    zd h0 = hankel0(kr);
+    acc.g += zd(-0.25 * w * h0.im, 0.25 * w * h0.re);
+  }
+  zd h1 = hankel1(kr);
+  // (i/4)(-k) h1 / r = (-k/(4r)) * (i h1) = (-k/(4r)) * (-h1.im, h1.re)
+  double c = -0.25 * k * w / r;
+  zd ih1(-h1.im, h1.re);
+  acc.gx += (c * X) * ih1;
+  acc.gy += (c * Y) * ih1;
+}
+
+// Shifted G_j = sum_{m=0..j} (-1)^m C(j,m) G(X, Y + m h) and gradient; skip_m0 drops the m = 0
+// term (the self term of the punctured Green function at coincident points).
+__device__ inline GreenVal green_j(double k, int j, double h, double X, double Y, bool skip_m0,
+                                   bool want_val, const double* binw) {
+  GreenVal acc;
+  acc.g = zd(0, 0);
+  acc.gx = zd(0, 0);
+  acc.gy = zd(0, 0);
+  for (int m = skip_m0 ? 1 : 0; m <= j; ++m) green0_add(k, X, Y + m * h, binw[m], want_val, acc);
+  return acc;
+}
+
+// S_{gamma,a}(x) of eq. S_def.
+__host__ __device__ inline double window_S(double x, double gamma, double a) {
+  x = fabs(x);
+  if (x <= gamma) return 1.0;
+  if (x >= a) return 0.0;
+  double u = (x - gamma) / (a - gamma);
+  return exp(2.0 * exp(-1.0 / u) / (u - 1.0));
+}
+
+#define SGF_CUDA_CHECK(call)                                                      \
+  do {                                                                            \
+    cudaError_t err__ = (call);                                                   \
+    if (err__ != cudaSuccess) {                                                   \
+      return set_err(ctx, SGF_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,   \
+                     cudaGetErrorString(err__));                                  \
+    }                                                                             \
+  } while (0)
+
+static inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }

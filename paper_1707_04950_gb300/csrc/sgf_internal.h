@@ -1,0 +1,118 @@
+// Internal state of an sgf context and the kernel launchers shared by the two translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/sgf.h"
+#include "sgf_common.cuh"
+
+// Geometry of one equivalent-source grid Pi_lambda^per (Section 5.4): X cyclic with Px points,
+// nrow rows in Y; FFT length Py >= 2 nrow - 1 in Y (linear convolution).
+struct Orient {
+  int Px, logPx, nrow, Py, logPy;
+  double dxg, dyg;
+};
+
+// Device operator data of one precision (T = double or float).
+template <typename T>
+struct OpData {
+  cplx<T>* P = nullptr;        // per cell [2 orientations][2 neq][n_q] projection matrices
+  cplx<T>* Ip = nullptr;       // per node [n_fit] reconstruction rows times the untwist e^{i alpha x_t}
+  cplx<T>* src_tw = nullptr;   // [n_occ][2][neq] twist e^{-i alpha x_src} of the scatter
+  cplx<T>* Khat[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [lam][mono, dip] spectra / (Px Py)
+  cplx<T>* grid[2] = {nullptr, nullptr};                          // [lam]: xi then zeta, Px*nrow each
+  cplx<T>* tw = nullptr;       // FFT twiddles e^{-2 pi i k / 2^twlog}
+};
+
+struct sgf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char err[2048] = {0};
+  // problem definition
+  double d = 0;
+  std::vector<double> fa, fb;
+  double k = 0, theta = 0, alpha = 0, beta = 0;
+  int bc = 0;
+  sgf_params prm{};
+  bool have_profile = false, have_wave = false, have_params = false, built = false;
+  // derived sizes
+  int N = 0, neq = 0, nfit = 0, nb = 0, n_occ = 0, nm = 0;
+  double dx = 0, L = 0, a_s = 0, gam = 0;
+  Orient og[2];
+  int twlog = 0;
+  // host geometry
+  std::vector<double> hx, hf, hf1, hf2;
+  std::vector<int> cell_start;  // [n_occ + 1] into node_idx
+  std::vector<int> node_idx;    // nodes in cell order
+  std::vector<int> occ_cx, occ_cy;
+  // device geometry and index tables
+  double *d_x = nullptr, *d_f = nullptr, *d_f1 = nullptr, *d_f2 = nullptr, *d_coef = nullptr;
+  int *d_cell_start = nullptr, *d_node_idx = nullptr, *d_node_cell = nullptr;
+  int *d_occ_cx = nullptr, *d_occ_cy = nullptr;
+  int* d_src_gidx = nullptr;   // [n_occ][2][neq]
+  int* d_samp_gidx = nullptr;  // [n_occ][n_fit]
+  double* d_binw = nullptr;    // (-1)^m C(j,m)
+  // near field: blocks (q, r) of dense n_q x n_r values
+  int n_blk = 0;
+  long nnz = 0;
+  int* d_blk_start = nullptr;  // [n_occ + 1] into block list
+  int* d_blk_r = nullptr;      // occupied index of the source cell
+  long* d_blk_off = nullptr;   // value offset
+  zd* d_blk_ph = nullptr;      // quasi-periodic phase of the source cell copy
+  zd* d_C = nullptr;
+  // modes
+  zd *d_MT = nullptr, *d_MS = nullptr, *d_msum = nullptr;
+  // precision-specific operator data
+  OpData<double> o64;
+  OpData<float> o32;
+  // FP64 kernel-table copies before the Y transform (testing)
+  zd* d_Tx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // workspace
+  zd *d_mu_tmp = nullptr, *d_out_tmp = nullptr;
+  std::vector<void*> allocs;
+  // profiling
+  bool profiling = false;
+  int debug_mask = 15;
+  cudaEvent_t ev[8] = {nullptr};
+  double stage_ms[8] = {0};
+  int launches_per_apply = 0;
+  double bytes64 = 0, bytes32 = 0;
+};
+
+sgf_status set_err(sgf_ctx* ctx, sgf_status st, const char* fmt, ...);
+
+// ---------------------------------------------------------------- launchers (sgf_kernels.cu)
+struct BuildArgs;
+cudaError_t launch_profile(sgf_ctx* c);
+cudaError_t launch_build_matrices(sgf_ctx* c, zd* d_Acoll, zd* d_Bfb, const double* d_coll_rel,
+                                  const double* d_src_rel, const double* d_samp_rel);
+cudaError_t launch_qr_pinv(sgf_ctx* c, zd* A, int m_out, int n, bool augment, double reg, zd* pinv, zd* scratch);
+cudaError_t launch_build_P(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel);
+cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel);
+cudaError_t launch_tables(sgf_ctx* c);
+cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const double* d_samp_rel,
+                           const double* d_src_rel);
+struct NearPairs {  // device arrays of the (q, r) block list
+  int n = 0;
+  int *q = nullptr, *r = nullptr, *wrap = nullptr, *dcx = nullptr;
+  long* off = nullptr;
+};
+cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
+                        const double* d_kress);
+cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n);
+cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s);
+cudaError_t launch_rhs(sgf_ctx* c, zd* out);
+cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
+cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
+cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B);
+cudaError_t launch_twiddles(sgf_ctx* c);
+cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);
+// Krylov helpers
+cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,
+                        cudaStream_t s);
+cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s);
+cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s);  // y = a x + b y

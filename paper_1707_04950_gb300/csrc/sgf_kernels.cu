@@ -1,0 +1,982 @@
+// Device kernels of the sgf library.
+//
+// Initialisation (Algorithm 2 of Bruno & Maas, all FP64):
+//   k_profile        nodes and profile derivatives (Section 4.2)
+//   k_build_coll     collocation matrix of the equivalent-source least squares (eq. eq_source_point)
+//   k_build_fb       cell-reconstruction matrix on the cell-boundary samples (eq. plwave_QR)
+//   k_qr_pinv        Householder QR least-squares operator R^{-1} Q^H of a small matrix (one block)
+//   k_build_P        per-cell projection matrices P_q = pinv_eq * T_q (EqSources as a linear map)
+//   k_build_I        per-node reconstruction rows (PlaneWaveWeights + NonIntersecting)
+//   k_table_spec     periodised kernel rows by the shifted spectral series, folded mod P_x
+//                    (eq. shifted_quasi_per_rayleigh, Remark large_FFT_eval)
+//   k_table_spat     periodised kernel rows near shifted poles by the windowed lattice sum,
+//                    warp-reduced over periods (eq. Gq_limit)
+//   k_phi_off        free-space shifted kernel between cell samples and local equivalent sources,
+//                    per relative cell offset (the q-independent local grid, eq. pi_q_hat)
+//   k_near           block-sparse near operator: exact intersecting sum (eq. final_correction_0),
+//                    singular quadrature (eq. local_mat) and the local equivalent-source
+//                    subtraction (eqs. small_convolution, psi_na_sum) folded into one matrix
+//   k_modes          separable factors of D_M (eq. D_M_deltax)
+// Forward map (Algorithm 3), templated on the far-field precision T:
+//   k_project        EqSources + GlobalEqSMerge (scatter with the quasi-periodic twist) + mode sums
+//   k_fft_x/k_conv_y GlobalFFT (sgf_fft.cuh)
+//   k_interp_near    Combine-lambda + NonIntersecting + Intersecting + EvalSingular + EvalModes +
+//                    AddOperators
+#include "sgf_internal.h"
+#include "sgf_fft.cuh"
+
+// ============================================================== small device helpers
+__device__ inline int orient_of_sample(int t, int p) { return t < 2 * (p + 1) ? 0 : 1; }
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ inline cplx<T> warp_sum(cplx<T> v) {
+  v.re = warp_sum(v.re);
+  v.im = warp_sum(v.im);
+  return v;
+}
+
+// J_n(x) e^{i n th} for any integer n (J_{-n} = (-1)^n J_n)
+__device__ inline zd fb_Z(int n, double kr, double th) {
+  int an = n < 0 ? -n : n;
+  double J = jn(an, kr);
+  if (n < 0 && (an & 1)) J = -J;
+  zd e = expi(n * th);
+  return J * e;
+}
+__device__ inline double fb_norm(int n, double krho0) {
+  int an = n < 0 ? -n : n;
+  double v = 1.0;
+  for (int i = 1; i <= an; ++i) v *= (krho0 / 2.0) / i;
+  return v;
+}
+
+// ============================================================== profile
+__global__ void k_profile(const double* __restrict__ coef, int M, double d, int N, double* x, double* f,
+                          double* f1, double* f2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* a = coef;
+  const double* b = coef + (M + 1);
+  double fv = a[0], d1 = 0, d2 = 0;
+  for (int m = 1; m <= M; ++m) {
+    long mm = ((long)m * (long)(i + 1)) % N;  // 2 pi m x/d = 2 pi m (i+1)/N
+    double s, c;
+    sincospi(2.0 * (double)mm / (double)N, &s, &c);
+    double w = 2.0 * SGF_PI * m / d;
+    fv += a[m] * c + b[m] * s;
+    d1 += w * (-a[m] * s + b[m] * c);
+    d2 += -w * w * (a[m] * c + b[m] * s);
+  }
+  x[i] = d * (double)(i + 1) / (double)N;
+  f[i] = fv;
+  f1[i] = d1;
+  f2[i] = d2;
+}
+
+cudaError_t launch_profile(sgf_ctx* c) {
+  int M = (int)c->fa.size() - 1;
+  k_profile<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(c->d_coef, M, c->d, c->N, c->d_x, c->d_f, c->d_f1, c->d_f2);
+  return cudaGetLastError();
+}
+
+// ============================================================== least-squares matrices
+// A[lam] is n_coll x 2 neq, column-major (lda = n_coll + 2 neq): monopole columns G(x_t - y_s), dipole
+// columns d/dnu_y G = -nu . grad G(x_t - y_s), nu = (0,1) for H and (1,0) for V.
+__global__ void k_build_coll(double k, int ncoll, int neq, const double* __restrict__ coll_rel,
+                             const double* __restrict__ src_rel, zd* A) {
+  const long lda = ncoll + 2 * neq;  // room for the Tikhonov rows
+  int lam = blockIdx.y;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ncoll * neq) return;
+  int t = idx % ncoll, s = idx / ncoll;
+  double X = coll_rel[2 * t] - src_rel[(lam * neq + s) * 2];
+  double Y = coll_rel[2 * t + 1] - src_rel[(lam * neq + s) * 2 + 1];
+  GreenVal g;
+  g.g = zd(0, 0); g.gx = zd(0, 0); g.gy = zd(0, 0);
+  green0_add(k, X, Y, 1.0, true, g);
+  zd* Al = A + (long)lam * lda * 2 * neq;
+  Al[(long)s * lda + t] = g.g;
+  Al[(long)(neq + s) * lda + t] = lam == 0 ? -g.gy : -g.gx;
+}
+
+// B is n_fit x nb column-major: b_n(x_t - centre), n = -n_fb..n_fb, scaled by (k rho0/2)^|n|/|n|!
+__global__ void k_build_fb(double k, double L, int nfit, int nfb, const double* __restrict__ samp_rel, zd* B) {
+  int nb = 2 * nfb + 1;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nfit * nb) return;
+  int t = idx % nfit, bi = idx / nfit;
+  int n = bi - nfb;
+  double X = samp_rel[2 * t] - 0.5 * L, Y = samp_rel[2 * t + 1] - 0.5 * L;
+  double r = hypot(X, Y), th = atan2(Y, X);
+  double krho0 = k * L / sqrt(2.0);
+  B[(long)bi * nfit + t] = (1.0 / fb_norm(n, krho0)) * fb_Z(n, k * r, th);
+}
+
+cudaError_t launch_build_matrices(sgf_ctx* c, zd* d_Acoll, zd* d_Bfb, const double* d_coll_rel,
+                                  const double* d_src_rel, const double* d_samp_rel) {
+  int nc = c->prm.n_coll, neq = c->neq;
+  dim3 g1(ceil_div((long)nc * neq, 128), 2);
+  k_build_coll<<<g1, 128, 0, c->stream>>>(c->k, nc, neq, d_coll_rel, d_src_rel, d_Acoll);
+  k_build_fb<<<ceil_div((long)c->nfit * c->nb, 128), 128, 0, c->stream>>>(c->k, c->L, c->nfit, c->prm.n_fb, d_samp_rel,
+                                                                          d_Bfb);
+  return cudaGetLastError();
+}
+
+// ============================================================== Householder QR least squares
+// Tikhonov augmentation of a column-major m0 x n matrix stored with leading dimension m0 + n:
+// rows m0..m0+n-1 become reg |A|_F I (one block).
+__global__ void k_augment(zd* A, int m0, int n, double reg) {
+  __shared__ double red[256];
+  const int lda = m0 + n;
+  double part = 0;
+  for (int idx = threadIdx.x; idx < m0 * n; idx += blockDim.x) part += abs2(A[(long)(idx / m0) * lda + idx % m0]);
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double s = reg * sqrt(red[0]);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int c = idx / n, r = idx % n;
+    A[(long)c * lda + m0 + r] = zd(r == c ? s : 0.0, 0);
+  }
+}
+
+// One block. A (m x n, column-major) is overwritten by the Householder vectors; pinv (n x m_out,
+// row-major: pinv[s*m_out + t]) = the first m_out columns of R^{-1} Q^H. scratch: n*n (R) + n
+// (alpha) + m*m (work) entries.
+__global__ void k_qr_pinv(zd* A, int m, int n, int m_out, zd* pinv, zd* scratch) {
+  __shared__ double red[256];
+  zd* R = scratch;
+  zd* alph = scratch + (long)n * n;
+  zd* E = alph + n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = 0; c < n; ++c) {
+    zd* col = A + (long)c * m;
+    double part = 0;
+    for (int i = c + tid; i < m; i += nt) part += abs2(col[i]);
+    red[tid] = part;
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    double xn2 = red[0];
+    __syncthreads();
+    zd x0 = col[c];
+    double ax0 = sqrt(abs2(x0));
+    double xn = sqrt(xn2);
+    zd ph = ax0 > 0 ? zd(x0.re / ax0, x0.im / ax0) : zd(1, 0);
+    zd al = -xn * ph;
+    zd v0 = x0 - al;
+    double vn2 = xn2 - ax0 * ax0 + abs2(v0);
+    double inv = vn2 > 0 ? 1.0 / sqrt(vn2) : 0.0;
+    __syncthreads();
+    for (int i = c + tid; i < m; i += nt) col[i] = (i == c ? v0 : col[i]) * inv;
+    if (tid == 0) alph[c] = al;
+    __syncthreads();
+    for (int cc = c + 1 + tid; cc < n; cc += nt) {
+      zd* cl = A + (long)cc * m;
+      zd dot(0, 0);
+      for (int i = c; i < m; ++i) dot += mulc(cl[i], col[i]);  // v^H a
+      for (int i = c; i < m; ++i) cl[i] -= 2.0 * (col[i] * dot);
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < n * n; r += nt) {
+    int i = r / n, jj = r % n;
+    R[r] = (jj > i) ? A[(long)jj * m + i] : (jj == i ? alph[i] : zd(0, 0));
+  }
+  __syncthreads();
+  for (int t = tid; t < m_out; t += nt) {
+    zd* e = E + (long)t * m;
+    for (int i = 0; i < m; ++i) e[i] = zd(i == t ? 1.0 : 0.0, 0);
+    for (int c = 0; c < n; ++c) {
+      const zd* v = A + (long)c * m;
+      zd dot(0, 0);
+      for (int i = c; i < m; ++i) dot += mulc(e[i], v[i]);
+      for (int i = c; i < m; ++i) e[i] -= 2.0 * (v[i] * dot);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      zd s = e[i];
+      for (int jj = i + 1; jj < n; ++jj) s -= R[(long)i * n + jj] * e[jj];
+      e[i] = cdiv(s, R[(long)i * n + i]);
+    }
+    for (int i = 0; i < n; ++i) pinv[(long)i * m_out + t] = e[i];
+  }
+}
+
+// augment: A is stored with leading dimension m_out + n and gets the Tikhonov rows (reg may be 0).
+cudaError_t launch_qr_pinv(sgf_ctx* c, zd* A, int m_out, int n, bool augment, double reg, zd* pinv, zd* scratch) {
+  int mt = augment ? m_out + n : m_out;
+  if (mt > 256) return cudaErrorInvalidValue;
+  if (augment) k_augment<<<1, 256, 0, c->stream>>>(A, m_out, n, reg);
+  k_qr_pinv<<<1, 256, 0, c->stream>>>(A, mt, n, m_out, pinv, scratch);
+  return cudaGetLastError();
+}
+
+// ============================================================== projection matrices P_q
+// Block per occupied cell, warp per node: T_t = true-field kernel at collocation point t, then
+// P[lam][s][l] = sum_t pinv_eq[lam][s][t] T_t.
+struct GeoArgs {
+  double k, alpha, d, dx, L, hmin, gam, a_s;
+  int N, j, bc, p, neq, nfit, ncoll, nb, nfb, Ma, nx;
+  double h;
+};
+
+__global__ void k_build_P(GeoArgs g, const int* __restrict__ cell_start, const int* __restrict__ node_idx,
+                          const int* __restrict__ occ_cx, const int* __restrict__ occ_cy,
+                          const double* __restrict__ x, const double* __restrict__ f, const double* __restrict__ f1,
+                          const double* __restrict__ coll_rel, const zd* __restrict__ pinv_eq, zd* P) {
+  extern __shared__ unsigned char smem_raw[];
+  zd* buf = reinterpret_cast<zd*>(smem_raw);
+  const int q = blockIdx.x;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int s0 = cell_start[q], nq = cell_start[q + 1] - s0;
+  const double cx = occ_cx[q] * g.L, cy = g.hmin + occ_cy[q] * g.L;
+  zd* T = buf + warp * g.ncoll;
+  const int nout = 4 * g.neq;
+  zd* Pq = P + (long)nout * s0;
+  for (int l = warp; l < nq; l += nw) {
+    int nid = node_idx[s0 + l];
+    double xl = x[nid], fl = f[nid], sl = sqrt(1 + f1[nid] * f1[nid]);
+    for (int t = lane; t < g.ncoll; t += 32) {
+      double X = cx + coll_rel[2 * t] - xl, Y = cy + coll_rel[2 * t + 1] - fl;
+      GreenVal gv;
+      gv.g = zd(0, 0); gv.gx = zd(0, 0); gv.gy = zd(0, 0);
+      green0_add(g.k, X, Y, 1.0, g.bc == 1, gv);
+      T[t] = g.bc == 0 ? g.dx * (f1[nid] * gv.gx - gv.gy) : (sl * g.dx) * gv.g;
+    }
+    __syncwarp();
+    for (int o = lane; o < nout; o += 32) {
+      int lam = o / (2 * g.neq), s = o % (2 * g.neq);
+      const zd* pr = pinv_eq + ((long)lam * 2 * g.neq + s) * g.ncoll;
+      zd acc(0, 0);
+      for (int t = 0; t < g.ncoll; ++t) acc += pr[t] * T[t];
+      Pq[(long)o * nq + l] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+static GeoArgs geo_args(sgf_ctx* c) {
+  GeoArgs g;
+  g.k = c->k; g.alpha = c->alpha; g.d = c->d; g.dx = c->dx; g.L = c->L; g.hmin = c->prm.hmin;
+  g.gam = c->gam; g.a_s = c->a_s; g.N = c->N; g.j = c->prm.j; g.bc = c->bc; g.p = c->prm.p; g.neq = c->neq;
+  g.nfit = c->nfit; g.ncoll = c->prm.n_coll; g.nb = c->nb; g.nfb = c->prm.n_fb; g.Ma = c->prm.Ma; g.nx = c->prm.nx;
+  g.h = c->prm.h;
+  return g;
+}
+
+
+cudaError_t launch_build_P(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel) {
+  GeoArgs g = geo_args(c);
+  size_t sm = (size_t)8 * g.ncoll * sizeof(zd);
+  cudaFuncSetAttribute(k_build_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_build_P<<<c->n_occ, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x, c->d_f,
+                                                c->d_f1, d_coll_rel, pinv_eq, c->o64.P);
+  return cudaGetLastError();
+}
+
+// ============================================================== reconstruction rows I
+// Thread per node (cell order): E_b = basis (Dirichlet) or its unit-normal derivative (Neumann)
+// at the node relative to the cell centre; I[t] = sum_b E_b pinv_fb[b][t]; Ip[t] = I[t] e^{i alpha x_t}.
+__global__ void k_build_I(GeoArgs g, const int* __restrict__ node_cell, const int* __restrict__ node_idx,
+                          const int* __restrict__ occ_cx, const int* __restrict__ occ_cy, const double* __restrict__ x,
+                          const double* __restrict__ f, const double* __restrict__ f1,
+                          const double* __restrict__ samp_rel, const zd* __restrict__ pinv_fb, zd* Iplain, zd* Ip) {
+  int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= g.N) return;
+  int q = node_cell[pos];
+  int nid = node_idx[pos];
+  double cxl = occ_cx[q] * g.L, cyl = g.hmin + occ_cy[q] * g.L;
+  double X = x[nid] - (cxl + 0.5 * g.L), Y = f[nid] - (cyl + 0.5 * g.L);
+  double r = hypot(X, Y), th = atan2(Y, X), kr = g.k * r;
+  double krho0 = g.k * g.L / sqrt(2.0);
+  double sn = sqrt(1 + f1[nid] * f1[nid]);
+  double nux = -f1[nid] / sn, nuy = 1.0 / sn;
+  zd E[64];
+  for (int bi = 0; bi < g.nb; ++bi) {
+    int n = bi - g.nfb;
+    double inv = 1.0 / fb_norm(n, krho0);
+    if (g.bc == 0) {
+      E[bi] = inv * fb_Z(n, kr, th);
+    } else {
+      zd zm = fb_Z(n - 1, kr, th), zp = fb_Z(n + 1, kr, th);
+      zd dzx = (0.5 * g.k) * (zm - zp);
+      zd dzy = zd(0, 0.5 * g.k) * (zp + zm);
+      E[bi] = inv * (nux * dzx + nuy * dzy);
+    }
+  }
+  for (int t = 0; t < g.nfit; ++t) {
+    zd acc(0, 0);
+    for (int bi = 0; bi < g.nb; ++bi) acc += E[bi] * pinv_fb[(long)bi * g.nfit + t];
+    Iplain[(long)pos * g.nfit + t] = acc;
+    double xt = cxl + samp_rel[2 * t];
+    Ip[(long)pos * g.nfit + t] = acc * expi(g.alpha * xt);
+  }
+}
+
+cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel) {
+  GeoArgs g = geo_args(c);
+  k_build_I<<<ceil_div(c->N, 64), 64, 0, c->stream>>>(g, c->d_node_cell, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x,
+                                                       c->d_f, c->d_f1, d_samp_rel, pinv_fb, d_Iplain, c->o64.Ip);
+  return cudaGetLastError();
+}
+
+// ============================================================== periodised kernel table
+struct TabArgs {
+  double k, alpha, d, h, dxg, dyg, delta_min, spec_exp, A, cwin;
+  int j, Px, logPx, Py, nrow, lam;
+};
+
+__device__ inline double row_delta(double Y, int j, double h) {
+  double dl = fabs(Y);
+  for (int m = 1; m <= j; ++m) dl = fmin(dl, fabs(Y + m * h));
+  return dl;
+}
+
+// (1 - e^{i beta h})^j / beta = (-2i)^j e^{i j beta h/2} sin^{j-1}(beta h/2) (h/2) sinc(beta h/2)
+__device__ inline zd Qj_dev(zd beta, double h, int j) {
+  if (j == 0) return cdiv(zd(1, 0), beta);
+  zd half = (0.5 * h) * beta;
+  zd sn = csin(half);
+  zd acc = (0.5 * h) * csinc(half);
+  for (int m = 1; m < j; ++m) acc = acc * sn;
+  zd mi2(1, 0);
+  for (int m = 0; m < j; ++m) mi2 = mi2 * zd(0, -2);
+  zd ij = cexpz(zd(0, (double)j) * half);
+  return mi2 * ij * acc;
+}
+
+// c_n(Y) and cy_n(Y) of the shifted spectral series (eq. shifted_quasi_per_rayleigh), with the
+// exact beta -> 0 rewrite of eq. betan_taylor where |beta| (|Y| + j h) < 1.
+__device__ inline void spec_coef(double k, double alpha, double d, int j, double h, double Y, int n,
+                                 const double* binw, zd& c, zd& cy, double& an) {
+  an = alpha + 2.0 * SGF_PI * n / d;
+  double q = k * k - an * an;
+  bool real_b = q >= 0;
+  double bm = sqrt(fabs(q));
+  zd beta = real_b ? zd(bm, 0) : zd(0, bm);
+  zd S0(0, 0), S1(0, 0);
+  for (int m = 0; m <= j; ++m) {
+    double t = Y + m * h, at = fabs(t);
+    zd em = real_b ? expi(bm * at) : zd(exp(-bm * at), 0);
+    S0 += binw[m] * em;
+    S1 += (t > 0 ? binw[m] : (t < 0 ? -binw[m] : 0.0)) * em;
+  }
+  cy = (-0.5 / d) * S1;
+  if (j >= 1 && bm * (fabs(Y) + j * h) < 1.0) {
+    zd acc = cexpz(zd(0, 1) * (Y * beta)) * Qj_dev(beta, h, j);
+    for (int m = 0; m <= j; ++m) {
+      double t = Y + m * h;
+      if (t < 0) acc -= zd(0, 2.0 * binw[m] * t) * csinc(t * beta);
+    }
+    c = zd(0, 0.5 / d) * acc;
+  } else {
+    c = zd(0, 0.5 / d) * cdiv(S0, beta);
+  }
+}
+
+// Block per lag row iy_lag in [-(nrow-1), nrow-1] whose delta >= delta_min: writes
+// Tx[kx][iy_cyc] = Px * sum_{n = kx mod Px} coefficient (the X transform of the twisted row).
+__global__ void k_table_spec(TabArgs a, const double* __restrict__ binw, zd* Txm, zd* Txd) {
+  const int iyl = (int)blockIdx.x - (a.nrow - 1);
+  const double Y = iyl * a.dyg;
+  const double dl = row_delta(Y, a.j, a.h);
+  if (dl < a.delta_min) return;
+  double T = sqrt(a.k * a.k + (a.spec_exp / dl) * (a.spec_exp / dl));
+  long n_hi = (long)ceil((T - a.alpha) * a.d / (2 * SGF_PI));
+  long n_lo = (long)floor((-T - a.alpha) * a.d / (2 * SGF_PI));
+  const int iyc = ((iyl % a.Py) + a.Py) % a.Py;
+  for (int kx = threadIdx.x; kx < a.Px; kx += blockDim.x) {
+    // n = kx + t Px within [n_lo, n_hi]
+    long t0 = (long)ceil((double)(n_lo - kx) / a.Px), t1 = (long)floor((double)(n_hi - kx) / a.Px);
+    zd Fm(0, 0), Fd(0, 0);
+    for (long t = t0; t <= t1; ++t) {
+      int n = (int)(kx + t * a.Px);
+      zd c, cy;
+      double an;
+      spec_coef(a.k, a.alpha, a.d, a.j, a.h, Y, n, binw, c, cy, an);
+      Fm += c;
+      Fd += (a.lam == 0) ? -cy : zd(0, -an) * c;
+    }
+    Txm[(long)kx * a.Py + iyc] = (double)a.Px * Fm;
+    Txd[(long)kx * a.Py + iyc] = (double)a.Px * Fd;
+  }
+}
+
+// Warp per lag point (ix, iy_lag) of a row with delta < delta_min: windowed lattice sum over
+// periods p (lanes), X reduced to [-d/2, d/2) by the integer lag, window after differentiation,
+// the (p = 0, m = 0) term dropped at lag (0, 0). Writes the twisted values to Tl[ix][iy_cyc].
+__global__ void k_table_spat(TabArgs a, const double* __restrict__ binw, zd* Tlm, zd* Tld) {
+  const int lane = threadIdx.x % 32;
+  const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const long npts = (long)a.Px * (2 * a.nrow - 1);
+  if (wid >= npts) return;
+  const int ix = (int)(wid % a.Px);
+  const int iyl = (int)(wid / a.Px) - (a.nrow - 1);
+  const double Y = iyl * a.dyg;
+  if (row_delta(Y, a.j, a.h) >= a.delta_min) return;
+  const int ixr = ix >= a.Px / 2 ? ix - a.Px : ix;
+  const double Xr = ixr * a.dxg;
+  const bool punct = (ix == 0 && iyl == 0);
+  const int P = (int)ceil(a.A / a.d) + 1;
+  zd g(0, 0), gx(0, 0), gy(0, 0);
+  for (int p = -P + lane; p <= P; p += 32) {
+    double xp = Xr + p * a.d;
+    double S = window_S(xp, a.cwin * a.A, a.A);
+    if (S <= 0) continue;
+    GreenVal gv = green_j(a.k, a.j, a.h, xp, Y, punct && p == 0, true, binw);
+    zd ph = expi(-a.alpha * p * a.d);
+    g += (S * ph) * gv.g;
+    gx += (S * ph) * gv.gx;
+    gy += (S * ph) * gv.gy;
+  }
+  g = warp_sum(g);
+  gx = warp_sum(gx);
+  gy = warp_sum(gy);
+  if (lane == 0) {
+    zd tw = expi(-a.alpha * Xr);
+    const int iyc = ((iyl % a.Py) + a.Py) % a.Py;
+    Tlm[(long)ix * a.Py + iyc] = tw * g;
+    Tld[(long)ix * a.Py + iyc] = tw * (a.lam == 0 ? -gy : -gx);
+  }
+}
+
+__global__ void k_add_scale(zd* dst, const zd* src, long n, double s) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = s * (dst[i] + src[i]);
+}
+__global__ void k_scale(zd* dst, long n, double s) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = s * dst[i];
+}
+__global__ void k_to_f32(const zd* __restrict__ s, zf* __restrict__ d, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = zf((float)s[i].re, (float)s[i].im);
+}
+__global__ void k_twiddles(zd* tw, int twlog) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 1 << twlog;
+  if (i >= n / 2) return;
+  double s, c;
+  sincospi(-2.0 * i / n, &s, &c);
+  tw[i] = zd(c, s);
+}
+
+cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s) {
+  k_to_f32<<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+static size_t fftx_smem(int Px, int ty, size_t esz) { return (size_t)Px * ty * esz; }
+static int fftx_ty(int Px, size_t esz) {
+  int ty = (int)(96 * 1024 / ((size_t)Px * esz));
+  if (ty > 32) ty = 32;
+  if (ty < 1) ty = 1;
+  return ty;
+}
+
+template <typename T>
+static cudaError_t run_fft_x(cplx<T>* g, const Orient& o, int nrow, int narr, const cplx<T>* tw, int twlog, int dir,
+                             cudaStream_t s) {
+  int ty = fftx_ty(o.Px, sizeof(cplx<T>));
+  size_t sm = fftx_smem(o.Px, ty, sizeof(cplx<T>));
+  cudaFuncSetAttribute(k_fft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  dim3 grid(ceil_div(nrow, ty), narr);
+  k_fft_x<T><<<grid, 256, sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables(sgf_ctx* c) {
+  cudaError_t e;
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    TabArgs a;
+    a.k = c->k; a.alpha = c->alpha; a.d = c->d; a.h = c->prm.h; a.dxg = o.dxg; a.dyg = o.dyg;
+    a.delta_min = c->prm.delta_min; a.spec_exp = c->prm.spec_exp; a.A = c->prm.n_per * c->d; a.cwin = c->prm.c_win;
+    a.j = c->prm.j; a.Px = o.Px; a.logPx = o.logPx; a.Py = o.Py; a.nrow = o.nrow; a.lam = lam;
+    long n = (long)o.Px * o.Py;
+    zd* Txm = c->d_Tx[lam][0];
+    zd* Txd = c->d_Tx[lam][1];
+    zd* Tlm = c->o64.Khat[lam][0];  // lag-space scratch, overwritten below by the spectra
+    zd* Tld = c->o64.Khat[lam][1];
+    cudaMemsetAsync(Txm, 0, n * sizeof(zd), c->stream);
+    cudaMemsetAsync(Txd, 0, n * sizeof(zd), c->stream);
+    cudaMemsetAsync(Tlm, 0, n * sizeof(zd), c->stream);
+    cudaMemsetAsync(Tld, 0, n * sizeof(zd), c->stream);
+    k_table_spec<<<2 * o.nrow - 1, 256, 0, c->stream>>>(a, c->d_binw, Txm, Txd);
+    long npts = (long)o.Px * (2 * o.nrow - 1);
+    k_table_spat<<<ceil_div(npts * 32, 256), 256, 0, c->stream>>>(a, c->d_binw, Tlm, Tld);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // X transform of the spatial rows (the arrays are [Px][Py]: Py "rows" of Px points)
+    if ((e = run_fft_x<double>(Tlm, o, o.Py, 1, c->o64.tw, c->twlog, -1, c->stream)) != cudaSuccess) return e;
+    if ((e = run_fft_x<double>(Tld, o, o.Py, 1, c->o64.tw, c->twlog, -1, c->stream)) != cudaSuccess) return e;
+    k_add_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Txm, Tlm, n, 1.0);
+    k_add_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Txd, Tld, n, 1.0);
+    // Y transform into the spectra, scaled by 1/(Px Py)
+    cudaMemcpyAsync(Tlm, Txm, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(Tld, Txd, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
+    size_t sm = (size_t)o.Py * sizeof(zd);
+    cudaFuncSetAttribute(k_fft_y_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft_y_full<double><<<o.Px, 512, sm, c->stream>>>(Tlm, o.logPy, c->o64.tw, c->twlog, -1);
+    k_fft_y_full<double><<<o.Px, 512, sm, c->stream>>>(Tld, o.logPy, c->o64.tw, c->twlog, -1);
+    double sc = 1.0 / ((double)o.Px * o.Py);
+    k_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Tlm, n, sc);
+    k_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Tld, n, sc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (c->o32.Khat[lam][0]) {
+      launch_to_f32(Tlm, c->o32.Khat[lam][0], n, c->stream);
+      launch_to_f32(Tld, c->o32.Khat[lam][1], n, c->stream);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles(sgf_ctx* c) {
+  int n = 1 << c->twlog;
+  k_twiddles<<<ceil_div(n / 2, 256), 256, 0, c->stream>>>(c->o64.tw, c->twlog);
+  if (c->o32.tw) launch_to_f32(c->o64.tw, c->o32.tw, n / 2, c->stream);
+  return cudaGetLastError();
+}
+
+// Inverse X transform of the FP64 table copy for testing: out[ix][iy] = IFFT_x(Tx)/Px.
+cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out) {
+  const Orient& o = c->og[lam];
+  long n = (long)o.Px * o.Py;
+  cudaMemcpyAsync(out, c->d_Tx[lam][kind], n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
+  cudaError_t e = run_fft_x<double>(out, o, o.Py, 1, c->o64.tw, c->twlog, +1, c->stream);
+  if (e != cudaSuccess) return e;
+  k_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(out, n, 1.0 / o.Px);
+  return cudaGetLastError();
+}
+
+// ============================================================== local kernel per cell offset
+// phi[(o * nfit + t) * 2neq + s] for o = (dcx + 1) * n_dcy + (dcy - dcy_min): monopole / dipole
+// shifted free-space kernel from source s of the orientation of sample t in the cell at offset
+// (dcx, dcy) to sample t of the target cell (punctured at coincident points: m = 0 dropped).
+__global__ void k_phi_off(GeoArgs g, int dcy_min, int n_dcy, const double* __restrict__ samp_rel,
+                          const double* __restrict__ src_rel, const double* __restrict__ binw, zd* phi) {
+  long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  long tot = (long)3 * n_dcy * g.nfit * 2 * g.neq;
+  if (idx >= tot) return;
+  int s2 = (int)(idx % (2 * g.neq));
+  long rest = idx / (2 * g.neq);
+  int t = (int)(rest % g.nfit);
+  int o = (int)(rest / g.nfit);
+  int dcx = o / n_dcy - 1, dcy = dcy_min + o % n_dcy;
+  int lam = orient_of_sample(t, g.p);
+  int s = s2 % g.neq;
+  double X = samp_rel[2 * t] - (dcx * g.L + src_rel[(lam * g.neq + s) * 2]);
+  double Y = samp_rel[2 * t + 1] - (dcy * g.L + src_rel[(lam * g.neq + s) * 2 + 1]);
+  bool same = fabs(X) < 1e-12 * g.L && fabs(Y) < 1e-12 * g.L;
+  bool mono = s2 < g.neq;
+  GreenVal gv = green_j(g.k, g.j, g.h, same ? 0.0 : X, same ? 0.0 : Y, same, mono, binw);
+  phi[idx] = mono ? gv.g : (lam == 0 ? -gv.gy : -gv.gx);
+}
+
+cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const double* d_samp_rel,
+                           const double* d_src_rel) {
+  GeoArgs g = geo_args(c);
+  long tot = (long)3 * n_dcy * c->nfit * 2 * c->neq;
+  k_phi_off<<<ceil_div(tot, 256), 256, 0, c->stream>>>(g, dcy_min, n_dcy, d_samp_rel, d_src_rel, c->d_binw, d_phi);
+  return cudaGetLastError();
+}
+
+// ============================================================== near operator blocks
+// Block per (q, r) pair: C_qr[i][l] = phase_r * ( exact (1 - S^f) dG_j/dnu w_l
+//   + S^f (R_s K_s + dx K_r)  [only where S^f > 0]  -  sum_t I_q[i][t] sum_s Phi_off[t][s] P_r[s][l] )
+__global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int* __restrict__ node_idx,
+                       const int* __restrict__ occ_cy, const double* __restrict__ x, const double* __restrict__ f,
+                       const double* __restrict__ f1, const double* __restrict__ f2, const zd* __restrict__ phi,
+                       int dcy_min, int n_dcy, const zd* __restrict__ Iplain, const zd* __restrict__ P,
+                       const int* __restrict__ pq, const int* __restrict__ pr, const int* __restrict__ pw,
+                       const long* __restrict__ poff, const int* __restrict__ pdcx, const double* __restrict__ kress,
+                       const double* __restrict__ binw, zd hk, zd* C) {
+  extern __shared__ unsigned char smem_raw[];
+  zd* Msh = reinterpret_cast<zd*>(smem_raw);
+  const int b = blockIdx.x;
+  const int q = pq[b], r = pr[b], wrap = pw[b];
+  const long off = poff[b];
+  const int qs = cell_start[q], nq = cell_start[q + 1] - qs;
+  const int rs = cell_start[r], nr = cell_start[r + 1] - rs;
+  const int dcx = pdcx[b];
+  const int dcy = occ_cy[r] - occ_cy[q];
+  const int o = (dcx + 1) * n_dcy + (dcy - dcy_min);
+  const zd* ph_o = phi + (long)o * g.nfit * 2 * g.neq;
+  const zd* Pr = P + (long)4 * g.neq * rs;
+  // M[t][l] = sum_s Phi_off[t][s] P_r[lam(t)][s][l]
+  for (int idx = threadIdx.x; idx < g.nfit * nr; idx += blockDim.x) {
+    int t = idx / nr, l = idx % nr;
+    int lam = orient_of_sample(t, g.p);
+    zd acc(0, 0);
+    for (int s = 0; s < 2 * g.neq; ++s) acc += ph_o[t * 2 * g.neq + s] * Pr[((long)lam * 2 * g.neq + s) * nr + l];
+    Msh[idx] = acc;
+  }
+  __syncthreads();
+  const zd wph = expi(g.alpha * g.d * wrap);
+  const double k = g.k;
+  for (int idx = threadIdx.x; idx < nq * nr; idx += blockDim.x) {
+    int il = idx / nr, l = idx % nr;
+    int i = node_idx[qs + il], ls = node_idx[rs + l];
+    double xi = x[i], fi = f[i], f1i = f1[i], si = sqrt(1 + f1i * f1i);
+    double xl = x[ls] + wrap * g.d, fl = f[ls], f1l = f1[ls], sl = sqrt(1 + f1l * f1l);
+    double X = xi - xl, Y = fi - fl;
+    double rr = hypot(X, Y);
+    double Sf = window_S(rr, g.gam, g.a_s);
+    zd val(0, 0);
+    if (i == ls && wrap == 0) {
+      double kr0 = f2[i] / (4 * SGF_PI * (1 + f1i * f1i));
+      val = g.dx * (zd(kr0, 0) + (g.bc == 0 ? hk : -hk));
+    } else {
+      GreenVal gv = green_j(k, g.j, g.h, X, Y, false, false, binw);
+      zd kern = g.bc == 0 ? (f1l * gv.gx - gv.gy) : ((-f1i * gv.gx + gv.gy) * (sl / si));
+      val = ((1.0 - Sf) * g.dx) * kern;
+      long sidx = (long)i - ((long)ls + (long)wrap * g.N);
+      if (Sf > 0 && sidx > -g.Ma && sidx < g.Ma) {
+        double j1r = k * j1(k * rr) / rr;
+        double Ks = g.bc == 0 ? -j1r / (4 * SGF_PI) * (Y - f1l * X) : j1r / (4 * SGF_PI) * (-f1i * X + Y) / si * sl;
+        double sn = sin(SGF_PI * X / (2 * g.a_s));
+        double lg = log(4 * sn * sn);
+        zd Kr = kern - (Ks * lg) * zd(1, 0);
+        double rw = kress[sidx + g.Ma - 1];
+        val += Sf * (zd(rw * Ks, 0) + g.dx * Kr);
+      }
+    }
+    const zd* Ii = Iplain + (long)(qs + il) * g.nfit;
+    zd sub(0, 0);
+    for (int t = 0; t < g.nfit; ++t) sub += Ii[t] * Msh[t * nr + l];
+    C[off + (long)il * nr + l] = wph * (val - sub);
+  }
+}
+
+cudaError_t near_hk(sgf_ctx* c, zd* hk);
+
+cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
+                        const double* d_kress) {
+  GeoArgs g = geo_args(c);
+  int maxnr = 0;
+  for (int q = 0; q < c->n_occ; ++q) maxnr = std::max(maxnr, c->cell_start[q + 1] - c->cell_start[q]);
+  size_t sm = (size_t)c->nfit * maxnr * sizeof(zd);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  cudaFuncSetAttribute(k_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  zd hk(0, 0);
+  cudaError_t e = near_hk(c, &hk);
+  if (e != cudaSuccess) return e;
+  k_near<<<pp.n, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cy, c->d_x, c->d_f, c->d_f1, c->d_f2,
+                                       d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp.q, pp.r, pp.wrap, pp.off, pp.dcx,
+                                       d_kress, c->d_binw, hk, c->d_C);
+  return cudaGetLastError();
+}
+
+__global__ void k_hk(double k, int j, double h, const double* binw, zd* out) {
+  zd acc(0, 0);
+  for (int m = 1; m <= j; ++m) {
+    zd h1 = hankel1(k * m * h);
+    acc += (binw[m] * 0.25 * k) * zd(-h1.im, h1.re);
+  }
+  *out = acc;
+}
+
+cudaError_t near_hk(sgf_ctx* c, zd* hk) {
+  k_hk<<<1, 1, 0, c->stream>>>(c->k, c->prm.j, c->prm.h, c->d_binw, c->d_msum);
+  cudaMemcpyAsync(hk, c->d_msum, sizeof(zd), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return cudaGetLastError();
+}
+
+// ============================================================== modes
+// d_modes_n: per mode [alpha_n, beta_re, beta_im]; MT[i][n] target factors, MS[n][i] source factors.
+__global__ void k_modes(GeoArgs g, int nm, const double* __restrict__ mn, const double* __restrict__ x,
+                        const double* __restrict__ f, const double* __restrict__ f1, zd* MT, zd* MS) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  double s = sqrt(1 + f1[i] * f1[i]);
+  for (int n = 0; n < nm; ++n) {
+    double an = mn[3 * n];
+    zd bn(mn[3 * n + 1], mn[3 * n + 2]);
+    // i (alpha_n x + beta_n f)
+    zd arg = zd(0, an * x[i]) + zd(0, 1) * (f[i] * bn);
+    zd t = cexpz(arg);
+    if (g.bc == 1) t = t * ((zd(0, an * (-f1[i])) + zd(0, 1) * bn) * (1.0 / s));
+    MT[(long)i * nm + n] = t;
+    MS[(long)n * g.N + i] = (s * g.dx) * cexpz(-arg);
+  }
+}
+
+cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n) {
+  if (c->nm == 0) return cudaSuccess;
+  GeoArgs g = geo_args(c);
+  k_modes<<<ceil_div(c->N, 128), 128, 0, c->stream>>>(g, c->nm, d_modes_n, c->d_x, c->d_f, c->d_f1, c->d_MT, c->d_MS);
+  return cudaGetLastError();
+}
+
+// ============================================================== right-hand side
+__global__ void k_rhs(GeoArgs g, double beta, const double* x, const double* f, const double* f1, zd* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  zd u = expi(g.alpha * x[i] - beta * f[i]);
+  if (g.bc == 0) {
+    out[i] = -u;
+  } else {
+    double s = sqrt(1 + f1[i] * f1[i]);
+    out[i] = zd(0, (g.alpha * f1[i] + beta) / s) * u;
+  }
+}
+cudaError_t launch_rhs(sgf_ctx* c, zd* out) {
+  GeoArgs g = geo_args(c);
+  k_rhs<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, c->beta, c->d_x, c->d_f, c->d_f1, out);
+  return cudaGetLastError();
+}
+
+// ============================================================== forward map
+template <typename T>
+__global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restrict__ cell_start,
+                          const int* __restrict__ node_idx, const zd* __restrict__ mu, const cplx<T>* __restrict__ P,
+                          const int* __restrict__ src_gidx, const cplx<T>* __restrict__ src_tw,
+                          cplx<T>* __restrict__ gH, long gH_stride, cplx<T>* __restrict__ gV, long gV_stride,
+                          const zd* __restrict__ MS, zd* __restrict__ msum) {
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  if ((int)blockIdx.x >= n_occ) {
+    // mode sums sum_i MS[n][i] mu_i (FP64)
+    __shared__ zd red[32];
+    int n = blockIdx.x - n_occ;
+    zd acc(0, 0);
+    for (long i = threadIdx.x; i < N; i += blockDim.x) acc += MS[n * N + i] * mu[i];
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      zd v = lane < nw ? red[lane] : zd(0, 0);
+      v = warp_sum(v);
+      if (lane == 0) msum[n] = v;
+    }
+    return;
+  }
+  cplx<T>* mus = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int q = blockIdx.x;
+  const int s0 = cell_start[q], nq = cell_start[q + 1] - s0;
+  for (int l = threadIdx.x; l < nq; l += blockDim.x) mus[l] = cplx<T>(mu[node_idx[s0 + l]]);
+  __syncthreads();
+  const int nout = 4 * neq;
+  const cplx<T>* Pq = P + (long)nout * s0;
+  for (int o = warp; o < nout; o += nw) {
+    const cplx<T>* row = Pq + (long)o * nq;
+    cplx<T> acc(0, 0);
+    for (int l = lane; l < nq; l += 32) acc = fma_c(row[l], mus[l], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      int lam = o / (2 * neq), s = o % (2 * neq);
+      int si = s % neq;
+      long gi = src_gidx[((long)q * 2 + lam) * neq + si];
+      cplx<T> v = acc * src_tw[((long)q * 2 + lam) * neq + si];
+      cplx<T>* base = lam == 0 ? gH + (s < neq ? 0 : gH_stride) : gV + (s < neq ? 0 : gV_stride);
+      atomicAdd(&base[gi].re, v.re);
+      atomicAdd(&base[gi].im, v.im);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, const int* __restrict__ cell_start,
+                              const int* __restrict__ node_idx, const int* __restrict__ samp_gidx, int pH,
+                              const cplx<T>* __restrict__ phiH, const cplx<T>* __restrict__ phiV,
+                              const cplx<T>* __restrict__ Ip, const int* __restrict__ blk_start,
+                              const int* __restrict__ blk_r, const long* __restrict__ blk_off,
+                              const zd* __restrict__ blk_ph, const zd* __restrict__ C, const zd* __restrict__ MT,
+                              const zd* __restrict__ msum, const zd* __restrict__ mu, zd* __restrict__ out) {
+  __shared__ cplx<T> ph[64];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int q = blockIdx.x;
+  const int s0 = cell_start[q], nq = cell_start[q + 1] - s0;
+  for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
+    long gi = samp_gidx[(long)q * nfit + t];
+    ph[t] = t < 2 * (pH + 1) ? phiH[gi] : phiV[gi];
+  }
+  __syncthreads();
+  const int b0 = blk_start[q], b1 = blk_start[q + 1];
+  for (int il = warp; il < nq; il += nw) {
+    const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
+    cplx<T> far(0, 0);
+    for (int t = lane; t < nfit; t += 32) far = fma_c(Ir[t], ph[t], far);
+    far = warp_sum(far);
+    zd acc(0, 0);
+    for (int b = b0; b < b1; ++b) {
+      int r = blk_r[b];
+      int rs = cell_start[r], nr = cell_start[r + 1] - rs;
+      const zd* Cr = C + blk_off[b] + (long)il * nr;
+      zd part(0, 0);
+      for (int l = lane; l < nr; l += 32) part = fma_c(Cr[l], mu[node_idx[rs + l]], part);
+      acc += part;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      int i = node_idx[s0 + il];
+      zd v(0, 0);
+      if (mask & 8) v += half_sigma * mu[i];
+      if (mask & 1) v += zd((double)far.re, (double)far.im);
+      if (mask & 2) v += acc;
+      if (mask & 4)
+        for (int n = 0; n < nm; ++n) v += MT[(long)i * nm + n] * msum[n];
+      out[i] = v;
+    }
+  }
+}
+
+template <typename T, int MAXR>
+static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
+                          const cplx<T>* tw, int twlog, cudaStream_t s) {
+  int threads = o.Py / MAXR;
+  if (threads < 64) threads = 64;
+  if (threads > 1024) return cudaErrorInvalidValue;
+  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  cudaFuncSetAttribute(k_conv_y<T, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_conv_y<T, MAXR><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
+  cudaStream_t s = c->stream;
+  const Orient& oH = c->og[0];
+  const Orient& oV = c->og[1];
+  long szH = (long)oH.Px * oH.nrow, szV = (long)oV.Px * oV.nrow;
+  if (c->profiling) cudaEventRecord(c->ev[0], s);
+  cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(cplx<T>), s);
+  cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(cplx<T>), s);
+  int maxnq = 0;
+  for (int q = 0; q < c->n_occ; ++q) maxnq = std::max(maxnq, c->cell_start[q + 1] - c->cell_start[q]);
+  k_project<T><<<c->n_occ + c->nm, 256, (size_t)maxnq * sizeof(cplx<T>), s>>>(
+      c->n_occ, c->neq, c->nm, c->N, c->d_cell_start, c->d_node_idx, mu, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
+      szH, od.grid[1], szV, c->d_MS, c->d_msum);
+  if (c->profiling) cudaEventRecord(c->ev[1], s);
+  cudaError_t e;
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, s)) != cudaSuccess) return e;
+  }
+  if (c->profiling) cudaEventRecord(c->ev[2], s);
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    long sz = (long)o.Px * o.nrow;
+    if (sizeof(T) == 8)
+      e = conv_y<T, 16>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog, s);
+    else
+      e = conv_y<T, 16>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (c->profiling) cudaEventRecord(c->ev[3], s);
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, s)) != cudaSuccess) return e;
+  }
+  if (c->profiling) cudaEventRecord(c->ev[4], s);
+  double hs = c->bc == 0 ? 0.5 : -0.5;
+  k_interp_near<T><<<c->n_occ, 256, 0, s>>>(c->debug_mask, c->nfit, c->nm, hs, c->d_cell_start, c->d_node_idx, c->d_samp_gidx,
+                                            c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_blk_start, c->d_blk_r,
+                                            c->d_blk_off, c->d_blk_ph, c->d_C, c->d_MT, c->d_msum, mu, out);
+  if (c->profiling) cudaEventRecord(c->ev[5], s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<double>(c, c->o64, mu, out); }
+cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<float>(c, c->o32, mu, out); }
+
+// ============================================================== Rayleigh coefficients
+// Block per mode: B_n = dx sum_i mu_i e^{-i(alpha_n x_i + beta_n f_i)} W_i (eq. rayexp with the
+// Y > 0 spectral form of G~ and M^eta); mp[n] = [alpha_n, beta_re, beta_im, Q_re, Q_im, indicator].
+__global__ void k_rayleigh(GeoArgs g, const double* __restrict__ mp, const double* __restrict__ x,
+                           const double* __restrict__ f, const double* __restrict__ f1, const zd* __restrict__ mu,
+                           zd* B) {
+  __shared__ zd red[32];
+  const int n = blockIdx.x;
+  const double an = mp[6 * n];
+  const zd bn(mp[6 * n + 1], mp[6 * n + 2]), Q(mp[6 * n + 3], mp[6 * n + 4]);
+  const double ind = mp[6 * n + 5];
+  zd acc(0, 0);
+  for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+    double s = sqrt(1 + f1[i] * f1[i]);
+    zd e = cexpz(-(zd(0, an * x[i]) + zd(0, 1) * (f[i] * bn)));
+    zd W = g.bc == 0 ? (bn - zd(an * f1[i], 0)) * Q * (0.5 / g.d) + zd(s * ind, 0)
+                     : s * (zd(0, 0.5 / g.d) * Q + zd(ind, 0));
+    acc += mu[i] * e * W;
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  acc = warp_sum(acc);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    zd v = lane < nw ? red[lane] : zd(0, 0);
+    v = warp_sum(v);
+    if (lane == 0) B[n] = g.dx * v;
+  }
+}
+
+cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B) {
+  GeoArgs g = geo_args(c);
+  k_rayleigh<<<nmodes, 256, 0, c->stream>>>(g, d_mp, c->d_x, c->d_f, c->d_f1, mu, d_B);
+  return cudaGetLastError();
+}
+
+// ============================================================== Krylov helpers (FP64)
+// partial[j][blk] = sum_{i in chunk blk} conj(V[j][i]) w[i]; then out[j] = sum_blk partial.
+__global__ void k_dots_partial(const zd* __restrict__ V, long ldv, const zd* __restrict__ w, long n, zd* partial,
+                               int nblk) {
+  __shared__ zd red[32];
+  const int j = blockIdx.y, blk = blockIdx.x;
+  long chunk = (n + nblk - 1) / nblk;
+  long i0 = blk * chunk, i1 = min(n, i0 + chunk);
+  const zd* v = V + j * ldv;
+  zd acc(0, 0);
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += mulc(w[i], v[i]);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  acc = warp_sum(acc);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    zd s = lane < nw ? red[lane] : zd(0, 0);
+    s = warp_sum(s);
+    if (lane == 0) partial[(long)j * nblk + blk] = s;
+  }
+}
+__global__ void k_dots_final(const zd* partial, int nblk, int m, zd* out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  zd s(0, 0);
+  for (int b = 0; b < nblk; ++b) s += partial[(long)j * nblk + b];
+  out[j] = s;
+}
+cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,
+                        cudaStream_t s) {
+  dim3 g(nblk, m);
+  k_dots_partial<<<g, 256, 0, s>>>(V, ldv, w, n, partial, nblk);
+  k_dots_final<<<ceil_div(m, 128), 128, 0, s>>>(partial, nblk, m, out);
+  return cudaGetLastError();
+}
+__global__ void k_update(zd* w, const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ h, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  zd acc = w[i];
+  for (int j = 0; j < m; ++j) acc -= V[j * ldv + i] * h[j];
+  w[i] = acc;
+}
+cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s) {
+  k_update<<<ceil_div(n, 256), 256, 0, s>>>(w, V, m, ldv, h, n);
+  return cudaGetLastError();
+}
+__global__ void k_axpby(zd* y, zd a, const zd* x, zd b, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s) {
+  k_axpby<<<ceil_div(n, 256), 256, 0, s>>>(y, a, x, b, n);
+  return cudaGetLastError();
+}

@@ -15,7 +15,8 @@ Parameter rules (readings of the paper where it prints no value):
     pole m h (1 <= m <= j) then stays at least dg/(j+1) away from a lag of the equivalent-source
     grids (Section 3.1 poles P_j); a half-integer offset would put 2h, 4h, ... on the grid;
   * spectral/spatial switch distance delta_min = d/64 (Section 3.2, estimate of the spectral decay);
-  * eta = 1e-3 for the mode completion M^eta (Section 3.1).
+  * eta = 1e-3 for the mode completion M^eta (Section 3.1);
+  * ls_reg = 1e-6: Tikhonov weight (relative to |A|_F) of the equivalent-source least squares.
 """
 from __future__ import annotations
 
@@ -84,7 +85,7 @@ def harmonic_surface(d, n_harm, scale, seed):
 
 def make_params(prof, k, theta_deg, bc, N, *, j=8, h0=0.5, n_per=40, nx, ny=None, hmin=None,
                 p=8, e=1, n_coll=200, n_fb=12, eta=1e-3, delta_min=None, spec_exp=40.0,
-                c_win=0.5, precision=64):
+                c_win=0.5, precision=64, ls_reg=1e-6):
     """Assemble the full parameter record of one scattering problem."""
     d = prof["d"]
     dx = d / N
@@ -112,6 +113,7 @@ def make_params(prof, k, theta_deg, bc, N, *, j=8, h0=0.5, n_per=40, nx, ny=None
         "nx": int(nx), "ny": int(ny), "L": float(L), "hmin": float(hmin),
         "p": int(p), "e": int(e), "n_coll": int(n_coll), "n_fb": int(n_fb),
         "delta_min": float(delta_min), "spec_exp": float(spec_exp), "precision": int(precision),
+        "ls_reg": float(ls_reg),
     }
 
 

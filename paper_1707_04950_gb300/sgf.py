@@ -1,0 +1,222 @@
+"""ctypes binding of the sgf C ABI (include/sgf.h): argument marshalling only.
+
+Every function keeps the C name. Device buffers are passed as integer addresses (for example
+`tensor.data_ptr()` of a torch complex128 CUDA tensor); host buffers as numpy arrays. The binding
+raises SgfError on any non-zero status and never falls back to another implementation: if the
+library is not built, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsgf.so")
+
+STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_ON_GRID", 4: "SGF_EWINDOW",
+          5: "SGF_ENOCONV", 6: "SGF_EBREAKDOWN", 7: "SGF_ENONFINITE", 8: "SGF_ETIMEOUT", 9: "SGF_ECUDA",
+          10: "SGF_ESTATE"}
+
+EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
+            "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve",
+            "sgf_rayleigh", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table"]
+
+
+class SgfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sgf_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("j", ctypes.c_int), ("h", ctypes.c_double), ("n_per", ctypes.c_int),
+                ("c_win", ctypes.c_double), ("Ma", ctypes.c_int), ("eta", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("hmin", ctypes.c_double), ("p", ctypes.c_int),
+                ("e", ctypes.c_int), ("n_coll", ctypes.c_int), ("n_fb", ctypes.c_int),
+                ("delta_min", ctypes.c_double), ("spec_exp", ctypes.c_double), ("precision", ctypes.c_int),
+                ("ls_reg", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libsgf.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"sgf library not built: {LIB_PATH} (run python -m paper_1707_04950_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "sgf_create": [ctypes.POINTER(vp), i, vp],
+        "sgf_set_profile_fourier": [vp, d, i, dp, dp],
+        "sgf_set_wave": [vp, d, d, i],
+        "sgf_set_params": [vp, ctypes.POINTER(sgf_params)],
+        "sgf_build_operator": [vp],
+        "sgf_apply": [vp, vp, vp, i, i],
+        "sgf_apply_host": [vp, vp, vp, i],
+        "sgf_rhs": [vp, vp],
+        "sgf_solve": [vp, d, i, vp, ctypes.POINTER(i), dp],
+        "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
+        "sgf_info": [vp, dp],
+        "sgf_set_profiling": [vp, i],
+        "sgf_stage_times": [vp, dp],
+        "sgf_debug_mask": [vp, i],
+        "sgf_debug_table": [vp, i, i, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.sgf_destroy.argtypes = [vp]
+    lib.sgf_destroy.restype = None
+    lib.sgf_last_error.argtypes = [vp]
+    lib.sgf_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st):
+    if st != 0:
+        msg = load().sgf_last_error(ctx)
+        raise SgfError(st, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def sgf_create(device=0, stream=0):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    st = lib.sgf_create(ctypes.byref(ctx), int(device), ctypes.c_void_p(stream or None))
+    _check(ctx, st)
+    return ctx
+
+
+def sgf_destroy(ctx):
+    load().sgf_destroy(ctx)
+
+
+def sgf_set_profile_fourier(ctx, d, a, b):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert a.shape == b.shape
+    _check(ctx, load().sgf_set_profile_fourier(ctx, float(d), len(a) - 1, _dptr(a), _dptr(b)))
+
+
+def sgf_set_wave(ctx, k, theta, bc):
+    _check(ctx, load().sgf_set_wave(ctx, float(k), float(theta), int(bc)))
+
+
+def sgf_set_params(ctx, p: sgf_params):
+    _check(ctx, load().sgf_set_params(ctx, ctypes.byref(p)))
+
+
+def sgf_build_operator(ctx):
+    _check(ctx, load().sgf_build_operator(ctx))
+
+
+def sgf_apply(ctx, mu_ptr, out_ptr, nrhs=1, transpose_conj=0):
+    _check(ctx, load().sgf_apply(ctx, ctypes.c_void_p(mu_ptr), ctypes.c_void_p(out_ptr), int(nrhs), int(transpose_conj)))
+
+
+def sgf_apply_host(ctx, mu, out, nrhs=1):
+    assert mu.dtype == np.complex128 and out.dtype == np.complex128
+    assert mu.flags.c_contiguous and out.flags.c_contiguous
+    _check(ctx, load().sgf_apply_host(ctx, mu.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                      int(nrhs)))
+
+
+def sgf_rhs(ctx, out_ptr):
+    _check(ctx, load().sgf_rhs(ctx, ctypes.c_void_p(out_ptr)))
+
+
+def sgf_solve(ctx, tol, maxit, mu_ptr):
+    its = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = load().sgf_solve(ctx, float(tol), int(maxit), ctypes.c_void_p(mu_ptr), ctypes.byref(its), ctypes.byref(rr))
+    return st, its.value, rr.value
+
+
+def sgf_rayleigh(ctx, mu_ptr, n_lo, n_hi):
+    n = n_hi - n_lo + 1
+    B = np.zeros(2 * n)
+    eff = np.zeros(n)
+    err = np.zeros(1)
+    _check(ctx, load().sgf_rayleigh(ctx, ctypes.c_void_p(mu_ptr), int(n_lo), int(n_hi), _dptr(B), _dptr(eff), _dptr(err)))
+    return B[0::2] + 1j * B[1::2], eff, float(err[0])
+
+
+INFO_KEYS = ["N", "n_occ", "nnz", "PxH", "nrowH", "PyH", "PxV", "nrowV", "PyV", "neq", "nfit", "nb", "nm",
+             "bytes64", "bytes32", "launches"]
+
+
+def sgf_info(ctx):
+    v = np.zeros(16)
+    _check(ctx, load().sgf_info(ctx, _dptr(v)))
+    return dict(zip(INFO_KEYS, v.tolist()))
+
+
+def sgf_set_profiling(ctx, on):
+    _check(ctx, load().sgf_set_profiling(ctx, int(on)))
+
+
+def sgf_stage_times(ctx):
+    v = np.zeros(8)
+    _check(ctx, load().sgf_stage_times(ctx, _dptr(v)))
+    return v
+
+
+def sgf_debug_mask(ctx, mask):
+    _check(ctx, load().sgf_debug_mask(ctx, int(mask)))
+
+
+def sgf_debug_table(ctx, lam, kind, shape):
+    out = np.zeros(shape, dtype=np.complex128)
+    _check(ctx, load().sgf_debug_table(ctx, int(lam), int(kind), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+# ------------------------------------------------------------------ convenience
+def params_from(par, precision=None) -> sgf_params:
+    """C parameter record from a workload dictionary (paper_1707_04950_gb300.inputs)."""
+    return sgf_params(N=par["N"], j=par["j"], h=par["h"], n_per=par["n_per"], c_win=par["c_win"], Ma=par["Ma"],
+                      eta=par["eta"], nx=par["nx"], ny=par["ny"], hmin=par["hmin"], p=par["p"], e=par["e"],
+                      n_coll=par["n_coll"], n_fb=par["n_fb"], delta_min=par["delta_min"],
+                      spec_exp=par["spec_exp"], precision=int(precision or par["precision"]),
+                      ls_reg=par["ls_reg"])
+
+
+class Operator:
+    """One built operator: sgf_create + setters + sgf_build_operator on a workload dictionary."""
+
+    def __init__(self, par, device=0, stream=0, precision=None):
+        self.par = par
+        self.ctx = sgf_create(device, stream)
+        try:
+            sgf_set_profile_fourier(self.ctx, par["d"], par["a"], par["b"])
+            sgf_set_wave(self.ctx, par["k"], par["theta"], par["bc"])
+            sgf_set_params(self.ctx, params_from(par, precision))
+            sgf_build_operator(self.ctx)
+        except Exception:
+            sgf_destroy(self.ctx)
+            self.ctx = None
+            raise
+        self.info = sgf_info(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            sgf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
