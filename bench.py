@@ -1,0 +1,317 @@
+"""Benchmark: FFT-accelerated shifted-Green matvecs/s at N = 16384 (deep corrugation, TM/Neumann,
+period 10 wavelengths, depth/period 2, 128 x 257 cells), mixed precision (FP32 complex
+projection/FFT/interpolation, FP64 near field) beside the FP64 path.
+
+One step = one application of the accelerated operator (Algorithm 3) to one density vector,
+inputs resident on the device. L2 is flushed (256 MiB write) before every timed step; each step is
+timed with CUDA events on the stream the library launches on, the flush outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank builds its own replica (independent problems, no collective) and the
+slowest rank's time is reported. `--impl reference` times the CPU oracle (the exact operator rows,
+matrix-free) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1707_04950_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "deep_corrugation_tm_d10_depth20_n16384_cells128x257"
+METRIC = "FFT-accel shifted-Green matvecs/s at N=16384; mixed vs FP64 at 1e-6 rel err"
+
+
+def workload():
+    return inputs.wl_deep_corrugation_neumann(N=16384, nx=128)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def stage_bytes(info, s):
+    """Algorithmic bytes per launch group of the forward map for far-field complex size s (8 or 16)."""
+    N, nnz, neq, nfit = info["N"], info["nnz"], info["neq"], info["nfit"]
+    gH, gV = info["PxH"] * info["nrowH"], info["PxV"] * info["nrowV"]
+    kH, kV = info["PxH"] * info["PyH"], info["PxV"] * info["PyV"]
+    return {
+        "project": s * 4 * neq * N + 16 * N + s * 2 * (gH + gV) * 2,
+        "fft_x": s * 2 * 2 * (gH + gV),
+        "conv_y": s * ((2 * gH + 2 * kH + gH) + (2 * gV + 2 * kV + gV)),
+        "ifft_x": s * 2 * (gH + gV),
+        "interp_near": s * nfit * N + 16 * nnz + s * info["n_occ"] * nfit + 32 * N,
+    }
+
+
+STAGES = ["project", "fft_x", "conv_y", "ifft_x", "interp_near"]
+LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "interp_near": 1}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1707_04950_gb300 import sgf
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    par = workload()
+    stream = torch.cuda.current_stream(dev)
+    mu_h = inputs.random_density(par["N"], 7 + rank)
+    mu = torch.from_numpy(mu_h).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    ops = {}
+    for prec in (64, 32):
+        op = sgf.Operator(par, device=local, stream=stream.cuda_stream, precision=prec)
+        ops[prec] = op
+        out = torch.empty_like(mu)
+        for _ in range(args.warmup):
+            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = Clocks(local)
+        if prec == 32:
+            clocks.start()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ck = clocks.stop() if prec == 32 else None
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        # stage times of the same launches (event pairs between stages), averaged over steps
+        sgf.sgf_set_profiling(op.ctx, 1)
+        st = np.zeros(8)
+        nprof = max(3, min(args.steps, 20))
+        for _ in range(nprof):
+            flush.zero_()
+            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+            st += sgf.sgf_stage_times(op.ctx)
+        sgf.sgf_set_profiling(op.ctx, 0)
+        st /= nprof
+        res[prec] = {"ms": ms, "stages_ms": dict(zip(STAGES, st[:5].tolist())), "clocks": ck,
+                     "out": out.clone(), "info": op.info}
+    # accuracy of the mixed path against the FP64 path on the benchmark input
+    y64, y32 = res[64]["out"], res[32]["out"]
+    mixed_err = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    op32 = ops[32]
+    mu_pin = torch.from_numpy(mu_h).pin_memory()
+    y_pin = torch.empty_like(mu_pin).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        sgf.sgf_apply_host_ptr(op32.ctx, mu_pin.data_ptr(), y_pin.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sgf.sgf_apply_host_ptr(op32.ctx, mu_pin.data_ptr(), y_pin.data_ptr())
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    for op in ops.values():
+        op.close()
+
+    ms32 = res[32]["ms"]
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms32, res[64]["ms"], e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32, ms64, e2e_s = t.tolist()
+    else:
+        ms64 = res[64]["ms"]
+    if rank != 0:
+        return
+    info = res[32]["info"]
+    # roofline of the dominant stage of the headline (mixed) path
+    hbm, kind = peaks()
+    sb = stage_bytes(info, 8)
+    stg = res[32]["stages_ms"]
+    dom = max(STAGES, key=lambda k: stg[k])
+    per_launch_ms = stg[dom] / LAUNCHES[dom]
+    ach = sb[dom] / LAUNCHES[dom] / (per_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": ws * 1000.0 / ms32,
+        "unit": "matvecs/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms32,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 far field (projection, FFT, interpolation) + c128 near field",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 16384, "cells": "128x257", "k": "2pi", "theta_deg": 45,
+                   "bc": "neumann", "shifts_j": 8, "n_per": 40, "eq_sources_per_orientation": int(info["neq"]),
+                   "fft_grids": f"H {int(info['PxH'])}x{int(info['PyH'])}, V {int(info['PxV'])}x{int(info['PyV'])}",
+                   "near_field_entries": int(info["nnz"]), "l2": "flushed (256 MiB write) before each timed step",
+                   "parallelism": f"replicas x{ws}"},
+        "fp64": {"value": ws * 1000.0 / ms64, "unit": "matvecs/s", "ms_per_step": ms64,
+                 "stages_ms": res[64]["stages_ms"]},
+        "mixed_rel_err_vs_fp64": mixed_err,
+        "stages_ms": stg,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "traffic": None, "peak_kind": kind,
+                     "algorithmic_bytes_per_launch": sb[dom] / LAUNCHES[dom]},
+        "e2e": {"value": ws / e2e_s, "unit": "matvecs/s", "h2d_bytes_per_step": 16 * 16384,
+                "d2h_bytes_per_step": 16 * 16384},
+        "gpu_launches": 8 * args.steps,
+        "clocks": res[32]["clocks"],
+    }
+    if not args.no_cpu_baseline and ws >= 1:
+        line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(rows=6):
+    """The CPU oracle (exact operator, matrix-free rows) on `rows` rows of the same workload; the
+    row rate is scaled to full matvecs (N rows each)."""
+    from oracle import direct
+
+    par = workload()
+    mu = inputs.random_density(par["N"], 7)
+    idx = np.linspace(0, par["N"] - 1, rows).astype(int)
+    t0 = time.perf_counter()
+    direct.apply_rows(par, mu, idx)
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt / par["N"], "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} rows of the exact operator (matrix-free, hybrid G~ per pair) at N=16384, "
+                      f"{dt:.1f} s, scaled by rows/N"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: every step evaluates one row of the exact operator
+    (matrix-free) of the benchmark workload; the row rate is scaled to matvecs (N rows)."""
+    from oracle import direct
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    par = workload()
+    mu = inputs.random_density(par["N"], 7)
+    rng = np.random.default_rng(0)
+    steps = min(args.steps, 60)
+    for _ in range(args.warmup):
+        direct.apply_rows(par, mu, [int(rng.integers(par["N"]))])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        direct.apply_rows(par, mu, [int(rng.integers(par["N"]))])
+    dt = time.perf_counter() - t0
+    v = steps / dt / par["N"]
+    sample = f"{steps} single rows of the exact operator at N=16384 in {dt:.1f} s, scaled by rows/N"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "matvecs/s", "n_gpus": ws,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 16384, "cells": "128x257", "parallelism": "cpu oracle, 1 core"},
+            "cpu_baseline": {"value": v, "unit": "matvecs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        args.warmup = 1
+        run_reference(args)
+    else:
+        from paper_1707_04950_gb300 import build
+
+        build.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -139,33 +139,32 @@ def apply_rows(par, mu, rows):
     """Rows `rows` of (sigma/2 I + D^dx) mu of the exact system, without assembling the matrix."""
     rows = np.asarray(rows)
     y = reg_matrix(par, rows) @ mu
-    r, c, v = sing_triplets(par)
+    r, c, v = sing_triplets(par, rows)
     pos = {int(t): n for n, t in enumerate(rows)}
-    for rr, cc, vv in zip(r, c, v):
-        if int(rr) in pos:
-            y[pos[int(rr)]] += vv * mu[cc]
+    np.add.at(y, np.array([pos[int(t)] for t in r]), v * mu[c])
     T, S = modes_factors(par)
     y += T[rows] @ (S @ mu)
     sigma = 0.5 if par["bc"] == 0 else -0.5
     return y + sigma * mu[rows]
 
 
-def sing_triplets(par):
-    """D~_sing (eq. local_mat) as (rows, cols, values) triplets; columns wrapped by
-    quasi-periodicity mu_{l+N} = e^{i alpha d} mu_l (eq. quasiper_disc)."""
+def sing_triplets(par, rows=None):
+    """D~_sing (eq. local_mat) as (rows, cols, values) triplets for all target rows (or the given
+    ones); columns wrapped by quasi-periodicity mu_{l+N} = e^{i alpha d} mu_l (eq. quasiper_disc)."""
     N, d, k, j, h = par["N"], par["d"], par["k"], par["j"], par["h"]
     dx = d / N
     al, _ = wave(par)
     x, f, f1, f2 = nodes(par)
     s = np.sqrt(1 + f1 * f1)
+    ii = np.arange(N) if rows is None else np.asarray(rows)
+    x, f, f1, f2, s = x[ii], f[ii], f1[ii], f2[ii], s[ii]
     a_s, gam = par["a_s"], par["gamma"]
     M = par["Ma"]
     ss, rw = kress_weights(M, dx)
     w = gr.binom_weights(j)
     hk = sum(w[m] * 0.25j * k * sp.hankel1(1, k * m * h) for m in range(1, j + 1))
-    rows, cols, vals = [], [], []
+    out_r, cols, vals = [], [], []
     for si, rs in zip(ss, rw):
-        ii = np.arange(N)
         ll = ii - si                      # unwrapped source index (0-based)
         lw = np.mod(ll, N)
         wrap = np.floor_divide(ll, N)
@@ -191,10 +190,10 @@ def sing_triplets(par):
             lg = np.log(4 * np.sin(math.pi * Xs / (2 * a_s)) ** 2)
             kr = kern - ks * lg
             val = (rs * ks + dx * kr) * sf
-        rows.append(ii)
+        out_r.append(ii)
         cols.append(lw)
         vals.append(val * ph)
-    return np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    return np.concatenate(out_r), np.concatenate(cols), np.concatenate(vals)
 
 
 def modes_factors(par):

@@ -43,7 +43,8 @@ __device__ inline cplx<T> warp_sum(cplx<T> v) {
 // J_n(x) e^{i n th} for any integer n (J_{-n} = (-1)^n J_n)
 __device__ inline zd fb_Z(int n, double kr, double th) {
   int an = n < 0 ? -n : n;
-  double J = jn(an, kr);
+  // J_n(0) = delta_{n0}; evaluated explicitly (a node can sit exactly at a cell centre)
+  double J = kr > 0 ? jn(an, kr) : (an == 0 ? 1.0 : 0.0);
   if (n < 0 && (an & 1)) J = -J;
   zd e = expi(n * th);
   return J * e;

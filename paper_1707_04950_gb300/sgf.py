@@ -133,6 +133,11 @@ def sgf_apply_host(ctx, mu, out, nrhs=1):
                                       int(nrhs)))
 
 
+def sgf_apply_host_ptr(ctx, mu_host_ptr, out_host_ptr, nrhs=1):
+    """sgf_apply_host on raw host addresses (e.g. pinned torch CPU tensors)."""
+    _check(ctx, load().sgf_apply_host(ctx, ctypes.c_void_p(mu_host_ptr), ctypes.c_void_p(out_host_ptr), int(nrhs)))
+
+
 def sgf_rhs(ctx, out_ptr):
     _check(ctx, load().sgf_rhs(ctx, ctypes.c_void_p(out_ptr)))
 

@@ -98,8 +98,11 @@ def test_apply_fp64_matches_oracle(name):
     modes = _apply(op, mu, 4)
     far_ref = _far_oracle(acc, st)
     near_ref = st["reg"] - far_ref + st["sing"]
-    e_far, e_near, e_mod = _rel(far, far_ref), _rel(near, near_ref), (
-        _rel(modes, st["modes"]) if np.linalg.norm(st["modes"]) > 0 else float(np.linalg.norm(modes)))
+    # stage errors on the scale of the full output (the near and mode terms are small parts of it;
+    # at a Wood anomaly beta_n of the grazing mode is the square root of a rounding-level number)
+    scale = np.linalg.norm(y_ref)
+    e_far, e_near, e_mod = (np.linalg.norm(far - far_ref) / scale, np.linalg.norm(near - near_ref) / scale,
+                            np.linalg.norm(modes - st["modes"]) / scale)
     op.close()
     assert e_far < 1e-10, f"far {e_far:.3e}"
     assert e_near < 1e-10, f"near {e_near:.3e}"
