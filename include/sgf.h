@@ -106,6 +106,22 @@ sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* ite
 sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                         double* energy_err);
 
+/* Same result as sgf_rayleigh, for callers that cannot allocate memory during the call: code running
+ * while a stream is being captured into a CUDA graph (cudaMalloc cannot be captured), processes
+ * working inside a device-memory budget fixed up front, real-time loops that must stay out of the
+ * allocator. (The paper has no counterpart; this is a property of the library, not of the method.)
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch (per-mode data and the
+ * B_n before they are copied back) lives in a static device array of 1024 modes x 64 bytes that
+ * every GPU loading the library holds until the process exits. At most 1024 modes
+ * (n_hi - n_lo + 1) per call; larger ranges return SGF_EINVAL with a message. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device current), so
+ * make that first call before any stream capture starts. All calls share the one array, which keeps
+ * the last call's contents; every entry a call reads is written by that call first. Calls whose GPU
+ * work overlaps (other streams, other host threads on the same device) race on the array: serialise
+ * them. Synchronises the context stream. */
+sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
+                                double* energy_err);
+
 /* Introspection: fills host info[0..15] with N, number of occupied cells, near-field entries,
  * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
  * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec. */

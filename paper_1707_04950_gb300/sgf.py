@@ -21,7 +21,7 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve",
-            "sgf_rayleigh", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table"]
+            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table"]
 
 
 class SgfError(RuntimeError):
@@ -62,6 +62,7 @@ def load():
         "sgf_rhs": [vp, vp],
         "sgf_solve": [vp, d, i, vp, ctypes.POINTER(i), dp],
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
+        "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
         "sgf_info": [vp, dp],
         "sgf_set_profiling": [vp, i],
         "sgf_stage_times": [vp, dp],
@@ -155,6 +156,17 @@ def sgf_rayleigh(ctx, mu_ptr, n_lo, n_hi):
     eff = np.zeros(n)
     err = np.zeros(1)
     _check(ctx, load().sgf_rayleigh(ctx, ctypes.c_void_p(mu_ptr), int(n_lo), int(n_hi), _dptr(B), _dptr(eff), _dptr(err)))
+    return B[0::2] + 1j * B[1::2], eff, float(err[0])
+
+
+def sgf_rayleigh_noalloc(ctx, mu_ptr, n_lo, n_hi):
+    """sgf_rayleigh without allocation (static device scratch, at most 1024 modes per call)."""
+    n = n_hi - n_lo + 1
+    B = np.zeros(2 * n)
+    eff = np.zeros(n)
+    err = np.zeros(1)
+    _check(ctx, load().sgf_rayleigh_noalloc(ctx, ctypes.c_void_p(mu_ptr), int(n_lo), int(n_hi), _dptr(B), _dptr(eff),
+                                            _dptr(err)))
     return B[0::2] + 1j * B[1::2], eff, float(err[0])
 
 
