@@ -122,9 +122,11 @@ sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, do
 sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                                 double* energy_err);
 
-/* Introspection: fills host info[0..15] with N, number of occupied cells, near-field entries,
+/* Introspection: fills host info[0..19] with N, number of occupied cells, near-field entries,
  * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
- * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec. */
+ * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec,
+ * 1 if applications run as captured CUDA graphs, the longest near-field row, the largest cell node
+ * count, log2 of the twiddle table length. */
 sgf_status sgf_info(const sgf_ctx* ctx, double* info);
 
 /* Device time of the stages of the last sgf_apply when profiling is switched on with

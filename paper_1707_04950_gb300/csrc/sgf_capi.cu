@@ -47,6 +47,7 @@ static sgf_status dalloc(sgf_ctx* ctx, T** p, size_t count) {
   } while (0)
 
 static void free_all(sgf_ctx* ctx) {
+  destroy_graphs(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->o64 = OpData<double>();
@@ -80,6 +81,9 @@ sgf_status sgf_create(sgf_ctx** out, int device, void* cuda_stream) {
     return SGF_ECUDA;
   }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&ctx->ev[i]);
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) ctx->side = nullptr;
+  cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
   *out = ctx;
   return SGF_OK;
 }
@@ -91,6 +95,12 @@ void sgf_destroy(sgf_ctx* ctx) {
   free_all(ctx);
   for (int i = 0; i < 8; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
 }
 
@@ -262,7 +272,8 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     c->og[l].Py = 1 << c->og[l].logPy;
   }
   c->twlog = std::max(std::max(H.logPx, V.logPx), std::max(H.logPy, V.logPy));
-  if (V.Py > 16384 || H.Px > 8192) return set_err(ctx, SGF_EINVAL, "FFT length above the shared-memory limit");
+  if (V.Py > 16384 || H.Py > 16384 || H.Px > 4096 || V.Px > 4096)
+    return set_err(ctx, SGF_EINVAL, "FFT length above the shared-memory limit");
   // shifted poles must stay off the finest grid lag (0, -m h)
   for (int m = 1; m <= P.j; ++m) {
     double r = m * P.h / V.dyg;
@@ -331,7 +342,29 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     for (int i : members[q]) { c->node_idx.push_back(i); node_cell.push_back(q); }
     maxnq = std::max(maxnq, (int)members[q].size());
   }
+  c->maxnq = maxnq;
   c->cell_start[c->n_occ] = c->N;
+  {  // work items: chunks of at most 32 nodes of one cell (balances the per-cell kernels)
+    std::vector<int> ic, il, ih;
+    for (int q = 0; q < c->n_occ; ++q) {
+      int nq = c->cell_start[q + 1] - c->cell_start[q];
+      for (int lo = 0; lo < nq; lo += 32) {
+        ic.push_back(q);
+        il.push_back(lo);
+        ih.push_back(std::min(nq, lo + 32));
+      }
+    }
+    c->n_items = (int)ic.size();
+    long covered = 0;
+    for (size_t t = 0; t < ic.size(); ++t) covered += ih[t] - il[t];
+    if (covered != c->N) return set_err(ctx, SGF_EINVAL, "internal: work items cover %ld of %d nodes", covered, c->N);
+    TRY(dalloc(ctx, &c->d_item_cell, ic.size()));
+    TRY(dalloc(ctx, &c->d_item_lo, il.size()));
+    TRY(dalloc(ctx, &c->d_item_hi, ih.size()));
+    CU(cudaMemcpy(c->d_item_cell, ic.data(), ic.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_item_lo, il.data(), il.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_item_hi, ih.data(), ih.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   if ((size_t)c->nfit * maxnq * sizeof(zd) > 200 * 1024)
     return set_err(ctx, SGF_EINVAL, "too many nodes (%d) in one cell for the near-field kernel", maxnq);
   TRY(dalloc(ctx, &c->d_cell_start, c->n_occ + 1));
@@ -434,9 +467,9 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(launch_build_I(c, d_pinv_fb, d_Iplain, d_samp_rel));
 
   // ---------------- kernel tables and spectra
-  TRY(dalloc(ctx, &c->o64.tw, (size_t)1 << (c->twlog - 1)));
+  TRY(dalloc(ctx, &c->o64.tw, (size_t)1 << c->twlog));
   bool mixed = P.precision == 32;
-  if (mixed) TRY(dalloc(ctx, &c->o32.tw, (size_t)1 << (c->twlog - 1)));
+  if (mixed) TRY(dalloc(ctx, &c->o32.tw, (size_t)1 << c->twlog));
   CU(launch_twiddles(c));
   for (int lam = 0; lam < 2; ++lam) {
     long n = (long)c->og[lam].Px * c->og[lam].Py;
@@ -450,17 +483,22 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(launch_tables(c));
 
   // ---------------- local sets L(q) and the near-field block list
-  std::vector<int> pq, pr, pw, pdcx;
-  std::vector<long> poff;
-  std::vector<int> blk_start(c->n_occ + 1, 0);
+  // Values of cell q form one row-major n_q x W_q block (W_q = sum of n_r over its local cells, in
+  // block order), so each target row is one contiguous stream.
+  std::vector<int> pq, pr, pw, pdcx, pld, bcol;
+  std::vector<long> poff, cell_off(c->n_occ + 1, 0);
+  std::vector<int> blk_start(c->n_occ + 1, 0), cellW(c->n_occ, 0);
   std::vector<std::set<int>> rowsS(P.ny);
   for (int cy = 0; cy < P.ny; ++cy) rowsS[cy] = rows_of_Sj(cy, P.j, P.h, c->L);
   long off = 0;
   int dcy_min = 1 << 30, dcy_max = -(1 << 30);
+  int maxW = 0;
   for (int q = 0; q < c->n_occ; ++q) {
     blk_start[q] = (int)pq.size();
+    cell_off[q] = off;
     int cxq = c->occ_cx[q], cyq = c->occ_cy[q];
     int nq = c->cell_start[q + 1] - c->cell_start[q];
+    int W = 0;
     for (int dcx = -1; dcx <= 1; ++dcx) {
       int cxr = cxq + dcx;
       int ref = ((cxr % P.nx) + P.nx) % P.nx;
@@ -470,16 +508,28 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
         if (r < 0) continue;
         if (!rowsS[cyr].count(cyq)) continue;
         int nr = c->cell_start[r + 1] - c->cell_start[r];
-        pq.push_back(q); pr.push_back(r); pw.push_back(wrap); pdcx.push_back(dcx); poff.push_back(off);
-        off += (long)nq * nr;
+        pq.push_back(q); pr.push_back(r); pw.push_back(wrap); pdcx.push_back(dcx);
+        bcol.push_back(W);
+        W += nr;
         dcy_min = std::min(dcy_min, cyr - cyq);
         dcy_max = std::max(dcy_max, cyr - cyq);
       }
     }
+    for (int b = blk_start[q]; b < (int)pq.size(); ++b) {
+      poff.push_back(off + bcol[b]);
+      pld.push_back(W);
+    }
+    cellW[q] = W;
+    maxW = std::max(maxW, W);
+    off += (long)nq * W;
   }
+  cell_off[c->n_occ] = off;
   blk_start[c->n_occ] = (int)pq.size();
   c->n_blk = (int)pq.size();
   c->nnz = off;
+  c->maxW = maxW;
+  if ((size_t)maxW * sizeof(zd) > 200 * 1024)
+    return set_err(ctx, SGF_EINVAL, "local set of %d nodes too large for the near-field kernel", maxW);
   int n_dcy = dcy_max - dcy_min + 1;
   NearPairs pp;
   pp.n = c->n_blk;
@@ -487,16 +537,39 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   TRY(dalloc(ctx, &pp.r, pp.n));
   TRY(dalloc(ctx, &pp.wrap, pp.n));
   TRY(dalloc(ctx, &pp.dcx, pp.n));
+  TRY(dalloc(ctx, &pp.ld, pp.n));
   TRY(dalloc(ctx, &pp.off, pp.n));
   CU(cudaMemcpy(pp.q, pq.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(pp.r, pr.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(pp.wrap, pw.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(pp.dcx, pdcx.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(pp.ld, pld.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMemcpy(pp.off, poff.data(), pp.n * sizeof(long), cudaMemcpyHostToDevice));
   TRY(dalloc(ctx, &c->d_blk_start, c->n_occ + 1));
   CU(cudaMemcpy(c->d_blk_start, blk_start.data(), (c->n_occ + 1) * sizeof(int), cudaMemcpyHostToDevice));
   c->d_blk_r = pp.r;
   c->d_blk_off = pp.off;
+  TRY(dalloc(ctx, &c->d_blk_col, pp.n));
+  CU(cudaMemcpy(c->d_blk_col, bcol.data(), pp.n * sizeof(int), cudaMemcpyHostToDevice));
+  TRY(dalloc(ctx, &c->d_cell_off, c->n_occ + 1));
+  CU(cudaMemcpy(c->d_cell_off, cell_off.data(), (c->n_occ + 1) * sizeof(long), cudaMemcpyHostToDevice));
+  TRY(dalloc(ctx, &c->d_cell_W, c->n_occ));
+  CU(cudaMemcpy(c->d_cell_W, cellW.data(), c->n_occ * sizeof(int), cudaMemcpyHostToDevice));
+  {  // node index of every local column of every cell (cells in order, columns in block order)
+    std::vector<int> cols, coloff(c->n_occ + 1, 0);
+    for (int q = 0; q < c->n_occ; ++q) {
+      coloff[q] = (int)cols.size();
+      for (int b = blk_start[q]; b < blk_start[q + 1]; ++b) {
+        int r = pr[b];
+        for (int l = c->cell_start[r]; l < c->cell_start[r + 1]; ++l) cols.push_back(c->node_idx[l]);
+      }
+    }
+    coloff[c->n_occ] = (int)cols.size();
+    TRY(dalloc(ctx, &c->d_cols, cols.size()));
+    TRY(dalloc(ctx, &c->d_coloff, c->n_occ + 1));
+    CU(cudaMemcpy(c->d_cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_coloff, coloff.data(), (c->n_occ + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  }
   TRY(dalloc(ctx, &c->d_C, c->nnz));
   zd* d_phi;
   TRY(dalloc(ctx, &d_phi, (size_t)3 * n_dcy * nfit * 2 * neq));
@@ -518,11 +591,15 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   TRY(dalloc(ctx, &c->d_MT, (size_t)c->N * std::max(1, c->nm)));
   TRY(dalloc(ctx, &c->d_MS, (size_t)c->N * std::max(1, c->nm)));
   CU(launch_modes(c, d_mn));
+  if (c->nm > 8) return set_err(ctx, SGF_EINVAL, "%d completion modes (at most 8 supported)", c->nm);
+  TRY(dalloc(ctx, &c->d_mpart, (size_t)std::max(1, c->nm) * c->mode_chunks));
+  TRY(dalloc(ctx, &c->d_mpart_ff, (size_t)std::max(1, c->nm) * c->mode_chunks));
 
   // ---------------- grids and FP32 copies
   for (int lam = 0; lam < 2; ++lam) {
     long sz = 2L * c->og[lam].Px * c->og[lam].nrow;
     TRY(dalloc(ctx, &c->o64.grid[lam], sz));
+    if (c->og[lam].Py > 2048) TRY(dalloc(ctx, &c->o64.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
     if (mixed) TRY(dalloc(ctx, &c->o32.grid[lam], sz));
   }
   if (mixed) {
@@ -532,6 +609,13 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     CU(launch_to_f32(c->o64.P, c->o32.P, (long)4 * neq * c->N, c->stream));
     CU(launch_to_f32(c->o64.Ip, c->o32.Ip, (long)nfit * c->N, c->stream));
     CU(launch_to_f32(c->o64.src_tw, c->o32.src_tw, (long)src_tw.size(), c->stream));
+    TRY(dalloc(ctx, &c->d_Cff, c->nnz));
+    TRY(dalloc(ctx, &c->d_muff, c->N));
+    CU(launch_split_ff(c->d_C, c->d_Cff, c->nnz, c->stream));
+    TRY(dalloc(ctx, &c->d_MTff, (size_t)c->N * std::max(1, c->nm)));
+    TRY(dalloc(ctx, &c->d_MSff, (size_t)c->N * std::max(1, c->nm)));
+    CU(launch_split_ff(c->d_MT, c->d_MTff, (long)c->N * c->nm, c->stream));
+    CU(launch_split_ff(c->d_MS, c->d_MSff, (long)c->N * c->nm, c->stream));
   }
   TRY(dalloc(ctx, &c->d_mu_tmp, (size_t)c->N * 2));
   TRY(dalloc(ctx, &c->d_out_tmp, (size_t)c->N * 2));
@@ -548,10 +632,27 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     }
     if (prec == 0) c->bytes64 = b; else c->bytes32 = b;
   }
-  c->launches_per_apply = 9;
+  c->launches_per_apply = 8;
   c->built = true;
+  // capture the forward map of each precision in use; on failure keep direct launches
+  c->use_graphs = getenv("SGF_NO_GRAPH") == nullptr;
+  if (c->use_graphs) {
+    for (int prec : {64, 32}) {
+      if (prec == 32 && !mixed) continue;
+      cudaError_t ge = build_apply_graph(c, prec);
+      if (ge != cudaSuccess) {
+        c->use_graphs = false;
+        snprintf(c->err, sizeof(c->err), "graph capture failed (%s); launching kernels directly",
+                 cudaGetErrorString(ge));
+        break;
+      }
+    }
+  }
+  CU(cudaStreamSynchronize(c->stream));
   return SGF_OK;
 }
+
+static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec);
 
 extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj) {
   if (!ctx) return SGF_EINVAL;
@@ -561,8 +662,8 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
   for (int r = 0; r < nrhs; ++r) {
     const zd* mu = (const zd*)mu_dev + (size_t)r * ctx->N;
     zd* out = (zd*)out_dev + (size_t)r * ctx->N;
-    cudaError_t e = ctx->prm.precision == 64 ? launch_apply64(ctx, mu, out) : launch_apply32(ctx, mu, out);
-    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "apply: %s", cudaGetErrorString(e));
+    sgf_status st = apply_prec(ctx, mu, out, ctx->prm.precision);
+    if (st != SGF_OK) return st;
   }
   if (ctx->profiling) {
     cudaEventSynchronize(ctx->ev[5]);
@@ -578,7 +679,12 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
 }
 
 static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec) {
-  cudaError_t e = prec == 64 ? launch_apply64(ctx, mu, out) : launch_apply32(ctx, mu, out);
+  const GraphSlot& gs = ctx->gs[prec == 64 ? 0 : 1];
+  cudaError_t e;
+  if (ctx->use_graphs && gs.ok && !ctx->profiling && ctx->debug_mask == 15)
+    e = launch_apply_graph(ctx, prec, mu, out);
+  else
+    e = prec == 64 ? launch_apply64(ctx, mu, out) : launch_apply32(ctx, mu, out);
   if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "apply: %s", cudaGetErrorString(e));
   return SGF_OK;
 }
@@ -816,10 +922,11 @@ extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, i
 extern "C" sgf_status sgf_info(const sgf_ctx* ctx, double* info) {
   if (!ctx || !info) return SGF_EINVAL;
   if (!ctx->built) return SGF_ESTATE;
-  double v[16] = {(double)ctx->N, (double)ctx->n_occ, (double)ctx->nnz, (double)ctx->og[0].Px,
+  double v[20] = {(double)ctx->N, (double)ctx->n_occ, (double)ctx->nnz, (double)ctx->og[0].Px,
                   (double)ctx->og[0].nrow, (double)ctx->og[0].Py, (double)ctx->og[1].Px, (double)ctx->og[1].nrow,
                   (double)ctx->og[1].Py, (double)ctx->neq, (double)ctx->nfit, (double)ctx->nb,
-                  (double)ctx->nm, ctx->bytes64, ctx->bytes32, (double)ctx->launches_per_apply};
+                  (double)ctx->nm, ctx->bytes64, ctx->bytes32, (double)ctx->launches_per_apply,
+                  ctx->use_graphs ? 1.0 : 0.0, (double)ctx->maxW, (double)ctx->maxnq, (double)ctx->twlog};
   memcpy(info, v, sizeof(v));
   return SGF_OK;
 }

@@ -129,7 +129,52 @@ __host__ __device__ inline double window_S(double x, double gamma, double a) {
   return exp(2.0 * exp(-1.0 / u) / (u - 1.0));
 }
 
-#define SGF_CUDA_CHECK(call)                                                      \
+// ---------------------------------------------------------------- float-float arithmetic
+// A value hi + lo held in two FP32 numbers (|lo| <= ulp(hi)/2): about 48 significant bits, computed
+// on the FP32 pipes with error-free transformations (two-sum, fma-based two-product). The explicit
+// round-to-nearest intrinsics keep the compiler from contracting or reassociating the steps.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_quick_two_sum(s, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_quick_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_from_double(double x) {
+  float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+// complex float-float packed as float4 {re.hi, im.hi, re.lo, im.lo}
+__device__ __forceinline__ float4 cff_from(zd z) {
+  ff r = ff_from_double(z.re), i = ff_from_double(z.im);
+  return make_float4(r.hi, i.hi, r.lo, i.lo);
+}
+// acc_re + i acc_im += c * m
+__device__ __forceinline__ void cff_mac(float4 c, float4 m, ff& acc_re, ff& acc_im) {
+  ff cr = {c.x, c.z}, ci = {c.y, c.w}, mr = {m.x, m.z}, mi = {m.y, m.w};
+  acc_re = ff_add(acc_re, ff_mul(cr, mr));
+  acc_re = ff_add(acc_re, ff_neg(ff_mul(ci, mi)));
+  acc_im = ff_add(acc_im, ff_mul(cr, mi));
+  acc_im = ff_add(acc_im, ff_mul(ci, mr));
+}
+
+#define SGF_CUDA_CHECK(call)                                                  \
   do {                                                                            \
     cudaError_t err__ = (call);                                                   \
     if (err__ != cudaSuccess) {                                                   \

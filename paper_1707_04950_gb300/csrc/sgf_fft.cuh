@@ -1,16 +1,124 @@
-// Shared-memory radix-2 FFT used by the global convolution of the accelerated operator
+// Shared-memory Stockham FFT used by the global convolution of the accelerated operator
 // (Bruno & Maas, eq. large_convolution_per_grid: cyclic in X after the quasi-periodic twist,
 // linear in Y with zero padding).
 #pragma once
 #include "sgf_common.cuh"
 
-// In-place radix-2 decimation-in-time FFT of `batch` sequences of length n = 2^logn held in shared
-// memory; element i of sequence b sits at s[b*bs + i*es]. tw[k] = e^{-2 pi i k / 2^twlog},
-// k < 2^(twlog-1). dir = -1 forward (e^{-2 pi i}), +1 inverse (unnormalised). Must be called by all
-// threads of the block; ends with __syncthreads().
+// Radix-R DFT in registers, R in {2, 4, 8}; dir = -1 forward, +1 inverse.
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
+  if (R == 2) {
+    cplx<T> t = a[0];
+    a[0] = t + a[1];
+    a[1] = t - a[1];
+  } else if (R == 4) {
+    // w4 = -i (forward) / +i (inverse)
+    cplx<T> v0 = a[0] + a[2], v2 = a[0] - a[2], v1 = a[1] + a[3], d = a[1] - a[3];
+    cplx<T> v3 = dir < 0 ? cplx<T>(d.im, -d.re) : cplx<T>(-d.im, d.re);
+    a[0] = v0 + v1;
+    a[2] = v0 - v1;
+    a[1] = v2 + v3;
+    a[3] = v2 - v3;
+  } else {
+    const T h = (T)0.70710678118654752440;
+    cplx<T> u[8];
+    for (int r = 0; r < 4; ++r) {
+      u[r] = a[r] + a[r + 4];
+      u[r + 4] = a[r] - a[r + 4];
+    }
+    // u5 *= w, u6 *= w^2, u7 *= w^3 with w = e^{-+ 2 pi i/8}
+    cplx<T> t5 = u[5], t6 = u[6], t7 = u[7];
+    if (dir < 0) {
+      u[5] = cplx<T>(h * (t5.re + t5.im), h * (t5.im - t5.re));
+      u[6] = cplx<T>(t6.im, -t6.re);
+      u[7] = cplx<T>(h * (t7.im - t7.re), -h * (t7.re + t7.im));
+    } else {
+      u[5] = cplx<T>(h * (t5.re - t5.im), h * (t5.im + t5.re));
+      u[6] = cplx<T>(-t6.im, t6.re);
+      u[7] = cplx<T>(-h * (t7.re + t7.im), h * (t7.re - t7.im));
+    }
+    for (int g = 0; g < 2; ++g) {
+      cplx<T>* c = u + 4 * g;
+      cplx<T> v0 = c[0] + c[2], v2 = c[0] - c[2], v1 = c[1] + c[3], d = c[1] - c[3];
+      cplx<T> v3 = dir < 0 ? cplx<T>(d.im, -d.re) : cplx<T>(-d.im, d.re);
+      a[g] = v0 + v1;
+      a[g + 4] = v0 - v1;
+      a[g + 2] = v2 + v3;
+      a[g + 6] = v2 - v3;
+    }
+  }
+}
+
+// One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es, int batch, int bs,
+                                               const cplx<T>* __restrict__ tw, int twlog, int dir) {
+  constexpr int U = 16 / R;  // items per thread: every item of the stage is loaded before any store
+  const int nR = n / R;
+  const int tot = batch * nR;
+  const int tstep = (1 << twlog) / (Ns * R);  // table stride of e^{-2 pi i / (Ns R)}
+  cplx<T> a[U][R];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int idx = u * blockDim.x + threadIdx.x;
+    if (idx < tot) {
+      const int b = idx / nR, j = idx - b * nR;
+      const int k = j % Ns;
+      const cplx<T>* sb = s + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) a[u][r] = sb[(j + r * nR) * es];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cplx<T> w = tw[r * k * tstep];
+          if (dir > 0) w.im = -w.im;
+          a[u][r] = a[u][r] * w;
+        }
+      }
+      dft_reg<T, R>(a[u], dir);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int idx = u * blockDim.x + threadIdx.x;
+    if (idx < tot) {
+      const int b = idx / nR, j = idx - b * nR;
+      const int k = j % Ns;
+      const int od = (j / Ns) * Ns * R + k;
+      cplx<T>* sb = s + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sb[(od + r * Ns) * es] = a[u][r];
+    }
+  }
+  __syncthreads();
+}
+
+// In-place FFT of `batch` sequences of length n = 2^logn held in shared memory; element i of
+// sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 8 (then 4 or 2 for the
+// remaining factor). tw[k] = e^{-2 pi i k / 2^twlog} over the full circle, twlog >= logn.
+// dir = -1 forward, +1 inverse (unnormalised). All threads of the block must call it.
+// Each stage exchanges through registers in place, so every thread holds all of its items at once:
+// the caller must keep batch * n <= 16 * blockDim.x.
 template <typename T>
 __device__ void smem_fft(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
                          int twlog, int dir) {
+  const int n = 1 << logn;
+  int Ns = 1, rem = logn;
+  while (rem >= 3) {
+    stockham_stage<T, 8>(s, n, Ns, es, batch, bs, tw, twlog, dir);
+    Ns <<= 3;
+    rem -= 3;
+  }
+  if (rem == 2) stockham_stage<T, 4>(s, n, Ns, es, batch, bs, tw, twlog, dir);
+  if (rem == 1) stockham_stage<T, 2>(s, n, Ns, es, batch, bs, tw, twlog, dir);
+  if (logn == 0) __syncthreads();
+}
+
+// Reference radix-2 decimation-in-time FFT (bit reversal + butterflies), kept for testing.
+template <typename T>
+__device__ void smem_fft_radix2(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
+                                int twlog, int dir) {
   const int n = 1 << logn;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int idx = tid; idx < batch * n; idx += nt) {
@@ -51,6 +159,8 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Px = 1 << logPx;
+  cplx<T>* tws = s + Px * ty;  // twiddles of this length, staged once per block
+  for (int i = threadIdx.x; i < Px; i += blockDim.x) tws[i] = tw[i << (twlog - logPx)];
   cplx<T>* a = g + blockIdx.y * arr_stride;
   const int iy0 = blockIdx.x * ty;
   for (int idx = threadIdx.x; idx < Px * ty; idx += blockDim.x) {
@@ -59,7 +169,7 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
     s[ix * ty + t] = (iy < nrow) ? a[(long)ix * nrow + iy] : cplx<T>(0, 0);
   }
   __syncthreads();
-  smem_fft<T>(s, logPx, ty, ty, 1, tw, twlog, dir);
+  smem_fft<T>(s, logPx, ty, ty, 1, tws, logPx, dir);
   for (int idx = threadIdx.x; idx < Px * ty; idx += blockDim.x) {
     int t = idx % ty, ix = idx / ty;
     int iy = iy0 + t;
@@ -85,37 +195,57 @@ __global__ void k_fft_y_full(cplx<T>* __restrict__ g, int logPy, const cplx<T>* 
 //   phi^(kx) = IFFT_y( Km^(kx) . FFT_y(xi^(kx)) + Kd^(kx) . FFT_y(zeta^(kx)) )
 // xi, zeta hold nrow rows (zero padded to Py here); the first nrow outputs overwrite xi.
 // K* hold the Py-point spectra per kx, already scaled by 1/(Px Py).
-template <typename T, int MAXR>
+template <typename T, int MAXR, bool ACCG>
 __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ zeta,
                          const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int logPy, int nrow,
-                         const cplx<T>* __restrict__ tw, int twlog) {
+                         const cplx<T>* __restrict__ tw, int twlog, cplx<T>* __restrict__ accg) {
+  // ACCG: the partial product K_m FFT(xi) waits in a global scratch column (used when registers
+  // cannot hold it next to the FFT's own values); otherwise it stays in registers.
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Py = 1 << logPy;
   const long kx = blockIdx.x;
-  cplx<T> acc[MAXR];
+  cplx<T> acc[ACCG ? 1 : MAXR];
+  // twiddles of this length in shared memory after the column (when there is room: !ACCG)
+  const cplx<T>* twf = tw;
+  int twl = twlog;
+  if (!ACCG) {
+    cplx<T>* tws = s + Py;
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = tw[i << (twlog - logPy)];
+    twf = tws;
+    twl = logPy;
+  }
   cplx<T>* col = xi + kx * nrow;
   const cplx<T>* colz = zeta + kx * nrow;
   const cplx<T>* km = Km + kx * Py;
   const cplx<T>* kd = Kd + kx * Py;
+  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, tw, twlog, -1);
+  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, -1);
+  if (ACCG) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) ag[i] = s[i] * km[i];
+  } else {
 #pragma unroll
-  for (int r = 0; r < MAXR; ++r) {
-    int i = threadIdx.x + r * blockDim.x;
-    if (i < Py) acc[r] = s[i] * km[i];
+    for (int r = 0; r < MAXR; ++r) {
+      int i = threadIdx.x + r * blockDim.x;
+      if (i < Py) acc[ACCG ? 0 : r] = s[i] * km[i];
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, tw, twlog, -1);
+  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, -1);
+  if (ACCG) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = s[i] * kd[i] + ag[i];
+  } else {
 #pragma unroll
-  for (int r = 0; r < MAXR; ++r) {
-    int i = threadIdx.x + r * blockDim.x;
-    if (i < Py) s[i] = s[i] * kd[i] + acc[r];
+    for (int r = 0; r < MAXR; ++r) {
+      int i = threadIdx.x + r * blockDim.x;
+      if (i < Py) s[i] = s[i] * kd[i] + acc[ACCG ? 0 : r];
+    }
   }
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, tw, twlog, +1);
+  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
 }

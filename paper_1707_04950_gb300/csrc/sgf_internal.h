@@ -25,7 +25,17 @@ struct OpData {
   cplx<T>* src_tw = nullptr;   // [n_occ][2][neq] twist e^{-i alpha x_src} of the scatter
   cplx<T>* Khat[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [lam][mono, dip] spectra / (Px Py)
   cplx<T>* grid[2] = {nullptr, nullptr};                          // [lam]: xi then zeta, Px*nrow each
-  cplx<T>* tw = nullptr;       // FFT twiddles e^{-2 pi i k / 2^twlog}
+  cplx<T>* tw = nullptr;       // FFT twiddles e^{-2 pi i k / 2^twlog}, full circle
+  cplx<T>* accg[2] = {nullptr, nullptr};  // [lam] Y-convolution scratch [Px][Py] (FP64, long columns)
+};
+
+// One captured forward map: the kernel nodes that take mu/out are updated before each launch.
+struct GraphSlot {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t n_proj = nullptr, n_interp = nullptr;
+  cudaKernelNodeParams kp_proj{}, kp_interp{};
+  bool ok = false;
 };
 
 struct sgf_ctx {
@@ -61,11 +71,26 @@ struct sgf_ctx {
   long nnz = 0;
   int* d_blk_start = nullptr;  // [n_occ + 1] into block list
   int* d_blk_r = nullptr;      // occupied index of the source cell
-  long* d_blk_off = nullptr;   // value offset
+  long* d_blk_off = nullptr;   // value offset of the block's first entry
+  int* d_blk_col = nullptr;    // column offset of the block within its cell's rows
+  long* d_cell_off = nullptr;  // [n_occ + 1] value offset of each cell's n_q x W_q rows
+  int* d_cell_W = nullptr;     // [n_occ] row length W_q
+  int* d_cols = nullptr;       // node index of each local column, cells in order
+  int* d_coloff = nullptr;     // [n_occ + 1] offsets into d_cols
+  int maxW = 0;
   zd* d_blk_ph = nullptr;      // quasi-periodic phase of the source cell copy
   zd* d_C = nullptr;
+  float4* d_Cff = nullptr;      // near operator as float-float pairs (mixed path)
+  float4* d_muff = nullptr;     // [N] float-float copy of the density (mixed path)
   // modes
   zd *d_MT = nullptr, *d_MS = nullptr, *d_msum = nullptr;
+  float4 *d_MTff = nullptr, *d_MSff = nullptr;  // float-float mode factors (mixed path)
+  zd* d_mpart = nullptr;        // [nm][mode_chunks] FP64 mode-sum partials
+  float4* d_mpart_ff = nullptr; // [nm][mode_chunks] float-float partials
+  int mode_chunks = 64;
+  // work items of the forward map: chunks of at most 32 nodes of one cell
+  int n_items = 0;
+  int *d_item_cell = nullptr, *d_item_lo = nullptr, *d_item_hi = nullptr;
   // precision-specific operator data
   OpData<double> o64;
   OpData<float> o32;
@@ -76,8 +101,13 @@ struct sgf_ctx {
   std::vector<void*> allocs;
   // profiling
   bool profiling = false;
+  GraphSlot gs[2];  // [0] FP64, [1] mixed
+  bool use_graphs = true;
+  int maxnq = 0;
   int debug_mask = 15;
   cudaEvent_t ev[8] = {nullptr};
+  cudaStream_t side = nullptr;  // second stream for the V orientation of the forward map
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double stage_ms[8] = {0};
   int launches_per_apply = 0;
   double bytes64 = 0, bytes32 = 0;
@@ -98,16 +128,20 @@ cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const 
                            const double* d_src_rel);
 struct NearPairs {  // device arrays of the (q, r) block list
   int n = 0;
-  int *q = nullptr, *r = nullptr, *wrap = nullptr, *dcx = nullptr;
+  int *q = nullptr, *r = nullptr, *wrap = nullptr, *dcx = nullptr, *ld = nullptr;
   long* off = nullptr;
 };
 cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
                         const double* d_kress);
 cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n);
 cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s);
+cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s);
 cudaError_t launch_rhs(sgf_ctx* c, zd* out);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
+cudaError_t build_apply_graph(sgf_ctx* c, int prec);
+cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out);
+void destroy_graphs(sgf_ctx* c);
 cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B);
 cudaError_t launch_twiddles(sgf_ctx* c);
 cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);

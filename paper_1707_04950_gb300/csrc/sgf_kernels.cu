@@ -260,7 +260,7 @@ __global__ void k_build_P(GeoArgs g, const int* __restrict__ cell_start, const i
       const zd* pr = pinv_eq + ((long)lam * 2 * g.neq + s) * g.ncoll;
       zd acc(0, 0);
       for (int t = 0; t < g.ncoll; ++t) acc += pr[t] * T[t];
-      Pq[(long)o * nq + l] = acc;
+      Pq[(long)l * nout + o] = acc;
     }
     __syncwarp();
   }
@@ -463,13 +463,23 @@ __global__ void k_to_f32(const zd* __restrict__ s, zf* __restrict__ d, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) d[i] = zf((float)s[i].re, (float)s[i].im);
 }
+// Full-circle table tw[i] = e^{-2 pi i i / 2^twlog}, i < 2^twlog.
 __global__ void k_twiddles(zd* tw, int twlog) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int n = 1 << twlog;
-  if (i >= n / 2) return;
+  if (i >= n) return;
   double s, c;
   sincospi(-2.0 * i / n, &s, &c);
   tw[i] = zd(c, s);
+}
+
+__global__ void k_split_ff(const zd* __restrict__ s, float4* __restrict__ d, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = cff_from(s[i]);
+}
+cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s) {
+  k_split_ff<<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s) {
@@ -477,22 +487,33 @@ cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static size_t fftx_smem(int Px, int ty, size_t esz) { return (size_t)Px * ty * esz; }
-static int fftx_ty(int Px, size_t esz) {
-  int ty = (int)(96 * 1024 / ((size_t)Px * esz));
-  if (ty > 32) ty = 32;
+static size_t fftx_smem(int Px, int ty, size_t esz) { return (size_t)Px * (ty + 1) * esz; }
+// Rows per block of the X passes: at least 16 contiguous bytes per column read, enough blocks for
+// two waves of the 152 SMs where the row count allows; threads = Px * ty / 16 (16 values each).
+static int fftx_ty(int Px, int nrow, size_t esz) {
+  int tmax = 8192 / Px;
+  int tcoal = (int)((16 + esz - 1) / esz);
+  int ttarget = (nrow + 303) / 304;
+  int ty = std::max(tcoal, ttarget);
+  if (ty > tmax) ty = tmax;
   if (ty < 1) ty = 1;
   return ty;
+}
+static int fftx_threads(int Px, int ty) {
+  int t = Px * ty / 16;
+  if (t < 64) t = 64;
+  if (t > 512) t = 512;
+  return t;
 }
 
 template <typename T>
 static cudaError_t run_fft_x(cplx<T>* g, const Orient& o, int nrow, int narr, const cplx<T>* tw, int twlog, int dir,
                              cudaStream_t s) {
-  int ty = fftx_ty(o.Px, sizeof(cplx<T>));
+  int ty = fftx_ty(o.Px, nrow, sizeof(cplx<T>));
   size_t sm = fftx_smem(o.Px, ty, sizeof(cplx<T>));
   cudaFuncSetAttribute(k_fft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(ceil_div(nrow, ty), narr);
-  k_fft_x<T><<<grid, 256, sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
+  k_fft_x<T><<<grid, fftx_threads(o.Px, ty), sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
   return cudaGetLastError();
 }
 
@@ -543,8 +564,8 @@ cudaError_t launch_tables(sgf_ctx* c) {
 
 cudaError_t launch_twiddles(sgf_ctx* c) {
   int n = 1 << c->twlog;
-  k_twiddles<<<ceil_div(n / 2, 256), 256, 0, c->stream>>>(c->o64.tw, c->twlog);
-  if (c->o32.tw) launch_to_f32(c->o64.tw, c->o32.tw, n / 2, c->stream);
+  k_twiddles<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->o64.tw, c->twlog);
+  if (c->o32.tw) launch_to_f32(c->o64.tw, c->o32.tw, n, c->stream);
   return cudaGetLastError();
 }
 
@@ -599,13 +620,15 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
                        const double* __restrict__ f1, const double* __restrict__ f2, const zd* __restrict__ phi,
                        int dcy_min, int n_dcy, const zd* __restrict__ Iplain, const zd* __restrict__ P,
                        const int* __restrict__ pq, const int* __restrict__ pr, const int* __restrict__ pw,
-                       const long* __restrict__ poff, const int* __restrict__ pdcx, const double* __restrict__ kress,
+                       const long* __restrict__ poff, const int* __restrict__ pld, const int* __restrict__ pdcx,
+                       const double* __restrict__ kress,
                        const double* __restrict__ binw, zd hk, zd* C) {
   extern __shared__ unsigned char smem_raw[];
   zd* Msh = reinterpret_cast<zd*>(smem_raw);
   const int b = blockIdx.x;
   const int q = pq[b], r = pr[b], wrap = pw[b];
   const long off = poff[b];
+  const long ld = pld[b];
   const int qs = cell_start[q], nq = cell_start[q + 1] - qs;
   const int rs = cell_start[r], nr = cell_start[r + 1] - rs;
   const int dcx = pdcx[b];
@@ -618,7 +641,7 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
     int t = idx / nr, l = idx % nr;
     int lam = orient_of_sample(t, g.p);
     zd acc(0, 0);
-    for (int s = 0; s < 2 * g.neq; ++s) acc += ph_o[t * 2 * g.neq + s] * Pr[((long)lam * 2 * g.neq + s) * nr + l];
+    for (int s = 0; s < 2 * g.neq; ++s) acc += ph_o[t * 2 * g.neq + s] * Pr[(long)l * 4 * g.neq + lam * 2 * g.neq + s];
     Msh[idx] = acc;
   }
   __syncthreads();
@@ -654,7 +677,7 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
     const zd* Ii = Iplain + (long)(qs + il) * g.nfit;
     zd sub(0, 0);
     for (int t = 0; t < g.nfit; ++t) sub += Ii[t] * Msh[t * nr + l];
-    C[off + (long)il * nr + l] = wph * (val - sub);
+    C[off + (long)il * ld + l] = wph * (val - sub);
   }
 }
 
@@ -672,7 +695,7 @@ cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, con
   cudaError_t e = near_hk(c, &hk);
   if (e != cudaSuccess) return e;
   k_near<<<pp.n, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cy, c->d_x, c->d_f, c->d_f1, c->d_f2,
-                                       d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp.q, pp.r, pp.wrap, pp.off, pp.dcx,
+                                       d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp.q, pp.r, pp.wrap, pp.off, pp.ld, pp.dcx,
                                        d_kress, c->d_binw, hk, c->d_C);
   return cudaGetLastError();
 }
@@ -738,109 +761,258 @@ cudaError_t launch_rhs(sgf_ctx* c, zd* out) {
 }
 
 // ============================================================== forward map
+// Mode-sum partials (eq. D_M_deltax, source factors): block (n, chunk) of the grid tail sums
+// MS[n][i] mu_i over one chunk of the nodes; FP64 for T = double, float-float for T = float.
+template <typename T>
+__device__ __forceinline__ void mode_partial(int n, int chunk, int MB, long N, const zd* __restrict__ mu,
+                                             const zd* __restrict__ MS, const float4* __restrict__ MSff,
+                                             zd* __restrict__ mpart, float4* __restrict__ mpart_ff) {
+  __shared__ float4 redf[32];
+  __shared__ zd redd[32];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const long len = (N + MB - 1) / MB, i0 = chunk * len, i1 = min(N, i0 + len);
+  if (sizeof(T) == 4) {
+    ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+    for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) cff_mac(MSff[n * N + i], cff_from(mu[i]), ar, ai);
+    for (int o = 16; o > 0; o >>= 1) {
+      ar = ff_add(ar, {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)});
+      ai = ff_add(ai, {__shfl_down_sync(0xffffffffu, ai.hi, o), __shfl_down_sync(0xffffffffu, ai.lo, o)});
+    }
+    if (lane == 0) redf[warp] = make_float4(ar.hi, ai.hi, ar.lo, ai.lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ff sr = {0.f, 0.f}, si = {0.f, 0.f};
+      for (int w = 0; w < nw; ++w) {
+        sr = ff_add(sr, {redf[w].x, redf[w].z});
+        si = ff_add(si, {redf[w].y, redf[w].w});
+      }
+      mpart_ff[n * MB + chunk] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+    }
+  } else {
+    zd acc(0, 0);
+    for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += MS[n * N + i] * mu[i];
+    acc = warp_sum(acc);
+    if (lane == 0) redd[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      zd v = lane < nw ? redd[lane] : zd(0, 0);
+      v = warp_sum(v);
+      if (lane == 0) mpart[n * MB + chunk] = v;
+    }
+  }
+}
+
+// EqSources + GlobalEqSMerge: block per occupied cell, one thread per output (orientation,
+// monopole/dipole, source) of P_q mu_q (P stored [node][output]), scattered with the quasi-periodic
+// twist into the X-major grids. The grid tail (nm * MB blocks) computes the mode-sum partials. For
+// the mixed path the cell blocks also write the float-float copy of mu used by the near field.
 template <typename T>
 __global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restrict__ cell_start,
                           const int* __restrict__ node_idx, const zd* __restrict__ mu, const cplx<T>* __restrict__ P,
                           const int* __restrict__ src_gidx, const cplx<T>* __restrict__ src_tw,
                           cplx<T>* __restrict__ gH, long gH_stride, cplx<T>* __restrict__ gV, long gV_stride,
-                          const zd* __restrict__ MS, zd* __restrict__ msum) {
+                          const zd* __restrict__ MS, const float4* __restrict__ MSff, zd* __restrict__ mpart,
+                          float4* __restrict__ mpart_ff, float4* __restrict__ muff, int MB, int n_items,
+                          const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                          const int* __restrict__ item_hi) {
   extern __shared__ unsigned char smem_raw[];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  if ((int)blockIdx.x >= n_occ) {
-    // mode sums sum_i MS[n][i] mu_i (FP64)
-    __shared__ zd red[32];
-    int n = blockIdx.x - n_occ;
-    zd acc(0, 0);
-    for (long i = threadIdx.x; i < N; i += blockDim.x) acc += MS[n * N + i] * mu[i];
-    acc = warp_sum(acc);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (warp == 0) {
-      zd v = lane < nw ? red[lane] : zd(0, 0);
-      v = warp_sum(v);
-      if (lane == 0) msum[n] = v;
-    }
+  if ((int)blockIdx.x >= n_items) {
+    const int t = blockIdx.x - n_items;
+    mode_partial<T>(t / MB, t % MB, MB, N, mu, MS, MSff, mpart, mpart_ff);
     return;
   }
+  // one block per chunk of at most 32 nodes of a cell: the scatter is additive, so chunks of one
+  // cell add their partial densities independently
   cplx<T>* mus = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int q = blockIdx.x;
-  const int s0 = cell_start[q], nq = cell_start[q + 1] - s0;
-  for (int l = threadIdx.x; l < nq; l += blockDim.x) mus[l] = cplx<T>(mu[node_idx[s0 + l]]);
+  const int q = item_cell[blockIdx.x];
+  const int ncell = cell_start[q + 1] - cell_start[q];
+  const int lo = item_lo[blockIdx.x], nq = item_hi[blockIdx.x] - lo;
+  const int s0 = cell_start[q] + lo;
+  for (int l = threadIdx.x; l < nq; l += blockDim.x) {
+    const int nid = node_idx[s0 + l];
+    const zd m = mu[nid];
+    mus[l] = cplx<T>(m);
+    if (muff) muff[nid] = cff_from(m);
+  }
   __syncthreads();
   const int nout = 4 * neq;
-  const cplx<T>* Pq = P + (long)nout * s0;
-  for (int o = warp; o < nout; o += nw) {
-    const cplx<T>* row = Pq + (long)o * nq;
-    cplx<T> acc(0, 0);
-    for (int l = lane; l < nq; l += 32) acc = fma_c(row[l], mus[l], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      int lam = o / (2 * neq), s = o % (2 * neq);
-      int si = s % neq;
-      long gi = src_gidx[((long)q * 2 + lam) * neq + si];
-      cplx<T> v = acc * src_tw[((long)q * 2 + lam) * neq + si];
-      cplx<T>* base = lam == 0 ? gH + (s < neq ? 0 : gH_stride) : gV + (s < neq ? 0 : gV_stride);
-      atomicAdd(&base[gi].re, v.re);
-      atomicAdd(&base[gi].im, v.im);
+  const cplx<T>* Pq = P + (long)nout * s0;  // [node][output] rows of this chunk
+  (void)ncell;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    cplx<T> acc(0, 0), acc1(0, 0), acc2(0, 0), acc3(0, 0);
+    int l = 0;
+    for (; l + 3 < nq; l += 4) {
+      acc = fma_c(Pq[(long)l * nout + o], mus[l], acc);
+      acc1 = fma_c(Pq[(long)(l + 1) * nout + o], mus[l + 1], acc1);
+      acc2 = fma_c(Pq[(long)(l + 2) * nout + o], mus[l + 2], acc2);
+      acc3 = fma_c(Pq[(long)(l + 3) * nout + o], mus[l + 3], acc3);
     }
+    for (; l < nq; ++l) acc = fma_c(Pq[(long)l * nout + o], mus[l], acc);
+    acc = (acc + acc1) + (acc2 + acc3);
+    int lam = o / (2 * neq), s = o % (2 * neq);
+    int si = s % neq;
+    long gi = src_gidx[((long)q * 2 + lam) * neq + si];
+    cplx<T> v = acc * src_tw[((long)q * 2 + lam) * neq + si];
+    cplx<T>* base = lam == 0 ? gH + (s < neq ? 0 : gH_stride) : gV + (s < neq ? 0 : gV_stride);
+    atomicAdd(&base[gi].re, v.re);
+    atomicAdd(&base[gi].im, v.im);
   }
 }
 
+// Combine-lambda + NonIntersecting + Intersecting + EvalSingular + EvalModes + AddOperators. Block
+// per occupied cell: the local densities are staged in shared memory once, each warp streams whole
+// rows of the cell's near block and reconstruction rows, and one thread per row adds the identity
+// and mode terms and writes the result. T = double: all FP64. T = float: FP32 far field; near field,
+// modes and identity in float-float (FP32 pipes; FP64 only for the final conversion).
 template <typename T>
 __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, const int* __restrict__ cell_start,
                               const int* __restrict__ node_idx, const int* __restrict__ samp_gidx, int pH,
                               const cplx<T>* __restrict__ phiH, const cplx<T>* __restrict__ phiV,
-                              const cplx<T>* __restrict__ Ip, const int* __restrict__ blk_start,
-                              const int* __restrict__ blk_r, const long* __restrict__ blk_off,
-                              const zd* __restrict__ blk_ph, const zd* __restrict__ C, const zd* __restrict__ MT,
-                              const zd* __restrict__ msum, const zd* __restrict__ mu, zd* __restrict__ out) {
+                              const cplx<T>* __restrict__ Ip, const int* __restrict__ cols,
+                              const int* __restrict__ coloff, const long* __restrict__ cell_off,
+                              const int* __restrict__ cell_W, const zd* __restrict__ C,
+                              const float4* __restrict__ Cff, const float4* __restrict__ muff,
+                              const zd* __restrict__ MT, const float4* __restrict__ MTff,
+                              const zd* __restrict__ mpart, const float4* __restrict__ mpart_ff, int MB,
+                              const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                              const int* __restrict__ item_hi, const zd* __restrict__ mu, zd* __restrict__ out) {
+  constexpr bool FF = sizeof(T) == 4;
+  extern __shared__ unsigned char smem_raw[];
   __shared__ cplx<T> ph[64];
+  __shared__ float4 msf[8];
+  __shared__ zd msd[8];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  const int q = blockIdx.x;
-  const int s0 = cell_start[q], nq = cell_start[q + 1] - s0;
+  // one block per chunk of at most 32 target rows of a cell
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  const int W = cell_W[q];
+  // shared layout: [W] densities (16 B each), then [nq] per-row results (16 B each)
+  zd* mus = reinterpret_cast<zd*>(smem_raw);
+  float4* musf = reinterpret_cast<float4*>(smem_raw);
+  zd* resd = reinterpret_cast<zd*>(smem_raw) + W;
+  float4* resf = reinterpret_cast<float4*>(smem_raw) + W;
   for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
     long gi = samp_gidx[(long)q * nfit + t];
     ph[t] = t < 2 * (pH + 1) ? phiH[gi] : phiV[gi];
   }
+  // mode sums from their chunk partials (warp per mode)
+  if (warp < nm && (mask & 4)) {
+    if (FF) {
+      ff sr = {0.f, 0.f}, si = {0.f, 0.f};
+      for (int cch = lane; cch < MB; cch += 32) {
+        float4 v = mpart_ff[warp * MB + cch];
+        sr = ff_add(sr, {v.x, v.z});
+        si = ff_add(si, {v.y, v.w});
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
+        si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
+      }
+      if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+    } else {
+      zd a(0, 0);
+      for (int cch = lane; cch < MB; cch += 32) a += mpart[warp * MB + cch];
+      a = warp_sum(a);
+      if (lane == 0) msd[warp] = a;
+    }
+  }
+  const int* cq = cols + coloff[q];
+  if (FF) {
+    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) musf[cc] = muff[cq[cc]];
+  } else {
+    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) mus[cc] = mu[cq[cc]];
+  }
   __syncthreads();
-  const int b0 = blk_start[q], b1 = blk_start[q + 1];
   for (int il = warp; il < nq; il += nw) {
     const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
     cplx<T> far(0, 0);
-    for (int t = lane; t < nfit; t += 32) far = fma_c(Ir[t], ph[t], far);
+    if (mask & 1)
+      for (int t = lane; t < nfit; t += 32) far = fma_c(Ir[t], ph[t], far);
     far = warp_sum(far);
-    zd acc(0, 0);
-    for (int b = b0; b < b1; ++b) {
-      int r = blk_r[b];
-      int rs = cell_start[r], nr = cell_start[r + 1] - rs;
-      const zd* Cr = C + blk_off[b] + (long)il * nr;
-      zd part(0, 0);
-      for (int l = lane; l < nr; l += 32) part = fma_c(Cr[l], mu[node_idx[rs + l]], part);
-      acc += part;
+    if (FF) {
+      ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+      if (mask & 2) {
+        const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
+        ff br = {0.f, 0.f}, bi = {0.f, 0.f};
+        int cc = lane;
+        for (; cc + 32 < W; cc += 64) {
+          cff_mac(Cr[cc], musf[cc], ar, ai);
+          cff_mac(Cr[cc + 32], musf[cc + 32], br, bi);
+        }
+        if (cc < W) cff_mac(Cr[cc], musf[cc], ar, ai);
+        ar = ff_add(ar, br);
+        ai = ff_add(ai, bi);
+        for (int o = 16; o > 0; o >>= 1) {
+          ar = ff_add(ar, {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)});
+          ai = ff_add(ai, {__shfl_down_sync(0xffffffffu, ai.hi, o), __shfl_down_sync(0xffffffffu, ai.lo, o)});
+        }
+      }
+      if (lane == 0) {
+        ar = ff_add(ar, {(float)far.re, 0.f});
+        ai = ff_add(ai, {(float)far.im, 0.f});
+        resf[il] = make_float4(ar.hi, ai.hi, ar.lo, ai.lo);
+      }
+    } else {
+      zd acc(0, 0);
+      if (mask & 2) {
+        const zd* Cr = C + cell_off[q] + (long)(rlo + il) * W;
+        zd acc1(0, 0), acc2(0, 0), acc3(0, 0);
+        int cc = lane;
+        for (; cc + 96 < W; cc += 128) {
+          acc = fma_c(Cr[cc], mus[cc], acc);
+          acc1 = fma_c(Cr[cc + 32], mus[cc + 32], acc1);
+          acc2 = fma_c(Cr[cc + 64], mus[cc + 64], acc2);
+          acc3 = fma_c(Cr[cc + 96], mus[cc + 96], acc3);
+        }
+        for (; cc < W; cc += 32) acc = fma_c(Cr[cc], mus[cc], acc);
+        acc = warp_sum((acc + acc1) + (acc2 + acc3));
+      }
+      if (lane == 0) resd[il] = acc + zd((double)far.re, (double)far.im);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      int i = node_idx[s0 + il];
-      zd v(0, 0);
-      if (mask & 8) v += half_sigma * mu[i];
-      if (mask & 1) v += zd((double)far.re, (double)far.im);
-      if (mask & 2) v += acc;
+  }
+  __syncthreads();
+  // thread per row: identity and mode terms, conversion, store
+  for (int il = threadIdx.x; il < nq; il += blockDim.x) {
+    const int i = node_idx[s0 + il];
+    if (FF) {
+      float4 r = resf[il];
+      ff vr = {r.x, r.z}, vi = {r.y, r.w};
+      if (mask & 8) {
+        float4 m = muff[i];
+        float hs = (float)half_sigma;  // +-1/2: exact scaling
+        vr = ff_add(vr, {hs * m.x, hs * m.z});
+        vi = ff_add(vi, {hs * m.y, hs * m.w});
+      }
       if (mask & 4)
-        for (int n = 0; n < nm; ++n) v += MT[(long)i * nm + n] * msum[n];
+        for (int n = 0; n < nm; ++n) cff_mac(MTff[(long)i * nm + n], msf[n], vr, vi);
+      out[i] = zd(ff_to_double(vr), ff_to_double(vi));
+    } else {
+      zd v = resd[il];
+      if (mask & 8) v += half_sigma * mu[i];
+      if (mask & 4)
+        for (int n = 0; n < nm; ++n) v += MT[(long)i * nm + n] * msd[n];
       out[i] = v;
     }
   }
 }
 
-template <typename T, int MAXR>
+template <typename T>
 static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
-                          const cplx<T>* tw, int twlog, cudaStream_t s) {
-  int threads = o.Py / MAXR;
+                          const cplx<T>* tw, int twlog, cplx<T>* accg, cudaStream_t s) {
+  int threads = o.Py / 16;
   if (threads < 64) threads = 64;
   if (threads > 1024) return cudaErrorInvalidValue;
   size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  cudaFuncSetAttribute(k_conv_y<T, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_conv_y<T, MAXR><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog);
+  if (sizeof(T) == 8 && o.Py > 2048) {  // no room for a twiddle table: global twiddles
+    if (!accg) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_conv_y<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog, accg);
+  } else {
+    sm *= 2;  // column + twiddle table
+    cudaFuncSetAttribute(k_conv_y<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog, nullptr);
+  }
   return cudaGetLastError();
 }
 
@@ -853,43 +1025,155 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
   if (c->profiling) cudaEventRecord(c->ev[0], s);
   cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(cplx<T>), s);
   cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(cplx<T>), s);
-  int maxnq = 0;
-  for (int q = 0; q < c->n_occ; ++q) maxnq = std::max(maxnq, c->cell_start[q + 1] - c->cell_start[q]);
-  k_project<T><<<c->n_occ + c->nm, 256, (size_t)maxnq * sizeof(cplx<T>), s>>>(
+  k_project<T><<<c->n_items + c->nm * c->mode_chunks, 128, (size_t)32 * sizeof(cplx<T>), s>>>(
       c->n_occ, c->neq, c->nm, c->N, c->d_cell_start, c->d_node_idx, mu, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
-      szH, od.grid[1], szV, c->d_MS, c->d_msum);
+      szH, od.grid[1], szV, c->d_MS, c->d_MSff, c->d_mpart, c->d_mpart_ff, sizeof(T) == 4 ? c->d_muff : nullptr,
+      c->mode_chunks, c->n_items, c->d_item_cell, c->d_item_lo, c->d_item_hi);
   if (c->profiling) cudaEventRecord(c->ev[1], s);
   cudaError_t e;
-  for (int lam = 0; lam < 2; ++lam) {
-    const Orient& o = c->og[lam];
-    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, s)) != cudaSuccess) return e;
-  }
-  if (c->profiling) cudaEventRecord(c->ev[2], s);
-  for (int lam = 0; lam < 2; ++lam) {
-    const Orient& o = c->og[lam];
-    long sz = (long)o.Px * o.nrow;
-    if (sizeof(T) == 8)
-      e = conv_y<T, 16>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog, s);
-    else
-      e = conv_y<T, 16>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog, s);
-    if (e != cudaSuccess) return e;
-  }
-  if (c->profiling) cudaEventRecord(c->ev[3], s);
-  for (int lam = 0; lam < 2; ++lam) {
-    const Orient& o = c->og[lam];
-    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, s)) != cudaSuccess) return e;
+  if (!c->profiling && c->side) {
+    // the two orientations are independent until the interpolation: V runs on the side stream
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    for (int lam = 0; lam < 2; ++lam) {
+      const Orient& o = c->og[lam];
+      cudaStream_t st = lam == 0 ? s : c->side;
+      long sz = (long)o.Px * o.nrow;
+      if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, st)) != cudaSuccess) return e;
+      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog,
+                    od.accg[lam], st);
+      if (e != cudaSuccess) return e;
+      if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, st)) != cudaSuccess) return e;
+    }
+    cudaEventRecord(c->ev_join, c->side);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
+  } else {
+    for (int lam = 0; lam < 2; ++lam) {
+      const Orient& o = c->og[lam];
+      if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, s)) != cudaSuccess) return e;
+    }
+    if (c->profiling) cudaEventRecord(c->ev[2], s);
+    for (int lam = 0; lam < 2; ++lam) {
+      const Orient& o = c->og[lam];
+      long sz = (long)o.Px * o.nrow;
+      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog,
+                    od.accg[lam], s);
+      if (e != cudaSuccess) return e;
+    }
+    if (c->profiling) cudaEventRecord(c->ev[3], s);
+    for (int lam = 0; lam < 2; ++lam) {
+      const Orient& o = c->og[lam];
+      if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, s)) != cudaSuccess) return e;
+    }
   }
   if (c->profiling) cudaEventRecord(c->ev[4], s);
   double hs = c->bc == 0 ? 0.5 : -0.5;
-  k_interp_near<T><<<c->n_occ, 256, 0, s>>>(c->debug_mask, c->nfit, c->nm, hs, c->d_cell_start, c->d_node_idx, c->d_samp_gidx,
-                                            c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_blk_start, c->d_blk_r,
-                                            c->d_blk_off, c->d_blk_ph, c->d_C, c->d_MT, c->d_msum, mu, out);
+  size_t smi = (size_t)(c->maxW + 32) * sizeof(zd);
+  cudaFuncSetAttribute(k_interp_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+  k_interp_near<T><<<c->n_items, 256, smi, s>>>(c->debug_mask, c->nfit, c->nm, hs, c->d_cell_start, c->d_node_idx,
+                                              c->d_samp_gidx, c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_cols,
+                                              c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff, c->d_muff,
+                                              c->d_MT, c->d_MTff, c->d_mpart, c->d_mpart_ff, c->mode_chunks, c->d_item_cell,
+                                              c->d_item_lo, c->d_item_hi, mu, out);
   if (c->profiling) cudaEventRecord(c->ev[5], s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<double>(c, c->o64, mu, out); }
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<float>(c, c->o32, mu, out); }
+
+// ------------------------------------------------------------------ CUDA graph of the forward map
+// Argument positions of mu / out in k_project and k_interp_near (kept in step with their signatures).
+static const int kProjArgs = 24, kProjMu = 6;
+static const int kInterpArgs = 28, kInterpMu = 26, kInterpOut = 27;
+
+void destroy_graphs(sgf_ctx* c) {
+  for (auto& gs : c->gs) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    if (gs.g) cudaGraphDestroy(gs.g);
+    gs = GraphSlot();
+  }
+}
+
+// Captures one application (on an internal stream, from the context's staging buffers) and keeps
+// the instantiated graph; returns the capture or instantiation error, in which case the context
+// keeps launching the kernels directly.
+cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
+  GraphSlot& gs = c->gs[prec == 64 ? 0 : 1];
+  cudaStream_t orig = c->stream, cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  const bool prof = c->profiling;
+  const int mask = c->debug_mask;
+  c->profiling = false;
+  c->debug_mask = 15;
+  c->stream = cap;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t ea = prec == 64 ? launch_apply64(c, c->d_mu_tmp, c->d_out_tmp) : launch_apply32(c, c->d_mu_tmp, c->d_out_tmp);
+    cudaError_t ee = cudaStreamEndCapture(cap, &g);
+    e = ea != cudaSuccess ? ea : ee;
+  }
+  c->stream = orig;
+  c->profiling = prof;
+  c->debug_mask = mask;
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e;
+  }
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  void* fp = prec == 64 ? (void*)k_project<double> : (void*)k_project<float>;
+  void* fi = prec == 64 ? (void*)k_interp_near<double> : (void*)k_interp_near<float>;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    cudaGraphNodeGetType(nd, &t);
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    cudaGraphKernelNodeGetParams(nd, &kp);
+    if (kp.func == fp) { gs.n_proj = nd; gs.kp_proj = kp; }
+    if (kp.func == fi) { gs.n_interp = nd; gs.kp_interp = kp; }
+  }
+  if (!gs.n_proj || !gs.n_interp) {
+    cudaGraphDestroy(g);
+    gs = GraphSlot();
+    return cudaErrorInvalidValue;
+  }
+  e = cudaGraphInstantiate(&gs.exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    gs = GraphSlot();
+    return e;
+  }
+  gs.g = g;
+  gs.ok = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out) {
+  GraphSlot& gs = c->gs[prec == 64 ? 0 : 1];
+  void* pa[kProjArgs];
+  void* pb[kInterpArgs];
+  for (int i = 0; i < kProjArgs; ++i) pa[i] = gs.kp_proj.kernelParams[i];
+  for (int i = 0; i < kInterpArgs; ++i) pb[i] = gs.kp_interp.kernelParams[i];
+  pa[kProjMu] = (void*)&mu;
+  pb[kInterpMu] = (void*)&mu;
+  pb[kInterpOut] = (void*)&out;
+  cudaKernelNodeParams p1 = gs.kp_proj, p2 = gs.kp_interp;
+  p1.kernelParams = pa;
+  p1.extra = nullptr;
+  p2.kernelParams = pb;
+  p2.extra = nullptr;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(gs.exec, gs.n_proj, &p1);
+  if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(gs.exec, gs.n_interp, &p2);
+  if (e == cudaSuccess) e = cudaGraphLaunch(gs.exec, c->stream);
+  return e;
+}
 
 // ============================================================== Rayleigh coefficients
 // Block per mode: B_n = dx sum_i mu_i e^{-i(alpha_n x_i + beta_n f_i)} W_i (eq. rayexp with the

@@ -171,11 +171,11 @@ def sgf_rayleigh_noalloc(ctx, mu_ptr, n_lo, n_hi):
 
 
 INFO_KEYS = ["N", "n_occ", "nnz", "PxH", "nrowH", "PyH", "PxV", "nrowV", "PyV", "neq", "nfit", "nb", "nm",
-             "bytes64", "bytes32", "launches"]
+             "bytes64", "bytes32", "launches", "graphs", "maxW", "maxnq", "twlog"]
 
 
 def sgf_info(ctx):
-    v = np.zeros(16)
+    v = np.zeros(20)
     _check(ctx, load().sgf_info(ctx, _dptr(v)))
     return dict(zip(INFO_KEYS, v.tolist()))
 
