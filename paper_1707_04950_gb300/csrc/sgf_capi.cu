@@ -60,11 +60,6 @@ static int ilog2_exact(long n) {
   while ((1L << l) < n) ++l;
   return ((1L << l) == n) ? l : -1;
 }
-static int next_pow2_log(long n) {
-  int l = 0;
-  while ((1L << l) < n) ++l;
-  return l;
-}
 
 extern "C" {
 
@@ -268,10 +263,24 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   H.Px = P.nx * P.p; H.logPx = ilog2_exact(H.Px); H.nrow = P.ny + 1; H.dxg = c->L / P.p; H.dyg = c->L;
   V.Px = P.nx; V.logPx = ilog2_exact(V.Px); V.nrow = P.ny * P.p + 1 + 2 * P.e; V.dxg = c->L; V.dyg = c->L / P.p;
   for (int l = 0; l < 2; ++l) {
-    c->og[l].logPy = next_pow2_log(2L * c->og[l].nrow - 1);
-    c->og[l].Py = 1 << c->og[l].logPy;
+    // smallest 2^a 3^b (b <= 2) holding the linear convolution of nrow rows
+    long need = 2L * c->og[l].nrow - 1, best = 1L << 40;
+    int ba = 0, bb = 0;
+    for (int b = 0; b <= 2; ++b) {
+      long p3 = b == 0 ? 1 : (b == 1 ? 3 : 9);
+      int a = 0;
+      while ((p3 << a) < need) ++a;
+      if ((p3 << a) < best) { best = p3 << a; ba = a; bb = b; }
+    }
+    c->og[l].Py = (int)best;
+    c->og[l].la = ba;
+    c->og[l].lb = bb;
   }
-  c->twlog = std::max(std::max(H.logPx, V.logPx), std::max(H.logPy, V.logPy));
+  c->twlog = std::max(H.logPx, V.logPx);
+  for (int l = 0; l < 2; ++l)
+    if (!conv_y_variant_of(c->og[l], 64) || (c->prm.precision == 32 && !conv_y_variant_of(c->og[l], 32)))
+      return set_err(ctx, SGF_EINVAL, "Y transform of %d points (%d cell rows) exceeds one thread block",
+                     c->og[l].Py, c->og[l].nrow);
   if (V.Py > 16384 || H.Py > 16384 || H.Px > 4096 || V.Px > 4096)
     return set_err(ctx, SGF_EINVAL, "FFT length above the shared-memory limit");
   // shifted poles must stay off the finest grid lag (0, -m h)
@@ -470,6 +479,10 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   TRY(dalloc(ctx, &c->o64.tw, (size_t)1 << c->twlog));
   bool mixed = P.precision == 32;
   if (mixed) TRY(dalloc(ctx, &c->o32.tw, (size_t)1 << c->twlog));
+  for (int lam = 0; lam < 2; ++lam) {
+    TRY(dalloc(ctx, &c->o64.twy[lam], c->og[lam].Py));
+    if (mixed) TRY(dalloc(ctx, &c->o32.twy[lam], c->og[lam].Py));
+  }
   CU(launch_twiddles(c));
   for (int lam = 0; lam < 2; ++lam) {
     long n = (long)c->og[lam].Px * c->og[lam].Py;
@@ -599,8 +612,11 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   for (int lam = 0; lam < 2; ++lam) {
     long sz = 2L * c->og[lam].Px * c->og[lam].nrow;
     TRY(dalloc(ctx, &c->o64.grid[lam], sz));
-    if (c->og[lam].Py > 2048) TRY(dalloc(ctx, &c->o64.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
+    if (conv_y_variant_of(c->og[lam], 64) == 2)
+      TRY(dalloc(ctx, &c->o64.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
     if (mixed) TRY(dalloc(ctx, &c->o32.grid[lam], sz));
+    if (mixed && conv_y_variant_of(c->og[lam], 32) == 2)
+      TRY(dalloc(ctx, &c->o32.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
   }
   if (mixed) {
     TRY(dalloc(ctx, &c->o32.P, (size_t)4 * neq * c->N));

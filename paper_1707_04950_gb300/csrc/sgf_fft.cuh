@@ -4,10 +4,18 @@
 #pragma once
 #include "sgf_common.cuh"
 
-// Radix-R DFT in registers, R in {2, 4, 8}; dir = -1 forward, +1 inverse.
+// Radix-R DFT in registers, R in {2, 3, 4, 8}; dir = -1 forward, +1 inverse.
 template <typename T, int R>
 __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
-  if (R == 2) {
+  if (R == 3) {
+    const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+    cplx<T> t1 = a[1] + a[2], df = a[1] - a[2];
+    cplx<T> t2 = a[0] - (T)0.5 * t1;
+    cplx<T> m = dir < 0 ? cplx<T>(h * df.im, -h * df.re) : cplx<T>(-h * df.im, h * df.re);
+    a[0] = a[0] + t1;
+    a[1] = t2 + m;
+    a[2] = t2 - m;
+  } else if (R == 2) {
     cplx<T> t = a[0];
     a[0] = t + a[1];
     a[1] = t - a[1];
@@ -52,11 +60,11 @@ __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
 // One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es, int batch, int bs,
-                                               const cplx<T>* __restrict__ tw, int twlog, int dir) {
+                                               const cplx<T>* __restrict__ tw, int twlen, int dir) {
   constexpr int U = 16 / R;  // items per thread: every item of the stage is loaded before any store
   const int nR = n / R;
   const int tot = batch * nR;
-  const int tstep = (1 << twlog) / (Ns * R);  // table stride of e^{-2 pi i / (Ns R)}
+  const int tstep = twlen / (Ns * R);  // table stride of e^{-2 pi i / (Ns R)} in a table of twlen
   cplx<T> a[U][R];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -94,60 +102,41 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es
   __syncthreads();
 }
 
-// In-place FFT of `batch` sequences of length n = 2^logn held in shared memory; element i of
-// sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 8 (then 4 or 2 for the
-// remaining factor). tw[k] = e^{-2 pi i k / 2^twlog} over the full circle, twlog >= logn.
-// dir = -1 forward, +1 inverse (unnormalised). All threads of the block must call it.
-// Each stage exchanges through registers in place, so every thread holds all of its items at once:
-// the caller must keep batch * n <= 16 * blockDim.x.
+// In-place FFT of `batch` sequences of length n = 2^la 3^lb held in shared memory; element i of
+// sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 8 (then 4 or 2), then
+// radix 3. tw[k] = e^{-2 pi i k / twlen} over the full circle, n dividing twlen. dir = -1 forward,
+// +1 inverse (unnormalised). All threads of the block must call it. Each stage exchanges through
+// registers in place, so every thread holds all of its items at once: the caller must keep
+// batch * n <= 16 * blockDim.x (<= 15 * blockDim.x when lb > 0).
 template <typename T>
-__device__ void smem_fft(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
-                         int twlog, int dir) {
-  const int n = 1 << logn;
-  int Ns = 1, rem = logn;
+__device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, int bs,
+                          const cplx<T>* __restrict__ tw, int twlen, int dir) {
+  int Ns = 1, rem = la;
   while (rem >= 3) {
-    stockham_stage<T, 8>(s, n, Ns, es, batch, bs, tw, twlog, dir);
+    stockham_stage<T, 8>(s, n, Ns, es, batch, bs, tw, twlen, dir);
     Ns <<= 3;
     rem -= 3;
   }
-  if (rem == 2) stockham_stage<T, 4>(s, n, Ns, es, batch, bs, tw, twlog, dir);
-  if (rem == 1) stockham_stage<T, 2>(s, n, Ns, es, batch, bs, tw, twlog, dir);
-  if (logn == 0) __syncthreads();
+  if (rem == 2) {
+    stockham_stage<T, 4>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    Ns <<= 2;
+  }
+  if (rem == 1) {
+    stockham_stage<T, 2>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    Ns <<= 1;
+  }
+  for (int t = 0; t < lb; ++t) {
+    stockham_stage<T, 3>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    Ns *= 3;
+  }
+  if (n == 1) __syncthreads();
 }
 
-// Reference radix-2 decimation-in-time FFT (bit reversal + butterflies), kept for testing.
+// Power-of-two length 2^logn with a full-circle table of length 2^twlog.
 template <typename T>
-__device__ void smem_fft_radix2(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
-                                int twlog, int dir) {
-  const int n = 1 << logn;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < batch * n; idx += nt) {
-    int b = idx >> logn, i = idx & (n - 1);
-    int r = (int)(__brev((unsigned)i) >> (32 - logn));
-    if (r > i) {
-      cplx<T> t = s[b * bs + i * es];
-      s[b * bs + i * es] = s[b * bs + r * es];
-      s[b * bs + r * es] = t;
-    }
-  }
-  __syncthreads();
-  const int halfn = n >> 1;
-  for (int st = 1; st <= logn; ++st) {
-    const int half = 1 << (st - 1);
-    for (int idx = tid; idx < batch * halfn; idx += nt) {
-      int b = idx / halfn, kk = idx - b * halfn;
-      int j = kk & (half - 1);
-      int i0 = ((kk >> (st - 1)) << st) + j;
-      int i1 = i0 + half;
-      cplx<T> w = tw[j << (twlog - st)];
-      if (dir > 0) w.im = -w.im;
-      cplx<T> a = s[b * bs + i0 * es];
-      cplx<T> c = s[b * bs + i1 * es] * w;
-      s[b * bs + i0 * es] = a + c;
-      s[b * bs + i1 * es] = a - c;
-    }
-    __syncthreads();
-  }
+__device__ void smem_fft(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
+                         int twlog, int dir) {
+  smem_fftn<T>(s, 1 << logn, logn, 0, es, batch, bs, tw, 1 << twlog, dir);
 }
 
 // FFT along X (the strided dimension) of arrays laid out g[ix * nrow + iy], ix < Px = 2^logPx,
@@ -177,17 +166,17 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
   }
 }
 
-// Forward FFT along Y (contiguous) of rows g[kx * Py + ...], in place, one block per kx.
+// FFT along Y (contiguous) of rows g[kx * Py + ...], Py = 2^la 3^lb, in place, one block per kx;
+// twy: full-circle table of length Py.
 template <typename T>
-__global__ void k_fft_y_full(cplx<T>* __restrict__ g, int logPy, const cplx<T>* __restrict__ tw, int twlog,
+__global__ void __launch_bounds__(1024) k_fft_y_full(cplx<T>* __restrict__ g, int Py, int la, int lb, const cplx<T>* __restrict__ twy,
                              int dir) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int Py = 1 << logPy;
   cplx<T>* a = g + (long)blockIdx.x * Py;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = a[i];
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, tw, twlog, dir);
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twy, Py, dir);
   for (int i = threadIdx.x; i < Py; i += blockDim.x) a[i] = s[i];
 }
 
@@ -197,23 +186,21 @@ __global__ void k_fft_y_full(cplx<T>* __restrict__ g, int logPy, const cplx<T>* 
 // K* hold the Py-point spectra per kx, already scaled by 1/(Px Py).
 template <typename T, int MAXR, bool ACCG>
 __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ zeta,
-                         const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int logPy, int nrow,
-                         const cplx<T>* __restrict__ tw, int twlog, cplx<T>* __restrict__ accg) {
-  // ACCG: the partial product K_m FFT(xi) waits in a global scratch column (used when registers
-  // cannot hold it next to the FFT's own values); otherwise it stays in registers.
+                         const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int Py, int la, int lb,
+                         int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg) {
+  // Py = 2^la 3^lb; twy: full-circle table of length Py. ACCG: the partial product K_m FFT(xi) waits
+  // in a global scratch column (when shared memory cannot hold a twiddle table next to the column
+  // and registers cannot hold the product next to the FFT's own values); otherwise it stays in
+  // registers and the twiddles are staged in shared memory.
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int Py = 1 << logPy;
   const long kx = blockIdx.x;
   cplx<T> acc[ACCG ? 1 : MAXR];
-  // twiddles of this length in shared memory after the column (when there is room: !ACCG)
-  const cplx<T>* twf = tw;
-  int twl = twlog;
+  const cplx<T>* twf = twy;
   if (!ACCG) {
     cplx<T>* tws = s + Py;
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = tw[i << (twlog - logPy)];
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
     twf = tws;
-    twl = logPy;
   }
   cplx<T>* col = xi + kx * nrow;
   const cplx<T>* colz = zeta + kx * nrow;
@@ -222,7 +209,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, -1);
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) ag[i] = s[i] * km[i];
   } else {
@@ -235,7 +222,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   __syncthreads();
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, -1);
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = s[i] * kd[i] + ag[i];
   } else {
@@ -246,6 +233,6 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
     }
   }
   __syncthreads();
-  smem_fft<T>(s, logPy, 1, 1, 0, twf, twl, +1);
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
 }

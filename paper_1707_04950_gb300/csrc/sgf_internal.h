@@ -13,7 +13,7 @@
 // Geometry of one equivalent-source grid Pi_lambda^per (Section 5.4): X cyclic with Px points,
 // nrow rows in Y; FFT length Py >= 2 nrow - 1 in Y (linear convolution).
 struct Orient {
-  int Px, logPx, nrow, Py, logPy;
+  int Px, logPx, nrow, Py, la, lb;  // Py = 2^la 3^lb >= 2 nrow - 1
   double dxg, dyg;
 };
 
@@ -25,7 +25,8 @@ struct OpData {
   cplx<T>* src_tw = nullptr;   // [n_occ][2][neq] twist e^{-i alpha x_src} of the scatter
   cplx<T>* Khat[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [lam][mono, dip] spectra / (Px Py)
   cplx<T>* grid[2] = {nullptr, nullptr};                          // [lam]: xi then zeta, Px*nrow each
-  cplx<T>* tw = nullptr;       // FFT twiddles e^{-2 pi i k / 2^twlog}, full circle
+  cplx<T>* tw = nullptr;       // FFT twiddles e^{-2 pi i k / 2^twlog}, full circle (X passes)
+  cplx<T>* twy[2] = {nullptr, nullptr};  // [lam] full-circle twiddles of length Py (Y passes)
   cplx<T>* accg[2] = {nullptr, nullptr};  // [lam] Y-convolution scratch [Px][Py] (FP64, long columns)
 };
 
@@ -144,6 +145,8 @@ cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out);
 void destroy_graphs(sgf_ctx* c);
 cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B);
 cudaError_t launch_twiddles(sgf_ctx* c);
+// which Y-convolution kernel serves this orientation: 1 registers, 2 global scratch, 0 none fits
+int conv_y_variant_of(const Orient& o, int precision);
 cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);
 // Krylov helpers
 cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,

@@ -499,6 +499,12 @@ static int fftx_ty(int Px, int nrow, size_t esz) {
   if (ty < 1) ty = 1;
   return ty;
 }
+// threads for one contiguous FFT of length Py: at most 15 values per thread, a multiple of 32
+static int conv_threads(int Py) {
+  int t = (Py + 14) / 15;
+  t = (t + 31) / 32 * 32;
+  return t < 64 ? 64 : t;
+}
 static int fftx_threads(int Px, int ty) {
   int t = Px * ty / 16;
   if (t < 64) t = 64;
@@ -548,8 +554,9 @@ cudaError_t launch_tables(sgf_ctx* c) {
     cudaMemcpyAsync(Tld, Txd, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
     size_t sm = (size_t)o.Py * sizeof(zd);
     cudaFuncSetAttribute(k_fft_y_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_fft_y_full<double><<<o.Px, 512, sm, c->stream>>>(Tlm, o.logPy, c->o64.tw, c->twlog, -1);
-    k_fft_y_full<double><<<o.Px, 512, sm, c->stream>>>(Tld, o.logPy, c->o64.tw, c->twlog, -1);
+    int ty_threads = conv_threads(o.Py);
+    k_fft_y_full<double><<<o.Px, ty_threads, sm, c->stream>>>(Tlm, o.Py, o.la, o.lb, c->o64.twy[lam], -1);
+    k_fft_y_full<double><<<o.Px, ty_threads, sm, c->stream>>>(Tld, o.Py, o.la, o.lb, c->o64.twy[lam], -1);
     double sc = 1.0 / ((double)o.Px * o.Py);
     k_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Tlm, n, sc);
     k_scale<<<ceil_div(n, 256), 256, 0, c->stream>>>(Tld, n, sc);
@@ -562,10 +569,23 @@ cudaError_t launch_tables(sgf_ctx* c) {
   return cudaGetLastError();
 }
 
+__global__ void k_twiddles_n(zd* tw, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sn, cs;
+  sincospi(-2.0 * i / n, &sn, &cs);
+  tw[i] = zd(cs, sn);
+}
+
 cudaError_t launch_twiddles(sgf_ctx* c) {
   int n = 1 << c->twlog;
   k_twiddles<<<ceil_div(n, 256), 256, 0, c->stream>>>(c->o64.tw, c->twlog);
   if (c->o32.tw) launch_to_f32(c->o64.tw, c->o32.tw, n, c->stream);
+  for (int lam = 0; lam < 2; ++lam) {
+    int py = c->og[lam].Py;
+    k_twiddles_n<<<ceil_div(py, 256), 256, 0, c->stream>>>(c->o64.twy[lam], py);
+    if (c->o32.twy[lam]) launch_to_f32(c->o64.twy[lam], c->o32.twy[lam], py, c->stream);
+  }
   return cudaGetLastError();
 }
 
@@ -997,21 +1017,45 @@ __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, con
   }
 }
 
+// Y convolution launch: at most 15 FFT values per thread (radix-3 stages), at least 64 threads.
+// The partial product K_m FFT(xi) stays in registers, with the twiddle table staged in shared
+// memory next to the column, when both fit (FP64 columns up to 6144 points); otherwise it goes to
+// the global scratch `accg` ([Px][Py]). Returns 0 (and launches nothing) when neither fits.
+template <typename T>
+static int conv_y_variant(const Orient& o) {
+  int threads = conv_threads(o.Py);
+  if (threads > 1024) return 0;
+  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  cudaFuncAttributes fa;
+  if (2 * sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, k_conv_y<T, 16, false>) == cudaSuccess &&
+      (long)fa.numRegs * threads <= 65536)
+    return 1;
+  if (sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, k_conv_y<T, 16, true>) == cudaSuccess &&
+      (long)fa.numRegs * threads <= 65536)
+    return 2;
+  return 0;
+}
+
+int conv_y_variant_of(const Orient& o, int precision) {
+  return precision == 64 ? conv_y_variant<double>(o) : conv_y_variant<float>(o);
+}
+
 template <typename T>
 static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
-                          const cplx<T>* tw, int twlog, cplx<T>* accg, cudaStream_t s) {
-  int threads = o.Py / 16;
-  if (threads < 64) threads = 64;
-  if (threads > 1024) return cudaErrorInvalidValue;
+                          const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
+  int threads = conv_threads(o.Py);
   size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  if (sizeof(T) == 8 && o.Py > 2048) {  // no room for a twiddle table: global twiddles
+  int v = conv_y_variant<T>(o);
+  if (v == 2) {
     if (!accg) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(k_conv_y<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog, accg);
-  } else {
+    k_conv_y<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
+  } else if (v == 1) {
     sm *= 2;  // column + twiddle table
     cudaFuncSetAttribute(k_conv_y<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.logPy, o.nrow, tw, twlog, nullptr);
+    k_conv_y<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, nullptr);
+  } else {
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -1040,7 +1084,7 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
       cudaStream_t st = lam == 0 ? s : c->side;
       long sz = (long)o.Px * o.nrow;
       if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, st)) != cudaSuccess) return e;
-      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog,
+      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.twy[lam],
                     od.accg[lam], st);
       if (e != cudaSuccess) return e;
       if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, st)) != cudaSuccess) return e;
@@ -1056,7 +1100,7 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
     for (int lam = 0; lam < 2; ++lam) {
       const Orient& o = c->og[lam];
       long sz = (long)o.Px * o.nrow;
-      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.tw, c->twlog,
+      e = conv_y<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.twy[lam],
                     od.accg[lam], s);
       if (e != cudaSuccess) return e;
     }
