@@ -255,6 +255,8 @@ class Accel:
 
     # ------------------------------------------------------------------ Algorithm 3
     def apply(self, mu, return_stages=False):
+        """Algorithm 3 on one density mu [N] or on a block of columns mu [N, R] (column by column;
+        every step is linear in mu)."""
         par = self.par
         k, d, j, h, al = self.k, self.d, self.j, self.h, self.alpha
         N = self.N
@@ -286,7 +288,7 @@ class Accel:
                     wrap = ixr // Px
                     ph = np.exp(-1j * al * d * wrap)
                     key = (ixr - wrap * Px, iy)
-                    a = merged[lam].setdefault(key, np.zeros(2, complex))
+                    a = merged[lam].setdefault(key, np.zeros((2,) + mu.shape[1:], complex))
                     a[0] += v[t] * ph
                     a[1] += v[self.neq + t] * ph
 
@@ -313,7 +315,7 @@ class Accel:
                 for t in ts:
                     six, siy = sample_grid(q, t)
                     km, kd = self.kernel(lam, six - gx_, siy - gy_)
-                    phi_all[(q, t)] = np.sum(km * xi + kd * ze)
+                    phi_all[(q, t)] = km @ xi + kd @ ze
         st["phi_all"] = phi_all
 
         # LocalEqSMerge + LocalFFT (eqs. sum_eqsources_local, small_convolution_grid): phi^int
@@ -324,7 +326,7 @@ class Accel:
             for t in range(len(self.samp_ori)):
                 lam = self.samp_ori[t]
                 x_t = self.samp_rel[t] + self.corner(*q)
-                acc = 0j
+                acc = np.zeros(mu.shape[1:], complex)
                 for (cxr, cyr) in loc:
                     ref = cxr % self.nx
                     wrap = (cxr - ref) // self.nx
@@ -343,11 +345,11 @@ class Accel:
                         Gv[same], ax[same], ay[same] = g1, b1, b2
                     nu = self.nu[lam]
                     dG = -(nu[0] * ax + nu[1] * ay)
-                    acc += np.sum(Gv * v[:self.neq] + dG * v[self.neq:])
+                    acc = acc + Gv @ v[:self.neq] + dG @ v[self.neq:]
                 phi_int[(q, t)] = acc
         st["phi_int"] = phi_int
 
-        out = np.zeros(N, complex)
+        out = np.zeros(mu.shape, complex)
         ctr = np.array([self.L / 2, self.L / 2])
         for q in self.cells:
             idx = np.array(self.cell_nodes[q])
@@ -364,7 +366,7 @@ class Accel:
                 Bn = self.fb_basis(rel, nuh)
             psi_ni = Bn @ wq
             # Intersecting (eq. final_correction_0): exact sum over nodes of the local cells
-            psi_int = np.zeros(len(idx), complex)
+            psi_int = np.zeros((len(idx),) + mu.shape[1:], complex)
             for (cxr, cyr) in self.local_cells(q):
                 ref = cxr % self.nx
                 wrap = (cxr - ref) // self.nx
@@ -387,8 +389,8 @@ class Accel:
 
         # EvalSingular (eq. local_mat), EvalModes (eq. D_M_deltax), AddOperators (eq. discrete_eq)
         r_, c_, v_ = self.sing
-        sing = np.zeros(N, complex)
-        np.add.at(sing, r_, v_ * mu[c_])
+        sing = np.zeros(mu.shape, complex)
+        np.add.at(sing, r_, v_.reshape((-1,) + (1,) * (mu.ndim - 1)) * mu[c_])
         T, S = self.modes
         modes = T @ (S @ mu)
         sigma = 0.5 if self.bc == 0 else -0.5
@@ -397,3 +399,14 @@ class Accel:
             st["sing"], st["modes"] = sing, modes
             return y, st
         return y
+
+    def matrix(self):
+        """The accelerated operator as a dense N x N matrix: Algorithm 3 applied to the identity."""
+        return self.apply(np.eye(self.N, dtype=complex))
+
+    def apply_adjoint(self, v, A=None):
+        """The adjoint (conjugate transpose) of the accelerated operator applied to v [N] or [N, R]:
+        plain definition, from the dense matrix (pass A = matrix() to reuse it)."""
+        if A is None:
+            A = self.matrix()
+        return A.conj().T @ np.asarray(v, complex)
