@@ -81,9 +81,14 @@ sgf_status sgf_set_params(sgf_ctx* ctx, const sgf_params* p);
  * subtraction folded in) and the mode factors of eq. D_M_deltax. Synchronises the stream. */
 sgf_status sgf_build_operator(sgf_ctx* ctx);
 
-/* Algorithm 3: out = (sigma/2 I + D^dx) mu for nrhs right-hand sides stored one after another
- * (column stride N). sigma = +1 Dirichlet, -1 Neumann. mu_dev/out_dev: device complex128.
- * transpose_conj must be 0 (the adjoint is not available). Enqueued on the context stream. */
+/* Algorithm 3: out = A mu, A = (sigma/2 I + D^dx) in its accelerated form, for nrhs right-hand
+ * sides stored one after another (column stride N). sigma = +1 Dirichlet, -1 Neumann.
+ * transpose_conj = 1 applies the conjugate transpose A^H instead: the stages of Algorithm 3 run
+ * backwards (reconstruction and sample gather transposed, grid convolution with conjugated spectra,
+ * scatter and projection transposed, near-field blocks, mode factors conjugate-transposed), in
+ * the same precision as the forward map. mu_dev/out_dev: device complex128, not overlapping.
+ * Enqueued on the context stream. SGF_EINVAL for transpose_conj outside {0, 1}, or when the
+ * adjoint near-field rows exceed the shared-memory limit (then only the forward map exists). */
 sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj);
 
 /* Same as sgf_apply with HOST complex128 buffers: copies mu to the device, applies, copies back,
@@ -98,6 +103,12 @@ sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev);
  * GMRES solves on the mixed operator. Writes the solution to mu_dev; *iters = operator
  * applications, *relres = final ||b - A mu|| / ||b|| with the FP64 operator. Synchronises. */
 sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres);
+
+/* Algorithm 1 on a caller's right-hand side: GMRES (as in sgf_solve, same precision handling) on
+ * A x = rhs (transpose_conj = 0) or A^H x = rhs (transpose_conj = 1, the adjoint system of a
+ * gradient computation). rhs_dev, x_dev: device complex128 of length N. Synchronises. */
+sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int transpose_conj, double tol, int maxit, void* x_dev,
+                         int* iters, double* relres);
 
 /* Rayleigh coefficients B_n for n = n_lo..n_hi (eq. rayexp) from the solution mu (device), into
  * host B[2*(n_hi-n_lo+1)] (interleaved complex); host eff[n_hi-n_lo+1] gets e_n = beta_n/beta |B_n|^2

@@ -278,7 +278,8 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   }
   c->twlog = std::max(H.logPx, V.logPx);
   for (int l = 0; l < 2; ++l)
-    if (!conv_y_variant_of(c->og[l], 64) || (c->prm.precision == 32 && !conv_y_variant_of(c->og[l], 32)))
+    if (!conv_y_variant_of(c->og[l], 64) || (c->prm.precision == 32 && !conv_y_variant_of(c->og[l], 32)) ||
+        !conv_y_variant_of(c->og[l], 64, true) || (c->prm.precision == 32 && !conv_y_variant_of(c->og[l], 32, true)))
       return set_err(ctx, SGF_EINVAL, "Y transform of %d points (%d cell rows) exceeds one thread block",
                      c->og[l].Py, c->og[l].nrow);
   if (V.Py > 16384 || H.Py > 16384 || H.Px > 4096 || V.Px > 4096)
@@ -589,6 +590,56 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(launch_phi_off(c, d_phi, dcy_min, n_dcy, d_samp_rel, d_src_rel));
   CU(launch_near(c, d_phi, dcy_min, n_dcy, d_Iplain, pp, d_kress));
 
+  // ---------------- adjoint near layout: the rows of cell r collect conj(C) of every block (q, r),
+  // blocks in block order, so each adjoint row is again one contiguous stream
+  {
+    std::vector<std::vector<int>> byr(c->n_occ);
+    for (int b = 0; b < c->n_blk; ++b) byr[pr[b]].push_back(b);
+    std::vector<long> cell_offT(c->n_occ + 1, 0), dst_off(c->n_blk, 0);
+    std::vector<int> cellWT(c->n_occ, 0), dst_ld(c->n_blk, 0), colsT, coloffT(c->n_occ + 1, 0);
+    long offT = 0;
+    int maxWT = 0;
+    for (int r = 0; r < c->n_occ; ++r) {
+      cell_offT[r] = offT;
+      coloffT[r] = (int)colsT.size();
+      int W = 0;
+      for (int b : byr[r]) {
+        dst_off[b] = offT + W;
+        int q = pq[b];
+        for (int l = c->cell_start[q]; l < c->cell_start[q + 1]; ++l) colsT.push_back(c->node_idx[l]);
+        W += c->cell_start[q + 1] - c->cell_start[q];
+      }
+      for (int b : byr[r]) dst_ld[b] = W;
+      cellWT[r] = W;
+      maxWT = std::max(maxWT, W);
+      offT += (long)(c->cell_start[r + 1] - c->cell_start[r]) * W;
+    }
+    cell_offT[c->n_occ] = offT;
+    coloffT[c->n_occ] = (int)colsT.size();
+    if (offT != c->nnz) return set_err(ctx, SGF_EINVAL, "adjoint near layout holds %ld of %ld entries", offT, c->nnz);
+    c->maxWT = maxWT;
+    c->adj_ok = (size_t)(maxWT + 32 + 4 * neq) * sizeof(zd) <= 200 * 1024;
+    if (c->adj_ok) {
+      long* d_dst_off;
+      int* d_dst_ld;
+      TRY(dalloc(ctx, &d_dst_off, c->n_blk));
+      TRY(dalloc(ctx, &d_dst_ld, c->n_blk));
+      CU(cudaMemcpy(d_dst_off, dst_off.data(), c->n_blk * sizeof(long), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(d_dst_ld, dst_ld.data(), c->n_blk * sizeof(int), cudaMemcpyHostToDevice));
+      TRY(dalloc(ctx, &c->d_cell_offT, c->n_occ + 1));
+      TRY(dalloc(ctx, &c->d_cell_WT, c->n_occ));
+      TRY(dalloc(ctx, &c->d_colsT, colsT.size()));
+      TRY(dalloc(ctx, &c->d_coloffT, c->n_occ + 1));
+      CU(cudaMemcpy(c->d_cell_offT, cell_offT.data(), (c->n_occ + 1) * sizeof(long), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(c->d_cell_WT, cellWT.data(), c->n_occ * sizeof(int), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(c->d_colsT, colsT.data(), colsT.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(c->d_coloffT, coloffT.data(), (c->n_occ + 1) * sizeof(int), cudaMemcpyHostToDevice));
+      TRY(dalloc(ctx, &c->d_CT, c->nnz));
+      CU(launch_near_transpose(c->n_blk, pp.q, pp.r, pp.off, pp.ld, d_dst_off, d_dst_ld, c->d_cell_start, c->d_C,
+                               c->d_CT, c->stream));
+    }
+  }
+
   // ---------------- modes
   std::vector<int> ue = ueta_set(c);
   c->nm = (int)ue.size();
@@ -604,6 +655,10 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   TRY(dalloc(ctx, &c->d_MT, (size_t)c->N * std::max(1, c->nm)));
   TRY(dalloc(ctx, &c->d_MS, (size_t)c->N * std::max(1, c->nm)));
   CU(launch_modes(c, d_mn));
+  TRY(dalloc(ctx, &c->d_MTh, (size_t)c->N * std::max(1, c->nm)));
+  TRY(dalloc(ctx, &c->d_MSh, (size_t)c->N * std::max(1, c->nm)));
+  CU(launch_conj_transpose(c->d_MT, c->N, c->nm, c->d_MTh, c->stream));
+  CU(launch_conj_transpose(c->d_MS, c->nm, c->N, c->d_MSh, c->stream));
   if (c->nm > 8) return set_err(ctx, SGF_EINVAL, "%d completion modes (at most 8 supported)", c->nm);
   TRY(dalloc(ctx, &c->d_mpart, (size_t)std::max(1, c->nm) * c->mode_chunks));
   TRY(dalloc(ctx, &c->d_mpart_ff, (size_t)std::max(1, c->nm) * c->mode_chunks));
@@ -612,10 +667,10 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   for (int lam = 0; lam < 2; ++lam) {
     long sz = 2L * c->og[lam].Px * c->og[lam].nrow;
     TRY(dalloc(ctx, &c->o64.grid[lam], sz));
-    if (conv_y_variant_of(c->og[lam], 64) == 2)
+    if (conv_y_variant_of(c->og[lam], 64) == 2 || conv_y_variant_of(c->og[lam], 64, true) == 2)
       TRY(dalloc(ctx, &c->o64.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
     if (mixed) TRY(dalloc(ctx, &c->o32.grid[lam], sz));
-    if (mixed && conv_y_variant_of(c->og[lam], 32) == 2)
+    if (mixed && (conv_y_variant_of(c->og[lam], 32) == 2 || conv_y_variant_of(c->og[lam], 32, true) == 2))
       TRY(dalloc(ctx, &c->o32.accg[lam], (size_t)c->og[lam].Px * c->og[lam].Py));
   }
   if (mixed) {
@@ -632,6 +687,14 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     TRY(dalloc(ctx, &c->d_MSff, (size_t)c->N * std::max(1, c->nm)));
     CU(launch_split_ff(c->d_MT, c->d_MTff, (long)c->N * c->nm, c->stream));
     CU(launch_split_ff(c->d_MS, c->d_MSff, (long)c->N * c->nm, c->stream));
+    TRY(dalloc(ctx, &c->d_MThff, (size_t)c->N * std::max(1, c->nm)));
+    TRY(dalloc(ctx, &c->d_MShff, (size_t)c->N * std::max(1, c->nm)));
+    CU(launch_split_ff(c->d_MTh, c->d_MThff, (long)c->N * c->nm, c->stream));
+    CU(launch_split_ff(c->d_MSh, c->d_MShff, (long)c->N * c->nm, c->stream));
+    if (c->adj_ok) {
+      TRY(dalloc(ctx, &c->d_CTff, c->nnz));
+      CU(launch_split_ff(c->d_CT, c->d_CTff, c->nnz, c->stream));
+    }
   }
   TRY(dalloc(ctx, &c->d_mu_tmp, (size_t)c->N * 2));
   TRY(dalloc(ctx, &c->d_out_tmp, (size_t)c->N * 2));
@@ -670,17 +733,27 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
 
 static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec);
 
+static sgf_status apply_adj_prec(sgf_ctx* ctx, const zd* v, zd* out, int prec) {
+  if (!ctx->adj_ok)
+    return set_err(ctx, SGF_EINVAL, "adjoint near rows of %d columns exceed the shared-memory limit", ctx->maxWT);
+  cudaError_t e = prec == 64 ? launch_apply_adj64(ctx, v, out) : launch_apply_adj32(ctx, v, out);
+  if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "adjoint apply: %s", cudaGetErrorString(e));
+  return SGF_OK;
+}
+
 extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj) {
   if (!ctx) return SGF_EINVAL;
   if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
-  if (transpose_conj) return set_err(ctx, SGF_EINVAL, "adjoint application is not available");
+  if (transpose_conj != 0 && transpose_conj != 1) return set_err(ctx, SGF_EINVAL, "transpose_conj must be 0 or 1");
   if (nrhs < 1 || !mu_dev || !out_dev) return set_err(ctx, SGF_EINVAL, "bad apply arguments");
   for (int r = 0; r < nrhs; ++r) {
     const zd* mu = (const zd*)mu_dev + (size_t)r * ctx->N;
     zd* out = (zd*)out_dev + (size_t)r * ctx->N;
-    sgf_status st = apply_prec(ctx, mu, out, ctx->prm.precision);
+    sgf_status st = transpose_conj ? apply_adj_prec(ctx, mu, out, ctx->prm.precision)
+                                   : apply_prec(ctx, mu, out, ctx->prm.precision);
     if (st != SGF_OK) return st;
   }
+  if (transpose_conj) return SGF_OK;
   if (ctx->profiling) {
     cudaEventSynchronize(ctx->ev[5]);
     float ms;
@@ -740,8 +813,12 @@ static sgf_status dot_host(sgf_ctx* ctx, Krylov& K, const zd* V, int m, const zd
 }
 
 // Solves A x = b from x = 0 with operator precision prec; returns applications in *its.
-static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, double tol, int maxit, int* its,
-                        double* relres) {
+static sgf_status apply_op(sgf_ctx* ctx, const zd* x, zd* out, int prec, bool adj) {
+  return adj ? apply_adj_prec(ctx, x, out, prec) : apply_prec(ctx, x, out, prec);
+}
+
+static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b, zd* x, double tol, int maxit,
+                        int* its, double* relres) {
   const long N = ctx->N;
   const int m = K.m;
   std::vector<cd> tmp;
@@ -754,7 +831,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, d
   std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (total < maxit) {
     // r = b - A x
-    TRY(apply_prec(ctx, x, K.r, prec));
+    TRY(apply_op(ctx, x, K.r, prec, adj));
     CU(launch_axpby(K.r, zd(1, 0), b, zd(-1, 0), N, ctx->stream));
     TRY(dot_host(ctx, K, K.r, 1, K.r, tmp));
     double beta = std::sqrt(tmp[0].real());
@@ -768,7 +845,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, d
     for (int jj = 0; jj < m && total < maxit; ++jj) {
       zd* vj = K.V + (size_t)jj * N;
       zd* w = K.V + (size_t)(jj + 1) * N;
-      TRY(apply_prec(ctx, vj, w, prec));
+      TRY(apply_op(ctx, vj, w, prec, adj));
       ++total;
       std::vector<cd> h1, h2;
       TRY(dot_host(ctx, K, K.V, jj + 1, w, h1));
@@ -819,7 +896,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, d
     if (res / bn <= tol) break;
   }
   // true residual
-  TRY(apply_prec(ctx, x, K.r, prec));
+  TRY(apply_op(ctx, x, K.r, prec, adj));
   CU(launch_axpby(K.r, zd(1, 0), b, zd(-1, 0), N, ctx->stream));
   TRY(dot_host(ctx, K, K.r, 1, K.r, tmp));
   *relres = std::sqrt(tmp[0].real()) / bn;
@@ -827,10 +904,13 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, const zd* b, zd* x, d
   return SGF_OK;
 }
 
-extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres) {
+// GMRES on A x = b (adj: A^H x = b); b = nullptr takes the right-hand side of sgf_rhs.
+static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol, int maxit, void* x_dev, int* iters,
+                             double* relres) {
   if (!ctx) return SGF_EINVAL;
   if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
-  if (!(tol > 0) || maxit < 1 || !mu_dev) return set_err(ctx, SGF_EINVAL, "bad solve arguments");
+  if (!(tol > 0) || maxit < 1 || !x_dev) return set_err(ctx, SGF_EINVAL, "bad solve arguments");
+  if (adj && !ctx->adj_ok) return apply_adj_prec(ctx, nullptr, nullptr, 64);
   const long N = ctx->N;
   Krylov K;
   K.m = std::min(200, maxit);
@@ -850,9 +930,12 @@ extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_de
   }
   int its = 0;
   double rr = 1;
-  launch_rhs(ctx, b);
+  if (b_in)
+    cudaMemcpyAsync(b, b_in, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
+  else
+    launch_rhs(ctx, b);
   if (ctx->prm.precision == 64) {
-    st = gmres(ctx, K, 64, b, x, tol, maxit, &its, &rr);
+    st = gmres(ctx, K, 64, adj, b, x, tol, maxit, &its, &rr);
   } else {
     // FP64 residual refinement around inner mixed-precision GMRES solves
     std::vector<cd> tmp;
@@ -863,14 +946,15 @@ extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_de
     zd* r = nullptr;
     if (st == SGF_OK) st = al(&r, N);
     if (st == SGF_OK) cudaMemcpyAsync(r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
-    for (int outer = 0; outer < 30 && st == SGF_OK; ++outer) {
+    if (st == SGF_OK && bn == 0) rr = 0;
+    for (int outer = 0; outer < 30 && st == SGF_OK && bn > 0; ++outer) {
       int it_in = 0;
       double rr_in = 1;
-      st = gmres(ctx, K, 32, r, dlt, 1e-6, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in);
+      st = gmres(ctx, K, 32, adj, r, dlt, 1e-6, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in);
       if (st != SGF_OK) break;
       its += it_in;
       launch_axpby(x, zd(1, 0), dlt, zd(1, 0), N, ctx->stream);
-      st = apply_prec(ctx, x, r, 64);
+      st = apply_op(ctx, x, r, 64, adj);
       ++its;
       if (st != SGF_OK) break;
       launch_axpby(r, zd(1, 0), b, zd(-1, 0), N, ctx->stream);
@@ -880,7 +964,7 @@ extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_de
     }
   }
   if (st == SGF_OK) {
-    cudaMemcpyAsync(mu_dev, x, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(x_dev, x, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
   }
   for (void* p : mine) cudaFree(p);
@@ -889,6 +973,18 @@ extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_de
   if (st != SGF_OK) return st;
   if (!(rr <= tol)) return set_err(ctx, SGF_ENOCONV, "GMRES stopped at relative residual %g after %d applications", rr, its);
   return SGF_OK;
+}
+
+extern "C" sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres) {
+  return solve_impl(ctx, nullptr, false, tol, maxit, mu_dev, iters, relres);
+}
+
+extern "C" sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int transpose_conj, double tol, int maxit,
+                                    void* x_dev, int* iters, double* relres) {
+  if (!ctx) return SGF_EINVAL;
+  if (!rhs_dev || (transpose_conj != 0 && transpose_conj != 1))
+    return set_err(ctx, SGF_EINVAL, "bad solve arguments");
+  return solve_impl(ctx, (const zd*)rhs_dev, transpose_conj == 1, tol, maxit, x_dev, iters, relres);
 }
 
 extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,

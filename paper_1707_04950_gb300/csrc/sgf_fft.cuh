@@ -236,3 +236,66 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
 }
+
+// Adjoint of k_conv_y (one block per kx). The forward column map is xi, zeta -> restrict(IFFT(Km
+// FFT(pad xi) + Kd FFT(pad zeta))), with the inverse transform unnormalised and 1/(Px Py) inside K*;
+// its adjoint takes phi (in xi, nrow rows) to
+//   xi   <- restrict(IFFT(conj(Km) . FFT(pad phi))),   zeta <- restrict(IFFT(conj(Kd) . FFT(pad phi)))
+// (the adjoint of zero padding is restriction and the adjoint of the unnormalised inverse DFT is
+// the forward DFT). FFT(pad phi) waits in registers, or in the global scratch column accg when
+// ACCG, between the two inverse transforms.
+template <typename T, int MAXR, bool ACCG>
+__global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zeta,
+                             const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int Py, int la, int lb,
+                             int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
+  const long kx = blockIdx.x;
+  cplx<T> acc[ACCG ? 1 : MAXR];
+  const cplx<T>* twf = twy;
+  if (!ACCG) {
+    cplx<T>* tws = s + Py;
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
+    twf = tws;
+  }
+  cplx<T>* col = xi + kx * nrow;
+  cplx<T>* colz = zeta + kx * nrow;
+  const cplx<T>* km = Km + kx * Py;
+  const cplx<T>* kd = Kd + kx * Py;
+  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
+  __syncthreads();
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
+  if (ACCG) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) {
+      cplx<T> v = s[i];
+      ag[i] = v;
+      s[i] = mulc(v, km[i]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      int i = threadIdx.x + r * blockDim.x;
+      if (i < Py) {
+        acc[ACCG ? 0 : r] = s[i];
+        s[i] = mulc(acc[ACCG ? 0 : r], km[i]);
+      }
+    }
+  }
+  __syncthreads();
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
+  __syncthreads();
+  if (ACCG) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = mulc(ag[i], kd[i]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      int i = threadIdx.x + r * blockDim.x;
+      if (i < Py) s[i] = mulc(acc[ACCG ? 0 : r], kd[i]);
+    }
+  }
+  __syncthreads();
+  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) colz[i] = s[i];
+}

@@ -79,6 +79,13 @@ struct sgf_ctx {
   int* d_cols = nullptr;       // node index of each local column, cells in order
   int* d_coloff = nullptr;     // [n_occ + 1] offsets into d_cols
   int maxW = 0;
+  // adjoint near field: rows of each cell r hold conj(C) of the blocks (q, r), W^T_r columns
+  zd* d_CT = nullptr;
+  float4* d_CTff = nullptr;
+  long* d_cell_offT = nullptr;
+  int *d_cell_WT = nullptr, *d_colsT = nullptr, *d_coloffT = nullptr;
+  int maxWT = 0;
+  bool adj_ok = false;
   zd* d_blk_ph = nullptr;      // quasi-periodic phase of the source cell copy
   zd* d_C = nullptr;
   float4* d_Cff = nullptr;      // near operator as float-float pairs (mixed path)
@@ -86,6 +93,8 @@ struct sgf_ctx {
   // modes
   zd *d_MT = nullptr, *d_MS = nullptr, *d_msum = nullptr;
   float4 *d_MTff = nullptr, *d_MSff = nullptr;  // float-float mode factors (mixed path)
+  zd *d_MTh = nullptr, *d_MSh = nullptr;        // adjoint mode factors: MTh[n][i], MSh[i][n]
+  float4 *d_MThff = nullptr, *d_MShff = nullptr;
   zd* d_mpart = nullptr;        // [nm][mode_chunks] FP64 mode-sum partials
   float4* d_mpart_ff = nullptr; // [nm][mode_chunks] float-float partials
   int mode_chunks = 64;
@@ -140,13 +149,19 @@ cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s);
 cudaError_t launch_rhs(sgf_ctx* c, zd* out);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
+cudaError_t launch_apply_adj64(sgf_ctx* c, const zd* v, zd* out);
+cudaError_t launch_apply_adj32(sgf_ctx* c, const zd* v, zd* out);
+cudaError_t launch_conj_transpose(const zd* src, long R, long Cc, zd* dst, cudaStream_t s);
+cudaError_t launch_near_transpose(int nblk, const int* bq, const int* br, const long* src_off, const int* src_ld,
+                                  const long* dst_off, const int* dst_ld, const int* cell_start, const zd* C, zd* CT,
+                                  cudaStream_t s);
 cudaError_t build_apply_graph(sgf_ctx* c, int prec);
 cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out);
 void destroy_graphs(sgf_ctx* c);
 cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B);
 cudaError_t launch_twiddles(sgf_ctx* c);
 // which Y-convolution kernel serves this orientation: 1 registers, 2 global scratch, 0 none fits
-int conv_y_variant_of(const Orient& o, int precision);
+int conv_y_variant_of(const Orient& o, int precision, bool adjoint = false);
 cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);
 // Krylov helpers
 cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,

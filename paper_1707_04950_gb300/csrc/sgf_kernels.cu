@@ -478,11 +478,13 @@ __global__ void k_split_ff(const zd* __restrict__ s, float4* __restrict__ d, lon
   if (i < n) d[i] = cff_from(s[i]);
 }
 cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
   k_split_ff<<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
   k_to_f32<<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
@@ -1021,23 +1023,24 @@ __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, con
 // The partial product K_m FFT(xi) stays in registers, with the twiddle table staged in shared
 // memory next to the column, when both fit (FP64 columns up to 6144 points); otherwise it goes to
 // the global scratch `accg` ([Px][Py]). Returns 0 (and launches nothing) when neither fits.
-template <typename T>
+template <typename T, bool ADJ>
 static int conv_y_variant(const Orient& o) {
   int threads = conv_threads(o.Py);
   if (threads > 1024) return 0;
   size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  const void* kreg = ADJ ? (const void*)k_conv_y_adj<T, 16, false> : (const void*)k_conv_y<T, 16, false>;
+  const void* kacc = ADJ ? (const void*)k_conv_y_adj<T, 16, true> : (const void*)k_conv_y<T, 16, true>;
   cudaFuncAttributes fa;
-  if (2 * sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, k_conv_y<T, 16, false>) == cudaSuccess &&
-      (long)fa.numRegs * threads <= 65536)
+  if (2 * sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, kreg) == cudaSuccess && (long)fa.numRegs * threads <= 65536)
     return 1;
-  if (sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, k_conv_y<T, 16, true>) == cudaSuccess &&
-      (long)fa.numRegs * threads <= 65536)
+  if (sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, kacc) == cudaSuccess && (long)fa.numRegs * threads <= 65536)
     return 2;
   return 0;
 }
 
-int conv_y_variant_of(const Orient& o, int precision) {
-  return precision == 64 ? conv_y_variant<double>(o) : conv_y_variant<float>(o);
+int conv_y_variant_of(const Orient& o, int precision, bool adjoint) {
+  if (adjoint) return precision == 64 ? conv_y_variant<double, true>(o) : conv_y_variant<float, true>(o);
+  return precision == 64 ? conv_y_variant<double, false>(o) : conv_y_variant<float, false>(o);
 }
 
 template <typename T>
@@ -1045,7 +1048,7 @@ static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, c
                           const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
   int threads = conv_threads(o.Py);
   size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  int v = conv_y_variant<T>(o);
+  int v = conv_y_variant<T, false>(o);
   if (v == 2) {
     if (!accg) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(k_conv_y<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1054,6 +1057,26 @@ static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, c
     sm *= 2;  // column + twiddle table
     cudaFuncSetAttribute(k_conv_y<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_conv_y<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, nullptr);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t conv_y_adj(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
+                              const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
+  int threads = conv_threads(o.Py);
+  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  int v = conv_y_variant<T, true>(o);
+  if (v == 2) {
+    if (!accg) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_conv_y_adj<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y_adj<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
+  } else if (v == 1) {
+    sm *= 2;
+    cudaFuncSetAttribute(k_conv_y_adj<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y_adj<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, nullptr);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1125,6 +1148,277 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
 
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<double>(c, c->o64, mu, out); }
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<float>(c, c->o32, mu, out); }
+
+// ============================================================== adjoint map
+// The forward map is  out = hs mu + MT (MS mu) + C mu + Ip G(K (S P mu))  with P the per-cell
+// projections, S the twisted scatter onto the grids, K the grid convolution, G the gather of the
+// cell samples and Ip the (untwisted) reconstruction rows. Its conjugate transpose runs the same
+// stages backwards: Ip^H and G^H (k_interp_adj), K^H (conjugate spectra, k_conv_y_adj), S^H and
+// P^H (k_project_adj), with C^H stored as its own row-contiguous layout and the mode factors
+// conjugate-transposed at build time.
+
+// dst[c * R + r] = conj(src[r * Cc + c])
+__global__ void k_conj_transpose(const zd* __restrict__ src, long R, long Cc, zd* __restrict__ dst) {
+  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= R * Cc) return;
+  long r = t / Cc, cc = t % Cc;
+  dst[cc * R + r] = conj(src[t]);
+}
+cudaError_t launch_conj_transpose(const zd* src, long R, long Cc, zd* dst, cudaStream_t s) {
+  if (R * Cc == 0) return cudaSuccess;
+  k_conj_transpose<<<ceil_div(R * Cc, 256), 256, 0, s>>>(src, R, Cc, dst);
+  return cudaGetLastError();
+}
+
+// Block (q, r) of the near operator (n_q x n_r at src_off, leading dimension src_ld) conjugated
+// and transposed into the rows of cell r of the adjoint layout (at dst_off, leading dimension dst_ld).
+__global__ void k_near_transpose(const int* __restrict__ bq, const int* __restrict__ br,
+                                 const long* __restrict__ src_off, const int* __restrict__ src_ld,
+                                 const long* __restrict__ dst_off, const int* __restrict__ dst_ld,
+                                 const int* __restrict__ cell_start, const zd* __restrict__ C, zd* __restrict__ CT) {
+  const int b = blockIdx.x;
+  const int q = bq[b], r = br[b];
+  const int nq = cell_start[q + 1] - cell_start[q], nr = cell_start[r + 1] - cell_start[r];
+  const zd* src = C + src_off[b];
+  zd* dst = CT + dst_off[b];
+  const int ls = src_ld[b], ld = dst_ld[b];
+  for (int t = threadIdx.x; t < nq * nr; t += blockDim.x) {
+    int i = t / nr, l = t % nr;
+    dst[(long)l * ld + i] = conj(src[(long)i * ls + l]);
+  }
+}
+cudaError_t launch_near_transpose(int nblk, const int* bq, const int* br, const long* src_off, const int* src_ld,
+                                  const long* dst_off, const int* dst_ld, const int* cell_start, const zd* C, zd* CT,
+                                  cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  k_near_transpose<<<nblk, 256, 0, s>>>(bq, br, src_off, src_ld, dst_off, dst_ld, cell_start, C, CT);
+  return cudaGetLastError();
+}
+
+// Ip^H and G^H: block per work item (chunk of at most 32 nodes of a cell), one thread per sample t:
+// the sample's share sum_i conj(Ip[i][t]) v_i is added into the grid point it was gathered from.
+// The tail blocks form the mode-sum partials sum_i conj(MT[i][n]) v_i; for the mixed path the
+// item blocks also write the float-float copy of v used by the adjoint near field.
+template <typename T>
+__global__ void k_interp_adj(int mask, int nfit, long N, int pH, const int* __restrict__ cell_start,
+                             const int* __restrict__ node_idx, const int* __restrict__ samp_gidx,
+                             const cplx<T>* __restrict__ Ip, cplx<T>* __restrict__ gH, cplx<T>* __restrict__ gV,
+                             const zd* __restrict__ MTh, const float4* __restrict__ MThff, zd* __restrict__ mpart,
+                             float4* __restrict__ mpart_ff, float4* __restrict__ vff, int MB, int n_items,
+                             const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                             const int* __restrict__ item_hi, const zd* __restrict__ v) {
+  __shared__ cplx<T> vs[32];
+  if ((int)blockIdx.x >= n_items) {
+    const int t = blockIdx.x - n_items;
+    mode_partial<T>(t / MB, t % MB, MB, N, v, MTh, MThff, mpart, mpart_ff);
+    return;
+  }
+  const int q = item_cell[blockIdx.x];
+  const int lo = item_lo[blockIdx.x], nq = item_hi[blockIdx.x] - lo;
+  const int s0 = cell_start[q] + lo;
+  for (int l = threadIdx.x; l < nq; l += blockDim.x) {
+    const int nid = node_idx[s0 + l];
+    const zd m = v[nid];
+    vs[l] = cplx<T>(m);
+    if (vff) vff[nid] = cff_from(m);
+  }
+  __syncthreads();
+  if (!(mask & 1)) return;
+  for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
+    cplx<T> acc(0, 0);
+    for (int l = 0; l < nq; ++l) acc += mulc(vs[l], Ip[(long)(s0 + l) * nfit + t]);
+    long gi = samp_gidx[(long)q * nfit + t];
+    cplx<T>* base = t < 2 * (pH + 1) ? gH : gV;
+    atomicAdd(&base[gi].re, acc.re);
+    atomicAdd(&base[gi].im, acc.im);
+  }
+}
+
+// S^H and P^H, then C^H, the mode and identity terms: block per work item, rows are the nodes of
+// the chunk. The adjoint source values g_o = conj(twist) * grid'(source o of the cell) are staged in
+// shared memory with the densities of the cell's adjoint columns; each warp reduces a row's
+// far (sum_o conj(P[i][o]) g_o) and near (C^H row) sums; one thread per row adds the identity and
+// mode terms. T = float: FP32 far field, float-float near field and modes, as in the forward map.
+template <typename T>
+__global__ void k_project_adj(int mask, int neq, int nm, double half_sigma, const int* __restrict__ cell_start,
+                              const int* __restrict__ node_idx, const cplx<T>* __restrict__ P,
+                              const int* __restrict__ src_gidx, const cplx<T>* __restrict__ src_tw,
+                              const cplx<T>* __restrict__ gH, long gH_stride, const cplx<T>* __restrict__ gV,
+                              long gV_stride, const int* __restrict__ colsT, const int* __restrict__ coloffT,
+                              const long* __restrict__ cell_offT, const int* __restrict__ cell_WT,
+                              const zd* __restrict__ CT, const float4* __restrict__ CTff,
+                              const float4* __restrict__ vff, const zd* __restrict__ MSh,
+                              const float4* __restrict__ MShff, const zd* __restrict__ mpart,
+                              const float4* __restrict__ mpart_ff, int MB, const int* __restrict__ item_cell,
+                              const int* __restrict__ item_lo, const int* __restrict__ item_hi,
+                              const zd* __restrict__ v, zd* __restrict__ out) {
+  constexpr bool FF = sizeof(T) == 4;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float4 msf[8];
+  __shared__ zd msd[8];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  const int W = cell_WT[q];
+  const int nout = 4 * neq;
+  // shared layout: [W] densities, [32] per-row results, [nout] source values (16 B each)
+  zd* vsd = reinterpret_cast<zd*>(smem_raw);
+  float4* vsf = reinterpret_cast<float4*>(smem_raw);
+  zd* resd = reinterpret_cast<zd*>(smem_raw) + W;
+  float4* resf = reinterpret_cast<float4*>(smem_raw) + W;
+  cplx<T>* g = reinterpret_cast<cplx<T>*>(reinterpret_cast<zd*>(smem_raw) + W + 32);
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    int lam = o / (2 * neq), sidx = o % (2 * neq), si = sidx % neq;
+    long idx = ((long)q * 2 + lam) * neq + si;
+    const cplx<T>* base = lam == 0 ? gH + (sidx < neq ? 0 : gH_stride) : gV + (sidx < neq ? 0 : gV_stride);
+    g[o] = mulc(base[src_gidx[idx]], src_tw[idx]);
+  }
+  if (warp < nm && (mask & 4)) {
+    if (FF) {
+      ff sr = {0.f, 0.f}, si = {0.f, 0.f};
+      for (int cch = lane; cch < MB; cch += 32) {
+        float4 a = mpart_ff[warp * MB + cch];
+        sr = ff_add(sr, {a.x, a.z});
+        si = ff_add(si, {a.y, a.w});
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
+        si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
+      }
+      if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+    } else {
+      zd a(0, 0);
+      for (int cch = lane; cch < MB; cch += 32) a += mpart[warp * MB + cch];
+      a = warp_sum(a);
+      if (lane == 0) msd[warp] = a;
+    }
+  }
+  const int* cq = colsT + coloffT[q];
+  if (FF) {
+    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) vsf[cc] = vff[cq[cc]];
+  } else {
+    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) vsd[cc] = v[cq[cc]];
+  }
+  __syncthreads();
+  for (int il = warp; il < nq; il += nw) {
+    cplx<T> far(0, 0);
+    if (mask & 1) {
+      const cplx<T>* Pr = P + (long)(s0 + il) * nout;
+      for (int o = lane; o < nout; o += 32) far += mulc(g[o], Pr[o]);
+    }
+    far = warp_sum(far);
+    if (FF) {
+      ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+      if (mask & 2) {
+        const float4* Cr = CTff + cell_offT[q] + (long)(rlo + il) * W;
+        ff br = {0.f, 0.f}, bi = {0.f, 0.f};
+        int cc = lane;
+        for (; cc + 32 < W; cc += 64) {
+          cff_mac(Cr[cc], vsf[cc], ar, ai);
+          cff_mac(Cr[cc + 32], vsf[cc + 32], br, bi);
+        }
+        if (cc < W) cff_mac(Cr[cc], vsf[cc], ar, ai);
+        ar = ff_add(ar, br);
+        ai = ff_add(ai, bi);
+        for (int o = 16; o > 0; o >>= 1) {
+          ar = ff_add(ar, {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)});
+          ai = ff_add(ai, {__shfl_down_sync(0xffffffffu, ai.hi, o), __shfl_down_sync(0xffffffffu, ai.lo, o)});
+        }
+      }
+      if (lane == 0) {
+        ar = ff_add(ar, {(float)far.re, 0.f});
+        ai = ff_add(ai, {(float)far.im, 0.f});
+        resf[il] = make_float4(ar.hi, ai.hi, ar.lo, ai.lo);
+      }
+    } else {
+      zd acc(0, 0);
+      if (mask & 2) {
+        const zd* Cr = CT + cell_offT[q] + (long)(rlo + il) * W;
+        zd acc1(0, 0), acc2(0, 0), acc3(0, 0);
+        int cc = lane;
+        for (; cc + 96 < W; cc += 128) {
+          acc = fma_c(Cr[cc], vsd[cc], acc);
+          acc1 = fma_c(Cr[cc + 32], vsd[cc + 32], acc1);
+          acc2 = fma_c(Cr[cc + 64], vsd[cc + 64], acc2);
+          acc3 = fma_c(Cr[cc + 96], vsd[cc + 96], acc3);
+        }
+        for (; cc < W; cc += 32) acc = fma_c(Cr[cc], vsd[cc], acc);
+        acc = warp_sum((acc + acc1) + (acc2 + acc3));
+      }
+      if (lane == 0) resd[il] = acc + zd((double)far.re, (double)far.im);
+    }
+  }
+  __syncthreads();
+  for (int il = threadIdx.x; il < nq; il += blockDim.x) {
+    const int i = node_idx[s0 + il];
+    if (FF) {
+      float4 r = resf[il];
+      ff vr = {r.x, r.z}, vi = {r.y, r.w};
+      if (mask & 8) {
+        float4 m = vff[i];
+        float hs = (float)half_sigma;
+        vr = ff_add(vr, {hs * m.x, hs * m.z});
+        vi = ff_add(vi, {hs * m.y, hs * m.w});
+      }
+      if (mask & 4)
+        for (int n = 0; n < nm; ++n) cff_mac(MShff[(long)i * nm + n], msf[n], vr, vi);
+      out[i] = zd(ff_to_double(vr), ff_to_double(vi));
+    } else {
+      zd a = resd[il];
+      if (mask & 8) a += half_sigma * v[i];
+      if (mask & 4)
+        for (int n = 0; n < nm; ++n) a += MSh[(long)i * nm + n] * msd[n];
+      out[i] = a;
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t apply_adj_t(sgf_ctx* c, OpData<T>& od, const zd* v, zd* out) {
+  cudaStream_t s = c->stream;
+  const Orient& oH = c->og[0];
+  const Orient& oV = c->og[1];
+  long szH = (long)oH.Px * oH.nrow, szV = (long)oV.Px * oV.nrow;
+  cudaMemsetAsync(od.grid[0], 0, szH * sizeof(cplx<T>), s);
+  cudaMemsetAsync(od.grid[1], 0, szV * sizeof(cplx<T>), s);
+  k_interp_adj<T><<<c->n_items + c->nm * c->mode_chunks, 64, 0, s>>>(
+      c->debug_mask, c->nfit, c->N, c->prm.p, c->d_cell_start, c->d_node_idx, c->d_samp_gidx, od.Ip, od.grid[0],
+      od.grid[1], c->d_MTh, c->d_MThff, c->d_mpart, c->d_mpart_ff, sizeof(T) == 4 ? c->d_muff : nullptr,
+      c->mode_chunks, c->n_items, c->d_item_cell, c->d_item_lo, c->d_item_hi, v);
+  cudaError_t e;
+  bool fork = c->side != nullptr;
+  if (fork) {
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  }
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    cudaStream_t st = (fork && lam == 1) ? c->side : s;
+    long sz = (long)o.Px * o.nrow;
+    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, -1, st)) != cudaSuccess) return e;
+    e = conv_y_adj<T>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.twy[lam],
+                      od.accg[lam], st);
+    if (e != cudaSuccess) return e;
+    if ((e = run_fft_x<T>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, +1, st)) != cudaSuccess) return e;
+  }
+  if (fork) {
+    cudaEventRecord(c->ev_join, c->side);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
+  }
+  double hs = c->bc == 0 ? 0.5 : -0.5;
+  size_t sm = (size_t)(c->maxWT + 32 + 4 * c->neq) * sizeof(zd);
+  cudaFuncSetAttribute(k_project_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_project_adj<T><<<c->n_items, 256, sm, s>>>(
+      c->debug_mask, c->neq, c->nm, hs, c->d_cell_start, c->d_node_idx, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
+      szH, od.grid[1], szV, c->d_colsT, c->d_coloffT, c->d_cell_offT, c->d_cell_WT, c->d_CT, c->d_CTff, c->d_muff,
+      c->d_MSh, c->d_MShff, c->d_mpart, c->d_mpart_ff, c->mode_chunks, c->d_item_cell, c->d_item_lo, c->d_item_hi, v,
+      out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_adj64(sgf_ctx* c, const zd* v, zd* out) { return apply_adj_t<double>(c, c->o64, v, out); }
+cudaError_t launch_apply_adj32(sgf_ctx* c, const zd* v, zd* out) { return apply_adj_t<float>(c, c->o32, v, out); }
 
 // ------------------------------------------------------------------ CUDA graph of the forward map
 // Argument positions of mu / out in k_project and k_interp_near (kept in step with their signatures).

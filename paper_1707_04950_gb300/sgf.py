@@ -20,7 +20,7 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
           10: "SGF_ESTATE"}
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
-            "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve",
+            "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
             "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table"]
 
 
@@ -61,6 +61,7 @@ def load():
         "sgf_apply_host": [vp, vp, vp, i],
         "sgf_rhs": [vp, vp],
         "sgf_solve": [vp, d, i, vp, ctypes.POINTER(i), dp],
+        "sgf_solve_rhs": [vp, vp, i, d, i, vp, ctypes.POINTER(i), dp],
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
         "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
         "sgf_info": [vp, dp],
@@ -147,6 +148,14 @@ def sgf_solve(ctx, tol, maxit, mu_ptr):
     its = ctypes.c_int(0)
     rr = ctypes.c_double(0)
     st = load().sgf_solve(ctx, float(tol), int(maxit), ctypes.c_void_p(mu_ptr), ctypes.byref(its), ctypes.byref(rr))
+    return st, its.value, rr.value
+
+
+def sgf_solve_rhs(ctx, rhs_ptr, transpose_conj, tol, maxit, x_ptr):
+    its = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = load().sgf_solve_rhs(ctx, ctypes.c_void_p(rhs_ptr), int(transpose_conj), float(tol), int(maxit),
+                              ctypes.c_void_p(x_ptr), ctypes.byref(its), ctypes.byref(rr))
     return st, its.value, rr.value
 
 
