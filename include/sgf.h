@@ -133,6 +133,37 @@ sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, do
 sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                                 double* energy_err);
 
+/* ------------------------------------------------------------------------------------------------
+ * Batches of independent problems (different surfaces, wavenumbers or incidence angles, each in its
+ * own built context). The paper solves one problem at a time; a batch launches the forward maps of
+ * all its problems as independent branches of one CUDA graph so that problems too small to fill
+ * the GPU alone share it, and runs GMRES on all of them in lockstep. */
+typedef struct sgf_batch sgf_batch;
+
+/* Create a batch over n built contexts (distinct, same device, each with its captured forward map:
+ * the default unless the environment sets SGF_NO_GRAPH). The batch keeps the context pointers, not
+ * ownership: destroy the batch before its contexts. Work is enqueued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default). While a batch call runs, the contexts' staging buffers and
+ * grids are in use: do not apply or solve with those contexts on other streams at the same time.
+ * On failure *out still receives a batch whose sgf_batch_last_error() explains it; destroy it. */
+sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* cuda_stream);
+void sgf_batch_destroy(sgf_batch* batch);
+const char* sgf_batch_last_error(const sgf_batch* batch);
+
+/* out_devs[p] = A_p mu_devs[p] for every problem p (Algorithm 3 in each context's precision), one
+ * graph launch for the whole batch. Host arrays of n device pointers (complex128, length N_p).
+ * Enqueued on the batch stream; does not synchronise. */
+sgf_status sgf_batch_apply(sgf_batch* batch, const void* const* mu_devs, void* const* out_devs);
+
+/* Algorithm 1 for every problem on its incident-wave right-hand side (as sgf_solve): restarted GMRES
+ * (restart 200, CGS2) in lockstep, one graph launch per Arnoldi step for all problems, one batched
+ * kernel per Gram-Schmidt pass. If any context uses precision 32, every problem runs FP64 residual
+ * refinement around inner solves (tolerance 1e-6) on its own operator. Solutions go to mu_devs[p];
+ * host iters[n] and relres[n] (may be NULL) receive operator applications and the final FP64
+ * relative residual of each problem. SGF_ENOCONV names the first problem above tol. Synchronises. */
+sgf_status sgf_batch_solve(sgf_batch* batch, double tol, int maxit, void* const* mu_devs, int* iters,
+                           double* relres);
+
 /* Introspection: fills host info[0..19] with N, number of occupied cells, near-field entries,
  * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
  * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec,

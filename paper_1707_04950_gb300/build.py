@@ -1,6 +1,6 @@
 """Build the sgf CUDA library (sm_103a) in-tree: paper_1707_04950_gb300/_lib/libsgf.so.
 
-Two translation units are compiled in parallel with nvcc and linked into one shared library with
+The translation units are compiled in parallel with nvcc and linked into one shared library with
 the static CUDA runtime. Run as `python -m paper_1707_04950_gb300.build`.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsgf.so")
-SOURCES = ["sgf_kernels.cu", "sgf_capi.cu", "sgf_noalloc.cu"]
+SOURCES = ["sgf_kernels.cu", "sgf_capi.cu", "sgf_noalloc.cu", "sgf_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,539 @@
+// Batches of independent problems (surfaces, wavenumbers, incidence angles): every problem keeps
+// its own context (operator data, captured forward map), and the batch launches all of their
+// forward maps as independent branches of ONE CUDA graph, so that problems too small to fill the
+// GPU alone run side by side. sgf_batch_solve runs restarted GMRES (Algorithm 1) on all problems
+// in lockstep: one graph launch applies every problem's operator, and each Gram-Schmidt pass,
+// update and norm is one launch over all problems (grid dimension = problem), with one host
+// synchronisation per pass for the whole batch instead of one per problem.
+#include <complex>
+#include <cmath>
+#include <cstring>
+
+#include "sgf_internal.h"
+
+typedef std::complex<double> cd;
+
+struct sgf_batch {
+  int n = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<sgf_ctx*> ctx;
+  std::vector<long> N;
+  long maxN = 0;
+  bool any_mixed = false;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] each context's own precision, [1] FP64
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long* d_N = nullptr;
+  zd** d_in = nullptr;    // contexts' staging inputs (read by their captured forward maps)
+  zd** d_out = nullptr;   // contexts' staging outputs
+  zd** d_ta = nullptr;    // per-call pointer tables
+  zd** d_tb = nullptr;
+  zd** h_tab = nullptr;   // pinned host staging of the per-call tables (2 n entries)
+  cudaEvent_t ev_tab = nullptr;
+  std::vector<void*> allocs;
+  char err[1024] = {0};
+};
+
+static sgf_status berr(sgf_batch* b, sgf_status st, const char* fmt, ...) {
+  if (b) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->err, sizeof(b->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define BCU(call)                                                                                          \
+  do {                                                                                                     \
+    cudaError_t e__ = (call);                                                                              \
+    if (e__ != cudaSuccess) return berr(B, SGF_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,            \
+                                        cudaGetErrorString(e__));                                          \
+  } while (0)
+#define BTRY(x)                        \
+  do {                                 \
+    sgf_status st__ = (x);             \
+    if (st__ != SGF_OK) return st__;   \
+  } while (0)
+
+template <typename T>
+static sgf_status balloc(sgf_batch* B, T** p, size_t count) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc((void**)p, (count ? count : 1) * sizeof(T));
+  if (e != cudaSuccess) return berr(B, SGF_ECUDA, "cudaMalloc of %zu bytes: %s", count * sizeof(T), cudaGetErrorString(e));
+  B->allocs.push_back((void*)*p);
+  return SGF_OK;
+}
+
+// ------------------------------------------------------------------ batched vector kernels
+// A "table" holds one base pointer per problem; vector k of problem p starts at tab[p] + k N_p.
+// Grids are (chunks of the longest vector, problems).
+__global__ void k_bcopy(zd* const* __restrict__ dt, int dk, zd* const* __restrict__ st, int sk,
+                        const long* __restrict__ N) {
+  const int p = blockIdx.y;
+  const long n = N[p];
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dt[p][dk * n + i] = st[p][sk * n + i];
+}
+// y_p = b_p - y_p
+__global__ void k_brsub(zd* const* __restrict__ yt, int yk, zd* const* __restrict__ bt, const long* __restrict__ N) {
+  const int p = blockIdx.y;
+  const long n = N[p];
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    zd* y = yt[p] + yk * n;
+    y[i] = bt[p][i] - y[i];
+  }
+}
+// y_p = s_p y_p (s_p real; s_p = 0 clears the vector of a problem that has stopped, so that it
+// carries zeros, not growing rounding noise, through the remaining lockstep steps)
+__global__ void k_bscale(zd* const* __restrict__ yt, int yk, const double* __restrict__ s, const long* __restrict__ N) {
+  const int p = blockIdx.y;
+  const long n = N[p];
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    zd* y = yt[p] + yk * n;
+    y[i] = s[p] * y[i];
+  }
+}
+// y_p += x_p
+__global__ void k_badd(zd* const* __restrict__ yt, zd* const* __restrict__ xt, const long* __restrict__ N) {
+  const int p = blockIdx.y;
+  const long n = N[p];
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) yt[p][i] += xt[p][i];
+}
+// h[p][j] = sum_i conj(V_p[j0 + j][i]) w_p[i], j < m: block per (j, p)
+__global__ void k_bdots(zd* const* __restrict__ Vt, int j0, int m, zd* const* __restrict__ wt, int wk,
+                        const long* __restrict__ N, zd* __restrict__ h) {
+  __shared__ zd red[32];
+  const int j = blockIdx.x, p = blockIdx.y;
+  const long n = N[p];
+  const zd* v = Vt[p] + (j0 + j) * n;
+  const zd* w = wt[p] + wk * n;
+  zd acc(0, 0);
+  for (long i = threadIdx.x; i < n; i += blockDim.x) acc += mulc(w[i], v[i]);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  acc = warp_sum(acc);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    zd s = lane < nw ? red[lane] : zd(0, 0);
+    s = warp_sum(s);
+    if (lane == 0) h[(long)p * m + j] = s;
+  }
+}
+// w_p -= sum_{j<m} V_p[j] h[p][j]
+__global__ void k_bupdate(zd* const* __restrict__ wt, int wk, zd* const* __restrict__ Vt, int m,
+                          const zd* __restrict__ h, const long* __restrict__ N) {
+  const int p = blockIdx.y;
+  const long n = N[p];
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  zd* w = wt[p] + wk * n;
+  const zd* V = Vt[p];
+  zd acc = w[i];
+  for (int j = 0; j < m; ++j) {
+    const zd hj = h[(long)p * m + j];
+    if (hj.re != 0.0 || hj.im != 0.0) acc -= V[j * n + i] * hj;
+  }
+  w[i] = acc;
+}
+
+// ------------------------------------------------------------------ batched forward map
+static dim3 bgrid(const sgf_batch* B) { return dim3(ceil_div(B->maxN, 256), B->n); }
+
+// dst[dk] = A src[sk] for every problem with the operators of graph slot `slot`.
+static sgf_status bapply(sgf_batch* B, int slot, zd** st, int sk, zd** dt, int dk) {
+  k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(B->d_in, 0, st, sk, B->d_N);
+  BCU(cudaGetLastError());
+  BCU(cudaGraphLaunch(B->exec[slot], B->stream));
+  k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(dt, dk, B->d_out, 0, B->d_N);
+  BCU(cudaGetLastError());
+  return SGF_OK;
+}
+
+// Writes two host pointer arrays into the device tables d_ta / d_tb (through pinned staging).
+static sgf_status set_tables(sgf_batch* B, const void* const* a, const void* const* b) {
+  BCU(cudaEventSynchronize(B->ev_tab));  // the previous upload has left the staging buffer
+  for (int p = 0; p < B->n; ++p) {
+    B->h_tab[p] = (zd*)a[p];
+    B->h_tab[B->n + p] = b ? (zd*)b[p] : nullptr;
+  }
+  BCU(cudaMemcpyAsync(B->d_ta, B->h_tab, B->n * sizeof(zd*), cudaMemcpyHostToDevice, B->stream));
+  BCU(cudaMemcpyAsync(B->d_tb, B->h_tab + B->n, B->n * sizeof(zd*), cudaMemcpyHostToDevice, B->stream));
+  BCU(cudaEventRecord(B->ev_tab, B->stream));
+  return SGF_OK;
+}
+
+static void free_batch(sgf_batch* B) {
+  for (int s = 0; s < 2; ++s) {
+    if (B->exec[s]) cudaGraphExecDestroy(B->exec[s]);
+    if (B->graph[s]) cudaGraphDestroy(B->graph[s]);
+  }
+  for (void* p : B->allocs) cudaFree(p);
+  if (B->h_tab) cudaFreeHost(B->h_tab);
+  if (B->ev_tab) cudaEventDestroy(B->ev_tab);
+}
+
+extern "C" {
+
+sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* cuda_stream) {
+  if (!out) return SGF_EINVAL;
+  *out = nullptr;
+  sgf_batch* B = new sgf_batch();
+  *out = B;
+  if (n < 1 || !ctxs) return berr(B, SGF_EINVAL, "empty batch");
+  B->n = n;
+  B->stream = (cudaStream_t)cuda_stream;
+  B->device = ctxs[0] ? ctxs[0]->device : 0;
+  for (int p = 0; p < n; ++p) {
+    sgf_ctx* c = ctxs[p];
+    if (!c || !c->built) return berr(B, SGF_ESTATE, "context %d is not built", p);
+    if (c->device != B->device) return berr(B, SGF_EINVAL, "context %d is on another device", p);
+    bool mixed = c->prm.precision == 32;
+    if (!c->use_graphs || !c->gs[0].ok || (mixed && !c->gs[1].ok))
+      return berr(B, SGF_ESTATE, "context %d has no captured forward map", p);
+    for (int q = 0; q < p; ++q)
+      if (ctxs[q] == c) return berr(B, SGF_EINVAL, "context %d appears twice", p);
+    B->ctx.push_back(c);
+    B->N.push_back(c->N);
+    B->maxN = std::max(B->maxN, (long)c->N);
+    B->any_mixed = B->any_mixed || mixed;
+  }
+  BCU(cudaSetDevice(B->device));
+  BCU(cudaEventCreateWithFlags(&B->ev_tab, cudaEventDisableTiming));
+  BCU(cudaEventRecord(B->ev_tab, B->stream));
+  BCU(cudaMallocHost((void**)&B->h_tab, 2 * n * sizeof(zd*)));
+  BTRY(balloc(B, &B->d_N, n));
+  BTRY(balloc(B, &B->d_in, n));
+  BTRY(balloc(B, &B->d_out, n));
+  BTRY(balloc(B, &B->d_ta, n));
+  BTRY(balloc(B, &B->d_tb, n));
+  std::vector<zd*> in(n), outp(n);
+  for (int p = 0; p < n; ++p) {
+    in[p] = B->ctx[p]->d_mu_tmp;
+    outp[p] = B->ctx[p]->d_out_tmp;
+  }
+  BCU(cudaMemcpy(B->d_N, B->N.data(), n * sizeof(long), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(B->d_in, in.data(), n * sizeof(zd*), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(B->d_out, outp.data(), n * sizeof(zd*), cudaMemcpyHostToDevice));
+  // one graph per slot: every problem's captured forward map as an independent child graph
+  for (int s = 0; s < 2; ++s) {
+    if (s == 1 && !B->any_mixed) break;
+    BCU(cudaGraphCreate(&B->graph[s], 0));
+    for (int p = 0; p < n; ++p) {
+      sgf_ctx* c = B->ctx[p];
+      int gi = (s == 0 && c->prm.precision == 32) ? 1 : 0;
+      cudaGraphNode_t nd;
+      BCU(cudaGraphAddChildGraphNode(&nd, B->graph[s], nullptr, 0, c->gs[gi].g));
+    }
+    BCU(cudaGraphInstantiate(&B->exec[s], B->graph[s], 0));
+  }
+  if (!B->any_mixed) B->exec[1] = nullptr;
+  return SGF_OK;
+}
+
+void sgf_batch_destroy(sgf_batch* B) {
+  if (!B) return;
+  if (B->n > 0) {
+    cudaSetDevice(B->device);
+    cudaStreamSynchronize(B->stream);
+  }
+  free_batch(B);
+  delete B;
+}
+
+const char* sgf_batch_last_error(const sgf_batch* B) { return B ? B->err : "null batch"; }
+
+sgf_status sgf_batch_apply(sgf_batch* B, const void* const* mu_devs, void* const* out_devs) {
+  if (!B) return SGF_EINVAL;
+  if (!B->exec[0]) return berr(B, SGF_ESTATE, "batch was not created");
+  if (!mu_devs || !out_devs) return berr(B, SGF_EINVAL, "null pointer arrays");
+  for (int p = 0; p < B->n; ++p)
+    if (!mu_devs[p] || !out_devs[p]) return berr(B, SGF_EINVAL, "null buffer for problem %d", p);
+  BTRY(set_tables(B, (const void* const*)mu_devs, (const void* const*)out_devs));
+  return bapply(B, 0, B->d_ta, 0, B->d_tb, 0);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ lockstep GMRES
+struct BWork {
+  int m = 0;
+  zd** d_V = nullptr;   // [p] Krylov basis, (m + 1) vectors of N_p
+  zd** d_r = nullptr;   // [p] residual / work vector
+  zd* d_h = nullptr;    // [p][m + 1] coefficients
+  double* d_s = nullptr;
+  std::vector<zd*> V, r;
+};
+
+// h_out[p][j] = V_p[j0 + j]^H w_p (j < m), synchronised to the host.
+static sgf_status bdots(sgf_batch* B, BWork& W, zd** Vt, int m, zd** wt, int wk, std::vector<cd>& h_out, int j0 = 0) {
+  k_bdots<<<dim3(m, B->n), 256, 0, B->stream>>>(Vt, j0, m, wt, wk, B->d_N, W.d_h);
+  BCU(cudaGetLastError());
+  h_out.resize((size_t)B->n * m);
+  BCU(cudaMemcpyAsync(h_out.data(), W.d_h, h_out.size() * sizeof(zd), cudaMemcpyDeviceToHost, B->stream));
+  BCU(cudaStreamSynchronize(B->stream));
+  return SGF_OK;
+}
+
+static sgf_status bscale(sgf_batch* B, BWork& W, zd** t, int k, const std::vector<double>& s) {
+  BCU(cudaMemcpyAsync(W.d_s, s.data(), B->n * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  k_bscale<<<bgrid(B), 256, 0, B->stream>>>(t, k, W.d_s, B->d_N);
+  BCU(cudaGetLastError());
+  return SGF_OK;
+}
+
+// w_p[wk] -= V_p[0..m) h[p][.] with host coefficients (m_stride entries per problem)
+static sgf_status bupdate(sgf_batch* B, BWork& W, zd** wt, int wk, zd** Vt, int m, const std::vector<cd>& h) {
+  BCU(cudaMemcpyAsync(W.d_h, h.data(), (size_t)B->n * m * sizeof(zd), cudaMemcpyHostToDevice, B->stream));
+  k_bupdate<<<bgrid(B), 256, 0, B->stream>>>(wt, wk, Vt, m, W.d_h, B->d_N);
+  BCU(cudaGetLastError());
+  return SGF_OK;
+}
+
+// Lockstep restarted GMRES from x = 0 on A_p x_p = b_p for every problem with `active`, operators
+// of graph slot `slot`. Problems stop (their iterates freeze) once their residual reaches tol.
+static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, const std::vector<zd*>& xs, double tol,
+                         int maxit, std::vector<int>& its, std::vector<double>& rr) {
+  const int n = B->n, m = W.m;
+  std::vector<cd> tmp;
+  for (int p = 0; p < n; ++p) BCU(cudaMemsetAsync(xs[p], 0, B->N[p] * sizeof(zd), B->stream));  // x = 0
+  BTRY(bdots(B, W, bt, 1, bt, 0, tmp));
+  std::vector<double> bn(n), res(n);
+  std::vector<char> done(n, 0);
+  for (int p = 0; p < n; ++p) {
+    bn[p] = std::sqrt(tmp[p].real());
+    its[p] = 0;
+    if (bn[p] == 0) done[p] = 1;
+  }
+  std::vector<cd> H((size_t)n * (m + 1) * m), cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
+  std::vector<int> jdone(n, 0);
+  std::vector<double> sc(n);
+  int total = 0;
+  bool first = true;
+  while (total < maxit) {
+    // r = b - A x (x = 0 on the first cycle: r = b)
+    if (first) {
+      k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(W.d_r, 0, bt, 0, B->d_N);
+      BCU(cudaGetLastError());
+    } else {
+      BTRY(bapply(B, slot, xt, 0, W.d_r, 0));
+      k_brsub<<<bgrid(B), 256, 0, B->stream>>>(W.d_r, 0, bt, B->d_N);
+      BCU(cudaGetLastError());
+    }
+    first = false;
+    BTRY(bdots(B, W, W.d_r, 1, W.d_r, 0, tmp));
+    bool any = false;
+    for (int p = 0; p < n; ++p) {
+      double beta = std::sqrt(tmp[p].real());
+      res[p] = beta;
+      if (!done[p] && beta / bn[p] <= tol) done[p] = 1;
+      sc[p] = done[p] || beta == 0 ? 0.0 : 1.0 / beta;
+      for (int i = 0; i <= m; ++i) g[(size_t)p * (m + 1) + i] = 0;
+      g[(size_t)p * (m + 1)] = beta;
+      jdone[p] = 0;
+      any = any || !done[p];
+    }
+    if (!any) break;
+    k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(W.d_V, 0, W.d_r, 0, B->d_N);
+    BCU(cudaGetLastError());
+    BTRY(bscale(B, W, W.d_V, 0, sc));
+    std::vector<char> live(n);
+    for (int p = 0; p < n; ++p) live[p] = !done[p];
+    int jj = 0;
+    for (; jj < m && total < maxit; ++jj) {
+      BTRY(bapply(B, slot, W.d_V, jj, W.d_V, jj + 1));
+      ++total;
+      for (int p = 0; p < n; ++p)
+        if (live[p]) ++its[p];
+      std::vector<cd> h1, h2;
+      BTRY(bdots(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h1));
+      BTRY(bupdate(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h1));
+      BTRY(bdots(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h2));
+      BTRY(bupdate(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h2));
+      BTRY(bdots(B, W, W.d_V, 1, W.d_V, jj + 1, tmp, jj + 1));  // |w|^2
+      bool any_live = false;
+      for (int p = 0; p < n; ++p) {
+        double hn = std::sqrt(std::max(0.0, tmp[p].real()));
+        sc[p] = 0.0;
+        if (!live[p]) continue;
+        if (!std::isfinite(hn)) return berr(B, SGF_ENONFINITE, "non-finite Krylov vector (problem %d)", p);
+        cd* Hp = &H[(size_t)p * (m + 1) * m];
+        for (int i = 0; i <= jj; ++i) Hp[(size_t)i * m + jj] = h1[(size_t)p * (jj + 1) + i] + h2[(size_t)p * (jj + 1) + i];
+        Hp[(size_t)(jj + 1) * m + jj] = hn;
+        cd* csp = &cs[(size_t)p * m];
+        cd* snp = &sn[(size_t)p * m];
+        cd* gp = &g[(size_t)p * (m + 1)];
+        for (int i = 0; i < jj; ++i) {
+          cd a = Hp[(size_t)i * m + jj], bb = Hp[(size_t)(i + 1) * m + jj];
+          Hp[(size_t)i * m + jj] = std::conj(csp[i]) * a + std::conj(snp[i]) * bb;
+          Hp[(size_t)(i + 1) * m + jj] = -snp[i] * a + csp[i] * bb;
+        }
+        cd a = Hp[(size_t)jj * m + jj], bb = Hp[(size_t)(jj + 1) * m + jj];
+        double den = std::sqrt(std::norm(a) + std::norm(bb));
+        csp[jj] = den > 0 ? a / den : cd(1);
+        snp[jj] = den > 0 ? bb / den : cd(0);
+        Hp[(size_t)jj * m + jj] = den;
+        Hp[(size_t)(jj + 1) * m + jj] = 0;
+        gp[jj + 1] = -snp[jj] * gp[jj];
+        gp[jj] = std::conj(csp[jj]) * gp[jj];
+        jdone[p] = jj + 1;
+        res[p] = std::abs(gp[jj + 1]);
+        if (res[p] / bn[p] <= tol || !(hn > 0)) live[p] = 0;
+        if (live[p]) sc[p] = 1.0 / hn;
+        any_live = any_live || live[p];
+      }
+      BTRY(bscale(B, W, W.d_V, jj + 1, sc));
+      if (!any_live) {
+        ++jj;
+        break;
+      }
+    }
+    // x_p += V_p y_p (back substitution per problem; coefficients zero past jdone_p)
+    int mm = 0;
+    for (int p = 0; p < n; ++p) mm = std::max(mm, jdone[p]);
+    if (mm > 0) {
+      std::vector<cd> ny((size_t)n * mm, cd(0));
+      for (int p = 0; p < n; ++p) {
+        if (done[p]) continue;
+        const cd* Hp = &H[(size_t)p * (m + 1) * m];
+        const cd* gp = &g[(size_t)p * (m + 1)];
+        std::vector<cd> y(jdone[p]);
+        for (int i = jdone[p] - 1; i >= 0; --i) {
+          cd s = gp[i];
+          for (int k2 = i + 1; k2 < jdone[p]; ++k2) s -= Hp[(size_t)i * m + k2] * y[k2];
+          y[i] = s / Hp[(size_t)i * m + i];
+        }
+        for (int i = 0; i < jdone[p]; ++i) ny[(size_t)p * mm + i] = -y[i];
+      }
+      BTRY(bupdate(B, W, xt, 0, W.d_V, mm, ny));
+    }
+    bool all = true;
+    for (int p = 0; p < n; ++p) {
+      if (!done[p] && res[p] / bn[p] <= tol) done[p] = 1;
+      all = all && done[p];
+    }
+    if (all) break;
+  }
+  // true residuals
+  BTRY(bapply(B, slot, xt, 0, W.d_r, 0));
+  k_brsub<<<bgrid(B), 256, 0, B->stream>>>(W.d_r, 0, bt, B->d_N);
+  BCU(cudaGetLastError());
+  BTRY(bdots(B, W, W.d_r, 1, W.d_r, 0, tmp));
+  for (int p = 0; p < n; ++p) rr[p] = bn[p] > 0 ? std::sqrt(tmp[p].real()) / bn[p] : 0.0;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void* const* mu_devs, int* iters,
+                                      double* relres) {
+  if (!B) return SGF_EINVAL;
+  if (!B->exec[0]) return berr(B, SGF_ESTATE, "batch was not created");
+  if (!(tol > 0) || maxit < 1 || !mu_devs) return berr(B, SGF_EINVAL, "bad solve arguments");
+  const int n = B->n;
+  for (int p = 0; p < n; ++p)
+    if (!mu_devs[p]) return berr(B, SGF_EINVAL, "null buffer for problem %d", p);
+  BWork W;
+  W.m = std::min(200, maxit);
+  std::vector<void*> mine;
+  auto al = [&](zd** ptr, size_t cnt) -> sgf_status {
+    cudaError_t e = cudaMalloc((void**)ptr, cnt * sizeof(zd));
+    if (e != cudaSuccess) return berr(B, SGF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    mine.push_back(*ptr);
+    return SGF_OK;
+  };
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(B->stream);
+    for (void* q : mine) cudaFree(q);
+  };
+  sgf_status st = SGF_OK;
+  std::vector<zd*> bv(n), xv(n), dv(n), rv(n), Vv(n), r2(n);
+  zd **d_bt = nullptr, **d_xt = nullptr, **d_dt = nullptr, **d_r2 = nullptr;
+  for (int p = 0; p < n && st == SGF_OK; ++p) {
+    long N = B->N[p];
+    if ((st = al(&Vv[p], (size_t)(W.m + 1) * N)) || (st = al(&rv[p], N)) || (st = al(&bv[p], N)) ||
+        (st = al(&dv[p], N)) || (st = al(&r2[p], N)))
+      break;
+    xv[p] = (zd*)mu_devs[p];
+  }
+  auto tab = [&](zd*** d, const std::vector<zd*>& h) -> sgf_status {
+    sgf_status s2 = al((zd**)d, (n * sizeof(zd*) + sizeof(zd) - 1) / sizeof(zd));
+    if (s2 != SGF_OK) return s2;
+    cudaError_t e = cudaMemcpy(*d, h.data(), n * sizeof(zd*), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? SGF_OK : berr(B, SGF_ECUDA, "table upload: %s", cudaGetErrorString(e));
+  };
+  if (st == SGF_OK) st = tab(&W.d_V, Vv);
+  if (st == SGF_OK) st = tab(&W.d_r, rv);
+  if (st == SGF_OK) st = tab(&d_bt, bv);
+  if (st == SGF_OK) st = tab(&d_xt, xv);
+  if (st == SGF_OK) st = tab(&d_dt, dv);
+  if (st == SGF_OK) st = tab(&d_r2, r2);
+  if (st == SGF_OK) st = al(&W.d_h, (size_t)n * (W.m + 2));
+  if (st == SGF_OK) st = al((zd**)&W.d_s, (n + 1) / 2 + 1);
+  if (st != SGF_OK) {
+    cleanup();
+    return st;
+  }
+  // right-hand sides of every problem (eq. discrete_eq)
+  for (int p = 0; p < n && st == SGF_OK; ++p) {
+    sgf_ctx* c = B->ctx[p];
+    cudaStream_t keep = c->stream;
+    c->stream = B->stream;
+    cudaError_t e = launch_rhs(c, bv[p]);
+    c->stream = keep;
+    if (e != cudaSuccess) st = berr(B, SGF_ECUDA, "rhs: %s", cudaGetErrorString(e));
+  }
+  std::vector<int> its(n, 0), it_in(n, 0);
+  std::vector<double> rr(n, 1.0), rr_in(n, 1.0);
+  if (st == SGF_OK && !B->any_mixed) {
+    st = bgmres(B, W, 0, d_bt, d_xt, xv, tol, maxit, its, rr);
+  } else if (st == SGF_OK) {
+    // FP64 residual refinement (graph slot 1) around lockstep inner solves on each context's own
+    // operator (slot 0) to 1e-6
+    std::vector<cd> tmp;
+    for (int p = 0; p < n; ++p) cudaMemsetAsync(xv[p], 0, B->N[p] * sizeof(zd), B->stream);
+    k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(d_r2, 0, d_bt, 0, B->d_N);
+    std::vector<double> bn(n);
+    st = bdots(B, W, d_bt, 1, d_bt, 0, tmp);
+    for (int p = 0; p < n && st == SGF_OK; ++p) bn[p] = std::sqrt(tmp[p].real());
+    int used = 0;
+    for (int outer = 0; outer < 30 && st == SGF_OK; ++outer) {
+      st = bgmres(B, W, 0, d_r2, d_dt, dv, 1e-6, std::max(1, maxit - used), it_in, rr_in);
+      if (st != SGF_OK) break;
+      int mx = 0;
+      for (int p = 0; p < n; ++p) {
+        its[p] += it_in[p];
+        mx = std::max(mx, it_in[p]);
+      }
+      used += mx + 1;
+      k_badd<<<bgrid(B), 256, 0, B->stream>>>(d_xt, d_dt, B->d_N);
+      st = bapply(B, 1, d_xt, 0, d_r2, 0);
+      if (st != SGF_OK) break;
+      k_brsub<<<bgrid(B), 256, 0, B->stream>>>(d_r2, 0, d_bt, B->d_N);
+      st = bdots(B, W, d_r2, 1, d_r2, 0, tmp);
+      bool all = true;
+      for (int p = 0; p < n; ++p) {
+        ++its[p];
+        rr[p] = bn[p] > 0 ? std::sqrt(tmp[p].real()) / bn[p] : 0.0;
+        all = all && rr[p] <= tol;
+      }
+      if (getenv("SGF_VERBOSE"))
+        for (int p = 0; p < n; ++p)
+          fprintf(stderr, "batch refinement %d problem %d inner its %d inner rr %.3e outer rr %.3e\n", outer, p,
+                  it_in[p], rr_in[p], rr[p]);
+      if (all || used >= maxit) break;
+    }
+  }
+  cleanup();
+  for (int p = 0; p < n; ++p) {
+    if (iters) iters[p] = its[p];
+    if (relres) relres[p] = rr[p];
+  }
+  if (st != SGF_OK) return st;
+  for (int p = 0; p < n; ++p)
+    if (!(rr[p] <= tol))
+      return berr(B, SGF_ENOCONV, "problem %d stopped at relative residual %g after %d applications", p, rr[p],
+                  its[p]);
+  return SGF_OK;
+}

@@ -49,6 +49,19 @@ __device__ inline cplx<T> fma_c(cplx<T> a, cplx<T> b, cplx<T> c) {  // a*b + c
   return cplx<T>(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
 }
 
+// sum over the 32 lanes of a warp (lane 0 holds the result)
+template <typename T>
+__device__ inline T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ inline cplx<T> warp_sum(cplx<T> v) {
+  v.re = warp_sum(v.re);
+  v.im = warp_sum(v.im);
+  return v;
+}
+
 typedef cplx<double> zd;
 typedef cplx<float> zf;
 

@@ -28,17 +28,6 @@
 // ============================================================== small device helpers
 __device__ inline int orient_of_sample(int t, int p) { return t < 2 * (p + 1) ? 0 : 1; }
 
-template <typename T>
-__device__ inline T warp_sum(T v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-template <typename T>
-__device__ inline cplx<T> warp_sum(cplx<T> v) {
-  v.re = warp_sum(v.re);
-  v.im = warp_sum(v.im);
-  return v;
-}
 
 // J_n(x) e^{i n th} for any integer n (J_{-n} = (-1)^n J_n)
 __device__ inline zd fb_Z(int n, double kr, double th) {

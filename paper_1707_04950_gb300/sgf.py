@@ -21,7 +21,8 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
-            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table"]
+            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve"]
 
 
 class SgfError(RuntimeError):
@@ -69,6 +70,9 @@ def load():
         "sgf_stage_times": [vp, dp],
         "sgf_debug_mask": [vp, i],
         "sgf_debug_table": [vp, i, i, vp],
+        "sgf_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), vp],
+        "sgf_batch_apply": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
+        "sgf_batch_solve": [vp, d, i, ctypes.POINTER(vp), ctypes.POINTER(i), dp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -78,6 +82,10 @@ def load():
     lib.sgf_destroy.restype = None
     lib.sgf_last_error.argtypes = [vp]
     lib.sgf_last_error.restype = ctypes.c_char_p
+    lib.sgf_batch_destroy.argtypes = [vp]
+    lib.sgf_batch_destroy.restype = None
+    lib.sgf_batch_last_error.argtypes = [vp]
+    lib.sgf_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -177,6 +185,44 @@ def sgf_rayleigh_noalloc(ctx, mu_ptr, n_lo, n_hi):
     _check(ctx, load().sgf_rayleigh_noalloc(ctx, ctypes.c_void_p(mu_ptr), int(n_lo), int(n_hi), _dptr(B), _dptr(eff),
                                             _dptr(err)))
     return B[0::2] + 1j * B[1::2], eff, float(err[0])
+
+
+def _bcheck(batch, st):
+    if st != 0:
+        msg = load().sgf_batch_last_error(batch)
+        raise SgfError(st, msg.decode() if msg else "")
+
+
+def _ptrs(seq):
+    return (ctypes.c_void_p * len(seq))(*[ctypes.c_void_p(int(x)) for x in seq])
+
+
+def sgf_batch_create(ctxs, stream=0):
+    lib = load()
+    b = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    st = lib.sgf_batch_create(ctypes.byref(b), len(ctxs), arr, ctypes.c_void_p(stream or None))
+    if st != 0:
+        msg = lib.sgf_batch_last_error(b)
+        lib.sgf_batch_destroy(b)
+        raise SgfError(st, msg.decode() if msg else "")
+    return b
+
+
+def sgf_batch_destroy(batch):
+    load().sgf_batch_destroy(batch)
+
+
+def sgf_batch_apply(batch, mu_ptrs, out_ptrs):
+    _bcheck(batch, load().sgf_batch_apply(batch, _ptrs(mu_ptrs), _ptrs(out_ptrs)))
+
+
+def sgf_batch_solve(batch, tol, maxit, mu_ptrs):
+    n = len(mu_ptrs)
+    its = (ctypes.c_int * n)()
+    rr = np.zeros(n)
+    st = load().sgf_batch_solve(batch, float(tol), int(maxit), _ptrs(mu_ptrs), its, _dptr(rr))
+    return st, list(its), rr
 
 
 INFO_KEYS = ["N", "n_occ", "nnz", "PxH", "nrowH", "PyH", "PxV", "nrowV", "PyV", "neq", "nfit", "nb", "nm",

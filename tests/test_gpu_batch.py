@@ -1,0 +1,146 @@
+"""Batches of independent problems (sgf_batch_*): the batched forward map against each problem's own
+sgf_apply and against the oracle, the lockstep batched GMRES against single solves and against the
+flat-surface closed form at several incidence angles, and the batch's argument checks.
+
+Tolerances: a batch runs each problem's captured forward map unchanged, so outputs agree with the
+single-problem path up to the summation order of the atomic scatter (1e-13). Solutions agree with
+single solves to the solver tolerance times the condition number (1e-9 FP64; 1e-6 mixed).
+"""
+import numpy as np
+import pytest
+
+from oracle import accel as ac, direct as dr
+from paper_1707_04950_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+sgf = pytest.importorskip("paper_1707_04950_gb300.sgf")
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def _single_apply(op, x):
+    xt, yt = _dev(x), torch.empty(len(x), dtype=torch.complex128, device="cuda")
+    sgf.sgf_apply(op.ctx, xt.data_ptr(), yt.data_ptr(), 1, 0)
+    torch.cuda.synchronize()
+    return yt.cpu().numpy()
+
+
+def _problems():
+    return [(I.wl_sinusoid_dirichlet(N=512), 64),
+            (I.wl_sinusoid_dirichlet(N=400), 64),
+            (I.wl_deep_corrugation_neumann_small(N=1024, nx=32), 32)]
+
+
+def test_batch_apply_matches_single_applies_and_oracle():
+    probs = _problems()
+    ops = [sgf.Operator(par, precision=prec) for par, prec in probs]
+    xs = [_dev(I.random_density(op.par["N"], 20 + p)) for p, op in enumerate(ops)]
+    ys = [torch.empty_like(x) for x in xs]
+    b = sgf.sgf_batch_create([op.ctx for op in ops])
+    try:
+        sgf.sgf_batch_apply(b, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys])
+        torch.cuda.synchronize()
+        # a second launch with the outputs as inputs: the per-call pointer tables are rebound
+        zs = [torch.empty_like(x) for x in xs]
+        sgf.sgf_batch_apply(b, [y.data_ptr() for y in ys], [z.data_ptr() for z in zs])
+        torch.cuda.synchronize()
+    finally:
+        sgf.sgf_batch_destroy(b)
+    for (_, prec), op, x, y, z in zip(probs, ops, xs, ys, zs):
+        # FP64: rounding order of the atomic scatter only; mixed: the FP32 scatter's rounding order,
+        # amplified by the far-field/local-subtraction cancellation (the mixed path's own error)
+        tol = 1e-13 if prec == 64 else 1e-5
+        ref = _single_apply(op, x.cpu().numpy())
+        assert _rel(y.cpu().numpy(), ref) < tol
+        assert _rel(z.cpu().numpy(), _single_apply(op, ref)) < 100 * tol
+    par = ops[0].par
+    ref = ac.Accel(par).apply(xs[0].cpu().numpy())
+    assert _rel(ys[0].cpu().numpy(), ref) < 1e-10
+    for op in ops:
+        op.close()
+
+
+def _single_solve(op):
+    mu = torch.zeros(op.par["N"], dtype=torch.complex128, device="cuda")
+    st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 2000, mu.data_ptr())
+    assert st == 0
+    return mu.cpu().numpy()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_solve_matches_single_solves(mixed):
+    probs = [(I.wl_sinusoid_dirichlet(N=512), 64), (I.wl_sinusoid_dirichlet(N=256), 64),
+             (I.flat(N=256, d=1.0, theta_deg=20.0, bc=1, nx=8, n_per=80), 64)]
+    if mixed:
+        probs = [(par, 32) for par, _ in probs]
+    ops = [sgf.Operator(par, precision=prec) for par, prec in probs]
+    mus = [torch.zeros(op.par["N"], dtype=torch.complex128, device="cuda") for op in ops]
+    b = sgf.sgf_batch_create([op.ctx for op in ops])
+    try:
+        st, its, rr = sgf.sgf_batch_solve(b, 1e-12, 2000, [m.data_ptr() for m in mus])
+        msg = sgf.load().sgf_batch_last_error(b)
+    finally:
+        sgf.sgf_batch_destroy(b)
+    assert st == 0, (msg, its, rr)
+    assert np.all(rr <= 1e-12) and all(i > 0 for i in its)
+    for op, m in zip(ops, mus):
+        ref = _single_solve(op)
+        assert _rel(m.cpu().numpy(), ref) < (1e-6 if mixed else 1e-9)
+        op.close()
+
+
+def test_batch_of_angles_flat_surface_closed_form():
+    # one surface, several incidence angles (independent problems): mu = c e^{i alpha x} with the
+    # closed-form c of the shifted system on a flat surface, within the accelerator's error
+    angles = [5.0, 20.0, 35.0, 50.0]
+    pars = [I.flat(N=256, d=1.0, theta_deg=t, bc=0, nx=8, n_per=80) for t in angles]
+    ops = [sgf.Operator(par) for par in pars]
+    mus = [torch.zeros(256, dtype=torch.complex128, device="cuda") for _ in ops]
+    b = sgf.sgf_batch_create([op.ctx for op in ops])
+    try:
+        st, its, rr = sgf.sgf_batch_solve(b, 1e-12, 2000, [m.data_ptr() for m in mus])
+    finally:
+        sgf.sgf_batch_destroy(b)
+    assert st == 0
+    for par, op, m in zip(pars, ops, mus):
+        al, be = dr.wave(par)
+        x = dr.nodes(par)[0]
+        _, Ueta = dr.mode_sets(par)
+        q = (1 - np.exp(1j * be * par["h"])) ** par["j"]
+        c = -1 / (q / 2 + (par["d"] if 0 in set(np.atleast_1d(Ueta).tolist()) else 0.0))
+        assert np.max(np.abs(m.cpu().numpy() - c * np.exp(1j * al * x))) < 1e-4 * abs(c)
+        op.close()
+
+
+def test_batch_argument_errors():
+    par = I.wl_sinusoid_dirichlet(N=256)
+    op = sgf.Operator(par)
+    with pytest.raises(sgf.SgfError) as e:
+        sgf.sgf_batch_create([])
+    assert e.value.status == 1
+    with pytest.raises(sgf.SgfError) as e:
+        sgf.sgf_batch_create([op.ctx, op.ctx])  # the same problem twice
+    assert e.value.status == 1
+    ctx = sgf.sgf_create(0)
+    try:
+        with pytest.raises(sgf.SgfError) as e:
+            sgf.sgf_batch_create([op.ctx, ctx])  # not built
+        assert e.value.status == 10
+    finally:
+        sgf.sgf_destroy(ctx)
+    b = sgf.sgf_batch_create([op.ctx])
+    try:
+        with pytest.raises(sgf.SgfError) as e:
+            sgf.sgf_batch_apply(b, [0], [0])
+        assert e.value.status == 1
+    finally:
+        sgf.sgf_batch_destroy(b)
+    op.close()
