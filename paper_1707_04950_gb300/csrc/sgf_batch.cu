@@ -293,10 +293,14 @@ static sgf_status bupdate(sgf_batch* B, BWork& W, zd** wt, int wk, zd** Vt, int 
   return SGF_OK;
 }
 
-// Lockstep restarted GMRES from x = 0 on A_p x_p = b_p for every problem with `active`, operators
-// of graph slot `slot`. Problems stop (their iterates freeze) once their residual reaches tol.
-static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, const std::vector<zd*>& xs, double tol,
-                         int maxit, std::vector<int>& its, std::vector<double>& rr) {
+// Lockstep restarted GMRES from x = 0 on A_p x_p = b_p for every problem, operators of graph slot
+// `slot`, relative tolerance tolv[p]. A problem stops (its iterate freezes) once its residual
+// reaches its tolerance: with true_check, the true residual at the start of a cycle decides (and a
+// cycle that fails to halve it ends the problem: attainable accuracy reached); without, the
+// Arnoldi estimate does (inner solves of the refinement).
+static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, const std::vector<zd*>& xs,
+                         const std::vector<double>& tolv, bool true_check, int maxit, std::vector<int>& its,
+                         std::vector<double>& rr) {
   const int n = B->n, m = W.m;
   std::vector<cd> tmp;
   for (int p = 0; p < n; ++p) BCU(cudaMemsetAsync(xs[p], 0, B->N[p] * sizeof(zd), B->stream));  // x = 0
@@ -310,8 +314,8 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
   }
   std::vector<cd> H((size_t)n * (m + 1) * m), cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
   std::vector<int> jdone(n, 0);
-  std::vector<double> sc(n);
-  int total = 0;
+  std::vector<double> sc(n), prev_true(n, 0.0);
+  int total = 0, cycles = 0;
   bool first = true;
   while (total < maxit) {
     // r = b - A x (x = 0 on the first cycle: r = b)
@@ -329,7 +333,9 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
     for (int p = 0; p < n; ++p) {
       double beta = std::sqrt(tmp[p].real());
       res[p] = beta;
-      if (!done[p] && beta / bn[p] <= tol) done[p] = 1;
+      if (!done[p] && beta / bn[p] <= tolv[p]) done[p] = 1;
+      if (!done[p] && true_check && cycles > 0 && beta > 0.5 * prev_true[p]) done[p] = 1;
+      prev_true[p] = beta;
       sc[p] = done[p] || beta == 0 ? 0.0 : 1.0 / beta;
       for (int i = 0; i <= m; ++i) g[(size_t)p * (m + 1) + i] = 0;
       g[(size_t)p * (m + 1)] = beta;
@@ -337,6 +343,7 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
       any = any || !done[p];
     }
     if (!any) break;
+    ++cycles;
     k_bcopy<<<bgrid(B), 256, 0, B->stream>>>(W.d_V, 0, W.d_r, 0, B->d_N);
     BCU(cudaGetLastError());
     BTRY(bscale(B, W, W.d_V, 0, sc));
@@ -381,7 +388,7 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
         gp[jj] = std::conj(csp[jj]) * gp[jj];
         jdone[p] = jj + 1;
         res[p] = std::abs(gp[jj + 1]);
-        if (res[p] / bn[p] <= tol || !(hn > 0)) live[p] = 0;
+        if (res[p] / bn[p] <= tolv[p] || !(hn > 0)) live[p] = 0;
         if (live[p]) sc[p] = 1.0 / hn;
         any_live = any_live || live[p];
       }
@@ -410,12 +417,14 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
       }
       BTRY(bupdate(B, W, xt, 0, W.d_V, mm, ny));
     }
-    bool all = true;
-    for (int p = 0; p < n; ++p) {
-      if (!done[p] && res[p] / bn[p] <= tol) done[p] = 1;
-      all = all && done[p];
+    if (!true_check) {
+      bool all = true;
+      for (int p = 0; p < n; ++p) {
+        if (!done[p] && res[p] / bn[p] <= tolv[p]) done[p] = 1;
+        all = all && done[p];
+      }
+      if (all) break;
     }
-    if (all) break;
   }
   // true residuals
   BTRY(bapply(B, slot, xt, 0, W.d_r, 0));
@@ -487,7 +496,7 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
   std::vector<int> its(n, 0), it_in(n, 0);
   std::vector<double> rr(n, 1.0), rr_in(n, 1.0);
   if (st == SGF_OK && !B->any_mixed) {
-    st = bgmres(B, W, 0, d_bt, d_xt, xv, tol, maxit, its, rr);
+    st = bgmres(B, W, 0, d_bt, d_xt, xv, std::vector<double>(n, tol), true, maxit, its, rr);
   } else if (st == SGF_OK) {
     // FP64 residual refinement (graph slot 1) around lockstep inner solves on each context's own
     // operator (slot 0) to 1e-6
@@ -497,9 +506,18 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
     std::vector<double> bn(n);
     st = bdots(B, W, d_bt, 1, d_bt, 0, tmp);
     for (int p = 0; p < n && st == SGF_OK; ++p) bn[p] = std::sqrt(tmp[p].real());
+    // as in sgf_solve: inner solves to 1e-6 on each context's own operator; once a problem's step
+    // gains less than a factor 10, the batch's remaining corrections run on the FP64 operators to
+    // each problem's final tolerance (problems already finished get tolerance 1: no work)
     int used = 0;
+    bool fp64_inner = false;
+    std::vector<double> rr_prev(n, 1.0), tolv(n);
+    std::vector<char> fin(n, 0);
     for (int outer = 0; outer < 30 && st == SGF_OK; ++outer) {
-      st = bgmres(B, W, 0, d_r2, d_dt, dv, 1e-6, std::max(1, maxit - used), it_in, rr_in);
+      for (int p = 0; p < n; ++p)
+        tolv[p] = fin[p] ? 1.0 : (fp64_inner ? std::min(0.5, tol / rr_prev[p]) : 1e-6);
+      st = bgmres(B, W, fp64_inner ? 1 : 0, d_r2, d_dt, dv, tolv, fp64_inner, std::max(1, maxit - used), it_in,
+                  rr_in);
       if (st != SGF_OK) break;
       int mx = 0;
       for (int p = 0; p < n; ++p) {
@@ -512,17 +530,22 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
       if (st != SGF_OK) break;
       k_brsub<<<bgrid(B), 256, 0, B->stream>>>(d_r2, 0, d_bt, B->d_N);
       st = bdots(B, W, d_r2, 1, d_r2, 0, tmp);
-      bool all = true;
+      bool all = true, switch64 = false;
       for (int p = 0; p < n; ++p) {
+        if (fin[p]) continue;
         ++its[p];
         rr[p] = bn[p] > 0 ? std::sqrt(tmp[p].real()) / bn[p] : 0.0;
-        all = all && rr[p] <= tol;
+        if (rr[p] <= tol || (fp64_inner && rr[p] > 0.5 * rr_prev[p])) fin[p] = 1;
+        if (!fin[p] && rr[p] > 0.1 * rr_prev[p]) switch64 = true;
+        rr_prev[p] = rr[p];
+        all = all && fin[p];
       }
       if (getenv("SGF_VERBOSE"))
         for (int p = 0; p < n; ++p)
-          fprintf(stderr, "batch refinement %d problem %d inner its %d inner rr %.3e outer rr %.3e\n", outer, p,
-                  it_in[p], rr_in[p], rr[p]);
+          fprintf(stderr, "batch refinement %d problem %d inner %s its %d outer rr %.3e\n", outer, p,
+                  fp64_inner ? "fp64" : "mixed", it_in[p], rr[p]);
       if (all || used >= maxit) break;
+      fp64_inner = fp64_inner || switch64;
     }
   }
   cleanup();

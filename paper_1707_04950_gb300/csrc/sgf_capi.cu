@@ -817,8 +817,13 @@ static sgf_status apply_op(sgf_ctx* ctx, const zd* x, zd* out, int prec, bool ad
   return adj ? apply_adj_prec(ctx, x, out, prec) : apply_prec(ctx, x, out, prec);
 }
 
+// Solves A x = b from x = 0 with operator precision prec; returns applications in *its. With
+// true_check (outer and FP64 solves) a cycle whose Arnoldi estimate reaches tol is followed by the
+// true residual b - A x: if that is still above tol another cycle runs, unless the true residual
+// fell by less than half over the last cycle (stagnation at the attainable accuracy). Without it
+// (inner solves of the refinement) the estimate decides.
 static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b, zd* x, double tol, int maxit,
-                        int* its, double* relres) {
+                        int* its, double* relres, bool true_check = true) {
   const long N = ctx->N;
   const int m = K.m;
   std::vector<cd> tmp;
@@ -829,6 +834,8 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   int total = 0;
   double res = bn;
   std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double prev_true = 0;
+  int cycles = 0;
   while (total < maxit) {
     // r = b - A x
     TRY(apply_op(ctx, x, K.r, prec, adj));
@@ -837,6 +844,9 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     double beta = std::sqrt(tmp[0].real());
     res = beta;
     if (beta / bn <= tol) break;
+    if (cycles > 0 && beta > 0.5 * prev_true) break;  // no progress over a whole cycle
+    prev_true = beta;
+    ++cycles;
     CU(cudaMemcpyAsync(K.V, K.r, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
     CU(launch_axpby(K.V, zd(0, 0), K.V, zd(1.0 / beta, 0), N, ctx->stream));
     std::fill(g.begin(), g.end(), cd(0));
@@ -893,7 +903,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     CU(cudaMemcpyAsync(K.h, ny.data(), jdone * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
     CU(launch_update(x, K.V, jdone, N, K.h, N, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (res / bn <= tol) break;
+    if (!true_check && res / bn <= tol) break;
   }
   // true residual
   TRY(apply_op(ctx, x, K.r, prec, adj));
@@ -947,10 +957,18 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
     if (st == SGF_OK) st = al(&r, N);
     if (st == SGF_OK) cudaMemcpyAsync(r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
     if (st == SGF_OK && bn == 0) rr = 0;
+    // Each step solves A_32 d = r to 1e-6 (Arnoldi estimate) and adds d. The step contracts the
+    // FP64 residual by about |A_64 - A_32| |A_32^{-1}|; when a step gains less than a factor 10
+    // (ill-conditioned systems), the remaining correction is solved with the FP64 operator to the
+    // final tolerance instead.
+    bool fp64_inner = false;
+    double rr_prev = 1.0;
     for (int outer = 0; outer < 30 && st == SGF_OK && bn > 0; ++outer) {
       int it_in = 0;
       double rr_in = 1;
-      st = gmres(ctx, K, 32, adj, r, dlt, 1e-6, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in);
+      double itol = fp64_inner ? std::min(0.5, tol / rr_prev) : 1e-6;
+      st = gmres(ctx, K, fp64_inner ? 64 : 32, adj, r, dlt, itol, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in,
+                 fp64_inner);
       if (st != SGF_OK) break;
       its += it_in;
       launch_axpby(x, zd(1, 0), dlt, zd(1, 0), N, ctx->stream);
@@ -960,7 +978,13 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
       launch_axpby(r, zd(1, 0), b, zd(-1, 0), N, ctx->stream);
       st = dot_host(ctx, K, r, 1, r, tmp);
       rr = std::sqrt(tmp[0].real()) / bn;
+      if (getenv("SGF_VERBOSE"))
+        fprintf(stderr, "refinement %d inner %s its %d outer rr %.3e\n", outer, fp64_inner ? "fp64" : "mixed", it_in,
+                rr);
       if (rr <= tol || its >= maxit) break;
+      if (fp64_inner && rr > 0.5 * rr_prev) break;  // the FP64 correction stagnated as well
+      if (rr > 0.1 * rr_prev) fp64_inner = true;
+      rr_prev = rr;
     }
   }
   if (st == SGF_OK) {

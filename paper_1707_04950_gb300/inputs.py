@@ -153,6 +153,14 @@ def wl_gaussian_wood(N=8192, nx=40, seed=2, **kw):
     return make_params(prof, k, th, DIRICHLET, N, nx=nx, **kw)
 
 
+def wl_gaussian_angles(i, N=2048, d=10.0, nx=32, surface_seed=5000, **kw):
+    """One of the 64 problems of the multi-problem workload: Gaussian rough surface (rms 0.5,
+    correlation length 2, period d), k = 2 pi, Dirichlet, incidence theta_i = 89 deg i / 63,
+    i = 0..63 (theta = 0 is a Wood configuration for integer d)."""
+    prof = gaussian_surface(d, 0.5, 2.0, surface_seed)
+    return make_params(prof, 2 * math.pi, 89.0 * i / 63.0, DIRICHLET, N, nx=nx, **kw)
+
+
 def flat(N=64, d=1.0, k=2 * math.pi, theta_deg=20.0, bc=DIRICHLET, nx=8, **kw):
     prof = {"d": float(d), "a": np.zeros(1), "b": np.zeros(1)}
     kw.setdefault("hmin", -0.5 * d / nx)
