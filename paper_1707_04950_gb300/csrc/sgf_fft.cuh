@@ -57,11 +57,17 @@ __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
   }
 }
 
-// One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences.
-template <typename T, int R>
+// Butterflies per thread of a radix-R stage when a thread may hold VPT values (at least one).
+template <int VPT, int R>
+struct StageItems {
+  static constexpr int value = VPT / R > 0 ? VPT / R : 1;
+};
+
+// One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences;
+// each thread takes up to U butterflies (every item of the stage is loaded before any store).
+template <typename T, int R, int U>
 __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es, int batch, int bs,
                                                const cplx<T>* __restrict__ tw, int twlen, int dir) {
-  constexpr int U = 16 / R;  // items per thread: every item of the stage is loaded before any store
   const int nR = n / R;
   const int tot = batch * nR;
   const int tstep = twlen / (Ns * R);  // table stride of e^{-2 pi i / (Ns R)} in a table of twlen
@@ -106,43 +112,44 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es
 // sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 8 (then 4 or 2), then
 // radix 3. tw[k] = e^{-2 pi i k / twlen} over the full circle, n dividing twlen. dir = -1 forward,
 // +1 inverse (unnormalised). All threads of the block must call it. Each stage exchanges through
-// registers in place, so every thread holds all of its items at once: the caller must keep
-// batch * n <= 16 * blockDim.x (<= 15 * blockDim.x when lb > 0).
-template <typename T>
+// registers in place, so every thread holds all of its items at once: with VPT = 16 the caller
+// must keep batch * n <= 16 * blockDim.x (<= 15 * blockDim.x when lb > 0); with VPT = 8,
+// batch * n <= 8 * blockDim.x (<= 6 * blockDim.x when lb > 0).
+template <typename T, int VPT = 16>
 __device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, int bs,
                           const cplx<T>* __restrict__ tw, int twlen, int dir) {
   int Ns = 1, rem = la;
   while (rem >= 3) {
-    stockham_stage<T, 8>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    stockham_stage<T, 8, StageItems<VPT, 8>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
     Ns <<= 3;
     rem -= 3;
   }
   if (rem == 2) {
-    stockham_stage<T, 4>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    stockham_stage<T, 4, StageItems<VPT, 4>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
     Ns <<= 2;
   }
   if (rem == 1) {
-    stockham_stage<T, 2>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    stockham_stage<T, 2, StageItems<VPT, 2>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
     Ns <<= 1;
   }
   for (int t = 0; t < lb; ++t) {
-    stockham_stage<T, 3>(s, n, Ns, es, batch, bs, tw, twlen, dir);
+    stockham_stage<T, 3, StageItems<VPT, 3>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
     Ns *= 3;
   }
   if (n == 1) __syncthreads();
 }
 
 // Power-of-two length 2^logn with a full-circle table of length 2^twlog.
-template <typename T>
+template <typename T, int VPT = 16>
 __device__ void smem_fft(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
                          int twlog, int dir) {
-  smem_fftn<T>(s, 1 << logn, logn, 0, es, batch, bs, tw, 1 << twlog, dir);
+  smem_fftn<T, VPT>(s, 1 << logn, logn, 0, es, batch, bs, tw, 1 << twlog, dir);
 }
 
 // FFT along X (the strided dimension) of arrays laid out g[ix * nrow + iy], ix < Px = 2^logPx,
 // iy < nrow; block b transforms rows iy in [b*ty, b*ty + ty). blockIdx.y selects the array
 // (arrays are nrow*Px apart).
-template <typename T>
+template <typename T, int VPT>
 __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, long arr_stride,
                         const cplx<T>* __restrict__ tw, int twlog, int dir) {
   extern __shared__ unsigned char smem_raw[];
@@ -158,7 +165,7 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
     s[ix * ty + t] = (iy < nrow) ? a[(long)ix * nrow + iy] : cplx<T>(0, 0);
   }
   __syncthreads();
-  smem_fft<T>(s, logPx, ty, ty, 1, tws, logPx, dir);
+  smem_fft<T, VPT>(s, logPx, ty, ty, 1, tws, logPx, dir);
   for (int idx = threadIdx.x; idx < Px * ty; idx += blockDim.x) {
     int t = idx % ty, ix = idx / ty;
     int iy = iy0 + t;
@@ -209,7 +216,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) ag[i] = s[i] * km[i];
   } else {
@@ -222,7 +229,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   __syncthreads();
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = s[i] * kd[i] + ag[i];
   } else {
@@ -233,7 +240,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
     }
   }
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
 }
 
@@ -265,7 +272,7 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
   cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) {
       cplx<T> v = s[i];
@@ -283,7 +290,7 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
     }
   }
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
   __syncthreads();
   if (ACCG) {
@@ -296,6 +303,6 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
     }
   }
   __syncthreads();
-  smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
   for (int i = threadIdx.x; i < nrow; i += blockDim.x) colz[i] = s[i];
 }

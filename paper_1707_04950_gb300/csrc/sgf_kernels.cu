@@ -490,27 +490,47 @@ static int fftx_ty(int Px, int nrow, size_t esz) {
   if (ty < 1) ty = 1;
   return ty;
 }
-// threads for one contiguous FFT of length Py: at most 15 values per thread, a multiple of 32
-static int conv_threads(int Py) {
-  int t = (Py + 14) / 15;
+// Threads for one contiguous FFT of length Py = 2^la 3^lb when a thread holds at most vpt values
+// (vpt = 16: 15 with radix-3 stages; vpt = 8: 6 with radix-3 stages), a multiple of 32, >= 64.
+static int conv_threads(int Py, int vpt, int lb) {
+  int per = lb > 0 ? (vpt == 16 ? 15 : 6) : vpt;
+  int t = (Py + per - 1) / per;
   t = (t + 31) / 32 * 32;
   return t < 64 ? 64 : t;
 }
-static int fftx_threads(int Px, int ty) {
-  int t = Px * ty / 16;
-  if (t < 64) t = 64;
-  if (t > 512) t = 512;
-  return t;
+static int fftx_threads(int Px, int ty, int vpt) {
+  int t = (Px * ty + vpt - 1) / vpt;
+  t = (t + 31) / 32 * 32;
+  return t < 64 ? 64 : t;
+}
+// Registers per thread of a kernel, looked up once per kernel.
+static int func_regs(const void* f) {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.numRegs : 255;
+}
+template <typename T, int VPT>
+static int fftx_regs() {
+  static const int r = func_regs((const void*)k_fft_x<T, VPT>);
+  return r;
 }
 
+// X passes: 8 values per thread (twice the threads of the 16-value variant, shorter per-thread
+// chains in each stage) whenever the block stays within 1024 threads and the register file.
 template <typename T>
 static cudaError_t run_fft_x(cplx<T>* g, const Orient& o, int nrow, int narr, const cplx<T>* tw, int twlog, int dir,
                              cudaStream_t s) {
   int ty = fftx_ty(o.Px, nrow, sizeof(cplx<T>));
   size_t sm = fftx_smem(o.Px, ty, sizeof(cplx<T>));
-  cudaFuncSetAttribute(k_fft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 grid(ceil_div(nrow, ty), narr);
-  k_fft_x<T><<<grid, fftx_threads(o.Px, ty), sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
+  int t8 = fftx_threads(o.Px, ty, 8);
+  if (t8 <= 1024 && (long)fftx_regs<T, 8>() * t8 <= 65536) {
+    cudaFuncSetAttribute(k_fft_x<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft_x<T, 8><<<grid, t8, sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
+  } else {
+    cudaFuncSetAttribute(k_fft_x<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_fft_x<T, 16><<<grid, fftx_threads(o.Px, ty, 16), sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog,
+                                                                dir);
+  }
   return cudaGetLastError();
 }
 
@@ -545,7 +565,7 @@ cudaError_t launch_tables(sgf_ctx* c) {
     cudaMemcpyAsync(Tld, Txd, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
     size_t sm = (size_t)o.Py * sizeof(zd);
     cudaFuncSetAttribute(k_fft_y_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int ty_threads = conv_threads(o.Py);
+    int ty_threads = conv_threads(o.Py, 16, o.lb);
     k_fft_y_full<double><<<o.Px, ty_threads, sm, c->stream>>>(Tlm, o.Py, o.la, o.lb, c->o64.twy[lam], -1);
     k_fft_y_full<double><<<o.Px, ty_threads, sm, c->stream>>>(Tld, o.Py, o.la, o.lb, c->o64.twy[lam], -1);
     double sc = 1.0 / ((double)o.Px * o.Py);
@@ -1012,18 +1032,23 @@ __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, con
 // The partial product K_m FFT(xi) stays in registers, with the twiddle table staged in shared
 // memory next to the column, when both fit (FP64 columns up to 6144 points); otherwise it goes to
 // the global scratch `accg` ([Px][Py]). Returns 0 (and launches nothing) when neither fits.
+template <typename T, bool ADJ, int VPT, bool ACCG>
+static int conv_regs() {
+  static const int r = func_regs(ADJ ? (const void*)k_conv_y_adj<T, VPT, ACCG> : (const void*)k_conv_y<T, VPT, ACCG>);
+  return r;
+}
+
+// 3: 8 values per thread, product in registers, twiddles in shared memory (the widest blocks);
+// 1: the same with 16 values per thread; 2: 16 values per thread, product in global scratch;
+// 0: no variant fits one block.
 template <typename T, bool ADJ>
 static int conv_y_variant(const Orient& o) {
-  int threads = conv_threads(o.Py);
-  if (threads > 1024) return 0;
-  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  const void* kreg = ADJ ? (const void*)k_conv_y_adj<T, 16, false> : (const void*)k_conv_y<T, 16, false>;
-  const void* kacc = ADJ ? (const void*)k_conv_y_adj<T, 16, true> : (const void*)k_conv_y<T, 16, true>;
-  cudaFuncAttributes fa;
-  if (2 * sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, kreg) == cudaSuccess && (long)fa.numRegs * threads <= 65536)
-    return 1;
-  if (sm <= 200 * 1024 && cudaFuncGetAttributes(&fa, kacc) == cudaSuccess && (long)fa.numRegs * threads <= 65536)
-    return 2;
+  const size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  const int t8 = conv_threads(o.Py, 8, o.lb), t16 = conv_threads(o.Py, 16, o.lb);
+  if (t8 <= 1024 && 2 * sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 8, false>() * t8 <= 65536) return 3;
+  if (t16 > 1024) return 0;
+  if (2 * sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, false>() * t16 <= 65536) return 1;
+  if (sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, true>() * t16 <= 65536) return 2;
   return 0;
 }
 
@@ -1032,44 +1057,50 @@ int conv_y_variant_of(const Orient& o, int precision, bool adjoint) {
   return precision == 64 ? conv_y_variant<double, false>(o) : conv_y_variant<float, false>(o);
 }
 
-template <typename T>
-static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
-                          const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
-  int threads = conv_threads(o.Py);
-  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  int v = conv_y_variant<T, false>(o);
-  if (v == 2) {
-    if (!accg) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_conv_y<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
-  } else if (v == 1) {
-    sm *= 2;  // column + twiddle table
-    cudaFuncSetAttribute(k_conv_y<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, nullptr);
+// One launch of the Y convolution (ADJ: its adjoint) with the variant chosen by conv_y_variant.
+template <typename T, bool ADJ, int VPT, bool ACCG>
+static void conv_launch(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
+                        const cplx<T>* twy, cplx<T>* accg, int threads, cudaStream_t s) {
+  size_t sm = (size_t)o.Py * sizeof(cplx<T>) * (ACCG ? 1 : 2);  // column (+ twiddle table)
+  if (ADJ) {
+    cudaFuncSetAttribute(k_conv_y_adj<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y_adj<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
   } else {
-    return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_conv_y<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_y<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
+  }
+}
+
+template <typename T, bool ADJ>
+static cudaError_t conv_y_any(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
+                              const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
+  switch (conv_y_variant<T, ADJ>(o)) {
+    case 3:
+      conv_launch<T, ADJ, 8, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 8, o.lb), s);
+      break;
+    case 1:
+      conv_launch<T, ADJ, 16, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 16, o.lb), s);
+      break;
+    case 2:
+      if (!accg) return cudaErrorInvalidValue;
+      conv_launch<T, ADJ, 16, true>(xi, zeta, Km, Kd, o, twy, accg, conv_threads(o.Py, 16, o.lb), s);
+      break;
+    default:
+      return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <typename T>
+static cudaError_t conv_y(cplx<T>* xi, const cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
+                          const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
+  return conv_y_any<T, false>(xi, const_cast<cplx<T>*>(zeta), Km, Kd, o, twy, accg, s);
+}
+
+template <typename T>
 static cudaError_t conv_y_adj(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
                               const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
-  int threads = conv_threads(o.Py);
-  size_t sm = (size_t)o.Py * sizeof(cplx<T>);
-  int v = conv_y_variant<T, true>(o);
-  if (v == 2) {
-    if (!accg) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_conv_y_adj<T, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y_adj<T, 16, true><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
-  } else if (v == 1) {
-    sm *= 2;
-    cudaFuncSetAttribute(k_conv_y_adj<T, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y_adj<T, 16, false><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, nullptr);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return conv_y_any<T, true>(xi, zeta, Km, Kd, o, twy, accg, s);
 }
 
 template <typename T>
