@@ -228,7 +228,7 @@ sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* 
       cudaGraphNode_t nd;
       BCU(cudaGraphAddChildGraphNode(&nd, B->graph[s], nullptr, 0, c->gs[gi].g));
     }
-    BCU(cudaGraphInstantiate(&B->exec[s], B->graph[s], 0));
+    BCU(cudaGraphInstantiate(&B->exec[s], B->graph[s], cudaGraphInstantiateFlagUseNodePriority));
   }
   if (!B->any_mixed) B->exec[1] = nullptr;
   return SGF_OK;

@@ -76,9 +76,15 @@ sgf_status sgf_create(sgf_ctx** out, int device, void* cuda_stream) {
     return SGF_ECUDA;
   }
   for (int i = 0; i < 8; ++i) cudaEventCreate(&ctx->ev[i]);
-  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess) ctx->side = nullptr;
+  // side: V convolution chain (highest priority, critical path); side2: near field (lowest)
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess) ctx->side = nullptr;
+  if (cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, prio_lo) != cudaSuccess) ctx->side2 = nullptr;
   cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_fork0, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
   *out = ctx;
   return SGF_OK;
 }
@@ -90,12 +96,13 @@ void sgf_destroy(sgf_ctx* ctx) {
   free_all(ctx);
   for (int i = 0; i < 8; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  if (ctx->side) {
-    cudaStreamSynchronize(ctx->side);
-    cudaStreamDestroy(ctx->side);
-  }
-  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (cudaStream_t st : {ctx->side, ctx->side2})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_join, ctx->ev_fork0, ctx->ev_join2})
+    if (ev) cudaEventDestroy(ev);
   delete ctx;
 }
 
@@ -711,7 +718,7 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     }
     if (prec == 0) c->bytes64 = b; else c->bytes32 = b;
   }
-  c->launches_per_apply = 8;
+  c->launches_per_apply = 9;  // projection, 2 X passes, 2 Y convolutions, 2 inverse X passes, near rows, far rows
   c->built = true;
   // capture the forward map of each precision in use; on failure keep direct launches
   c->use_graphs = getenv("SGF_NO_GRAPH") == nullptr;

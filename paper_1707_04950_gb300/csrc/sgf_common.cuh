@@ -187,6 +187,43 @@ __device__ __forceinline__ void cff_mac(float4 c, float4 m, ff& acc_re, ff& acc_
   acc_im = ff_add(acc_im, ff_mul(ci, mr));
 }
 
+// Compensated complex dot product of float-float operands (the Dot2 scheme of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005)): the hi*hi products are
+// split exactly (fma residual), summed with TwoSum into an FP32 running sum whose rounding errors,
+// the product residuals and the hi*lo cross terms collect in a separate FP32 error sum. The result
+// is as accurate as a float-float evaluation for these sums at about two thirds of the instructions.
+struct dot2c {
+  float sr, si, er, ei;
+};
+__device__ __forceinline__ void two_sum_into(float& s, float& e, float p) {
+  float t = __fadd_rn(s, p);
+  float bp = __fsub_rn(t, s);
+  e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+  s = t;
+}
+// a += c * m; float4 = {re.hi, im.hi, re.lo, im.lo}
+__device__ __forceinline__ void dot2_mac(float4 c, float4 m, dot2c& a) {
+  float p1 = __fmul_rn(c.x, m.x), q1 = __fmaf_rn(c.x, m.x, -p1);
+  float p2 = __fmul_rn(-c.y, m.y), q2 = __fmaf_rn(-c.y, m.y, -p2);
+  float p3 = __fmul_rn(c.x, m.y), q3 = __fmaf_rn(c.x, m.y, -p3);
+  float p4 = __fmul_rn(c.y, m.x), q4 = __fmaf_rn(c.y, m.x, -p4);
+  float xr = __fmaf_rn(c.x, m.z, __fmaf_rn(c.z, m.x, __fmaf_rn(-c.y, m.w, -__fmul_rn(c.w, m.y))));
+  float xi = __fmaf_rn(c.x, m.w, __fmaf_rn(c.z, m.y, __fmaf_rn(c.y, m.z, __fmul_rn(c.w, m.x))));
+  two_sum_into(a.sr, a.er, p1);
+  two_sum_into(a.sr, a.er, p2);
+  two_sum_into(a.si, a.ei, p3);
+  two_sum_into(a.si, a.ei, p4);
+  a.er = __fadd_rn(a.er, __fadd_rn(__fadd_rn(q1, q2), xr));
+  a.ei = __fadd_rn(a.ei, __fadd_rn(__fadd_rn(q3, q4), xi));
+}
+// b folded into a (two partial dot products of one row)
+__device__ __forceinline__ void dot2_merge(dot2c& a, const dot2c& b) {
+  two_sum_into(a.sr, a.er, b.sr);
+  two_sum_into(a.si, a.ei, b.si);
+  a.er = __fadd_rn(a.er, b.er);
+  a.ei = __fadd_rn(a.ei, b.ei);
+}
+
 #define SGF_CUDA_CHECK(call)                                                  \
   do {                                                                            \
     cudaError_t err__ = (call);                                                   \

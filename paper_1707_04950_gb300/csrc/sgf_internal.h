@@ -34,8 +34,8 @@ struct OpData {
 struct GraphSlot {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t n_proj = nullptr, n_interp = nullptr;
-  cudaKernelNodeParams kp_proj{}, kp_interp{};
+  cudaGraphNode_t n_proj = nullptr, n_interp = nullptr, n_near = nullptr;
+  cudaKernelNodeParams kp_proj{}, kp_interp{}, kp_near{};
   bool ok = false;
 };
 
@@ -116,8 +116,9 @@ struct sgf_ctx {
   int maxnq = 0;
   int debug_mask = 15;
   cudaEvent_t ev[8] = {nullptr};
-  cudaStream_t side = nullptr;  // second stream for the V orientation of the forward map
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side = nullptr;   // second stream for the V orientation of the forward map
+  cudaStream_t side2 = nullptr;  // third stream for the near field of the forward map
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr, ev_join2 = nullptr;
   double stage_ms[8] = {0};
   int launches_per_apply = 0;
   double bytes64 = 0, bytes32 = 0;

@@ -890,30 +890,23 @@ __global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restr
   }
 }
 
-// Combine-lambda + NonIntersecting + Intersecting + EvalSingular + EvalModes + AddOperators. Block
-// per occupied cell: the local densities are staged in shared memory once, each warp streams whole
-// rows of the cell's near block and reconstruction rows, and one thread per row adds the identity
-// and mode terms and writes the result. T = double: all FP64. T = float: FP32 far field; near field,
-// modes and identity in float-float (FP32 pipes; FP64 only for the final conversion).
+// Intersecting + EvalSingular (the block-sparse near operator C, local subtraction folded in) and
+// the sigma/2 identity of AddOperators: out = C mu + sigma/2 mu. Block per work item (chunk of at
+// most 32 target rows of a cell): the densities of the cell's local columns are staged in shared
+// memory once (as float-float for the mixed path), each warp streams whole rows of the cell's near
+// block. It needs nothing but mu, so it runs beside the projection and the FFT convolution; the
+// far-field and mode terms are added afterwards by k_interp_far. T = double: FP64. T = float:
+// float-float on the FP32 pipes, converted to FP64 at the store.
 template <typename T>
-__global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, const int* __restrict__ cell_start,
-                              const int* __restrict__ node_idx, const int* __restrict__ samp_gidx, int pH,
-                              const cplx<T>* __restrict__ phiH, const cplx<T>* __restrict__ phiV,
-                              const cplx<T>* __restrict__ Ip, const int* __restrict__ cols,
-                              const int* __restrict__ coloff, const long* __restrict__ cell_off,
-                              const int* __restrict__ cell_W, const zd* __restrict__ C,
-                              const float4* __restrict__ Cff, const float4* __restrict__ muff,
-                              const zd* __restrict__ MT, const float4* __restrict__ MTff,
-                              const zd* __restrict__ mpart, const float4* __restrict__ mpart_ff, int MB,
-                              const int* __restrict__ item_cell, const int* __restrict__ item_lo,
-                              const int* __restrict__ item_hi, const zd* __restrict__ mu, zd* __restrict__ out) {
+__global__ void k_near_rows(int mask, double half_sigma, const int* __restrict__ cell_start,
+                            const int* __restrict__ node_idx, const int* __restrict__ cols,
+                            const int* __restrict__ coloff, const long* __restrict__ cell_off,
+                            const int* __restrict__ cell_W, const zd* __restrict__ C, const float4* __restrict__ Cff,
+                            const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                            const int* __restrict__ item_hi, const zd* __restrict__ mu, zd* __restrict__ out) {
   constexpr bool FF = sizeof(T) == 4;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ cplx<T> ph[64];
-  __shared__ float4 msf[8];
-  __shared__ zd msd[8];
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
-  // one block per chunk of at most 32 target rows of a cell
   const int q = item_cell[blockIdx.x];
   const int rlo = item_lo[blockIdx.x];
   const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
@@ -923,12 +916,111 @@ __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, con
   float4* musf = reinterpret_cast<float4*>(smem_raw);
   zd* resd = reinterpret_cast<zd*>(smem_raw) + W;
   float4* resf = reinterpret_cast<float4*>(smem_raw) + W;
+  const int* cq = cols + coloff[q];
+  if (mask & 2) {
+    if (FF) {
+      for (int cc = threadIdx.x; cc < W; cc += blockDim.x) musf[cc] = cff_from(mu[cq[cc]]);
+    } else {
+      for (int cc = threadIdx.x; cc < W; cc += blockDim.x) mus[cc] = mu[cq[cc]];
+    }
+  }
+  __syncthreads();
+  for (int il = warp; il < nq; il += nw) {
+    if (FF) {
+      dot2c a = {0.f, 0.f, 0.f, 0.f};
+      if (mask & 2) {
+        const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
+        dot2c b = {0.f, 0.f, 0.f, 0.f}, c2 = {0.f, 0.f, 0.f, 0.f}, d2 = {0.f, 0.f, 0.f, 0.f};
+        int cc = lane;
+        for (; cc + 96 < W; cc += 128) {  // four loads in flight per lane
+          float4 v0 = Cr[cc], v1 = Cr[cc + 32], v2 = Cr[cc + 64], v3 = Cr[cc + 96];
+          dot2_mac(v0, musf[cc], a);
+          dot2_mac(v1, musf[cc + 32], b);
+          dot2_mac(v2, musf[cc + 64], c2);
+          dot2_mac(v3, musf[cc + 96], d2);
+        }
+        for (; cc < W; cc += 32) dot2_mac(Cr[cc], musf[cc], a);
+        dot2_merge(a, b);
+        dot2_merge(c2, d2);
+        dot2_merge(a, c2);
+        for (int o = 16; o > 0; o >>= 1) {
+          dot2c t = {__shfl_down_sync(0xffffffffu, a.sr, o), __shfl_down_sync(0xffffffffu, a.si, o),
+                     __shfl_down_sync(0xffffffffu, a.er, o), __shfl_down_sync(0xffffffffu, a.ei, o)};
+          dot2_merge(a, t);
+        }
+      }
+      if (lane == 0) {
+        ff vr = ff_add({a.sr, 0.f}, {a.er, 0.f}), vi = ff_add({a.si, 0.f}, {a.ei, 0.f});
+        resf[il] = make_float4(vr.hi, vi.hi, vr.lo, vi.lo);
+      }
+    } else {
+      zd acc(0, 0);
+      if (mask & 2) {
+        const zd* Cr = C + cell_off[q] + (long)(rlo + il) * W;
+        zd acc1(0, 0), acc2(0, 0), acc3(0, 0);
+        int cc = lane;
+        for (; cc + 96 < W; cc += 128) {
+          acc = fma_c(Cr[cc], mus[cc], acc);
+          acc1 = fma_c(Cr[cc + 32], mus[cc + 32], acc1);
+          acc2 = fma_c(Cr[cc + 64], mus[cc + 64], acc2);
+          acc3 = fma_c(Cr[cc + 96], mus[cc + 96], acc3);
+        }
+        for (; cc < W; cc += 32) acc = fma_c(Cr[cc], mus[cc], acc);
+        acc = warp_sum((acc + acc1) + (acc2 + acc3));
+      }
+      if (lane == 0) resd[il] = acc;
+    }
+  }
+  __syncthreads();
+  // thread per row: identity term, conversion, store
+  for (int il = threadIdx.x; il < nq; il += blockDim.x) {
+    const int i = node_idx[s0 + il];
+    if (FF) {
+      float4 r = resf[il];
+      ff vr = {r.x, r.z}, vi = {r.y, r.w};
+      if (mask & 8) {
+        float4 m = cff_from(mu[i]);
+        float hs = (float)half_sigma;  // +-1/2: exact scaling
+        vr = ff_add(vr, {hs * m.x, hs * m.z});
+        vi = ff_add(vi, {hs * m.y, hs * m.w});
+      }
+      out[i] = zd(ff_to_double(vr), ff_to_double(vi));
+    } else {
+      zd v = resd[il];
+      if (mask & 8) v += half_sigma * mu[i];
+      out[i] = v;
+    }
+  }
+}
+
+// Combine-lambda + NonIntersecting (PlaneWaveWeights folded into the reconstruction rows Ip) and
+// EvalModes, added to the near-field result already in out. Block per work item: the cell's
+// n_fit samples of the convolved grids are gathered once, each warp reduces rows of Ip against
+// them (four threads per row, blockDim = 128), and one thread per row adds the far-field and mode
+// terms to out[i]. T = float: FP32 far field, float-float mode sums; the final additions are FP64.
+template <typename T>
+__global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__ cell_start,
+                             const int* __restrict__ node_idx, const int* __restrict__ samp_gidx, int pH,
+                             const cplx<T>* __restrict__ phiH, const cplx<T>* __restrict__ phiV,
+                             const cplx<T>* __restrict__ Ip, const zd* __restrict__ MT,
+                             const float4* __restrict__ MTff, const zd* __restrict__ mpart,
+                             const float4* __restrict__ mpart_ff, int MB, const int* __restrict__ item_cell,
+                             const int* __restrict__ item_lo, const int* __restrict__ item_hi,
+                             zd* __restrict__ out) {
+  constexpr bool FF = sizeof(T) == 4;
+  __shared__ cplx<T> ph[64];
+  __shared__ cplx<T> far_s[32];
+  __shared__ float4 msf[8];
+  __shared__ zd msd[8];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
   for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
     long gi = samp_gidx[(long)q * nfit + t];
     ph[t] = t < 2 * (pH + 1) ? phiH[gi] : phiV[gi];
   }
-  // mode sums from their chunk partials (warp per mode)
-  if (warp < nm && (mask & 4)) {
+  if (warp < nm && (mask & 4)) {  // mode sums from their chunk partials (warp per mode)
     if (FF) {
       ff sr = {0.f, 0.f}, si = {0.f, 0.f};
       for (int cch = lane; cch < MB; cch += 32) {
@@ -948,83 +1040,34 @@ __global__ void k_interp_near(int mask, int nfit, int nm, double half_sigma, con
       if (lane == 0) msd[warp] = a;
     }
   }
-  const int* cq = cols + coloff[q];
-  if (FF) {
-    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) musf[cc] = muff[cq[cc]];
-  } else {
-    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) mus[cc] = mu[cq[cc]];
-  }
   __syncthreads();
-  for (int il = warp; il < nq; il += nw) {
-    const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
+  {  // four threads per row (blockDim = 128 covers the 32 rows at once), every 4th sample each
+    const int il = threadIdx.x / 4, part = threadIdx.x % 4;
     cplx<T> far(0, 0);
-    if (mask & 1)
-      for (int t = lane; t < nfit; t += 32) far = fma_c(Ir[t], ph[t], far);
-    far = warp_sum(far);
-    if (FF) {
-      ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
-      if (mask & 2) {
-        const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
-        ff br = {0.f, 0.f}, bi = {0.f, 0.f};
-        int cc = lane;
-        for (; cc + 32 < W; cc += 64) {
-          cff_mac(Cr[cc], musf[cc], ar, ai);
-          cff_mac(Cr[cc + 32], musf[cc + 32], br, bi);
-        }
-        if (cc < W) cff_mac(Cr[cc], musf[cc], ar, ai);
-        ar = ff_add(ar, br);
-        ai = ff_add(ai, bi);
-        for (int o = 16; o > 0; o >>= 1) {
-          ar = ff_add(ar, {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)});
-          ai = ff_add(ai, {__shfl_down_sync(0xffffffffu, ai.hi, o), __shfl_down_sync(0xffffffffu, ai.lo, o)});
-        }
-      }
-      if (lane == 0) {
-        ar = ff_add(ar, {(float)far.re, 0.f});
-        ai = ff_add(ai, {(float)far.im, 0.f});
-        resf[il] = make_float4(ar.hi, ai.hi, ar.lo, ai.lo);
-      }
-    } else {
-      zd acc(0, 0);
-      if (mask & 2) {
-        const zd* Cr = C + cell_off[q] + (long)(rlo + il) * W;
-        zd acc1(0, 0), acc2(0, 0), acc3(0, 0);
-        int cc = lane;
-        for (; cc + 96 < W; cc += 128) {
-          acc = fma_c(Cr[cc], mus[cc], acc);
-          acc1 = fma_c(Cr[cc + 32], mus[cc + 32], acc1);
-          acc2 = fma_c(Cr[cc + 64], mus[cc + 64], acc2);
-          acc3 = fma_c(Cr[cc + 96], mus[cc + 96], acc3);
-        }
-        for (; cc < W; cc += 32) acc = fma_c(Cr[cc], mus[cc], acc);
-        acc = warp_sum((acc + acc1) + (acc2 + acc3));
-      }
-      if (lane == 0) resd[il] = acc + zd((double)far.re, (double)far.im);
+    if (il < nq && (mask & 1)) {
+      const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
+      for (int t = part; t < nfit; t += 4) far = fma_c(Ir[t], ph[t], far);
     }
+    for (int o = 2; o > 0; o >>= 1) {
+      far.re += __shfl_down_sync(0xffffffffu, far.re, o);
+      far.im += __shfl_down_sync(0xffffffffu, far.im, o);
+    }
+    if (part == 0 && il < nq) far_s[il] = far;
   }
   __syncthreads();
-  // thread per row: identity and mode terms, conversion, store
   for (int il = threadIdx.x; il < nq; il += blockDim.x) {
     const int i = node_idx[s0 + il];
-    if (FF) {
-      float4 r = resf[il];
-      ff vr = {r.x, r.z}, vi = {r.y, r.w};
-      if (mask & 8) {
-        float4 m = muff[i];
-        float hs = (float)half_sigma;  // +-1/2: exact scaling
-        vr = ff_add(vr, {hs * m.x, hs * m.z});
-        vi = ff_add(vi, {hs * m.y, hs * m.w});
-      }
-      if (mask & 4)
+    zd v = out[i] + zd((double)far_s[il].re, (double)far_s[il].im);
+    if (mask & 4) {
+      if (FF) {
+        ff vr = {0.f, 0.f}, vi = {0.f, 0.f};
         for (int n = 0; n < nm; ++n) cff_mac(MTff[(long)i * nm + n], msf[n], vr, vi);
-      out[i] = zd(ff_to_double(vr), ff_to_double(vi));
-    } else {
-      zd v = resd[il];
-      if (mask & 8) v += half_sigma * mu[i];
-      if (mask & 4)
+        v += zd(ff_to_double(vr), ff_to_double(vi));
+      } else {
         for (int n = 0; n < nm; ++n) v += MT[(long)i * nm + n] * msd[n];
-      out[i] = v;
+      }
     }
+    out[i] = v;
   }
 }
 
@@ -1109,13 +1152,30 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
   const Orient& oH = c->og[0];
   const Orient& oV = c->og[1];
   long szH = (long)oH.Px * oH.nrow, szV = (long)oV.Px * oV.nrow;
+  const double hs = c->bc == 0 ? 0.5 : -0.5;
+  const size_t smn = (size_t)(c->maxW + 32) * sizeof(zd);
+  cudaFuncSetAttribute(k_near_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn);
+  auto near_rows = [&](cudaStream_t st) {
+    k_near_rows<T><<<c->n_items, 256, smn, st>>>(c->debug_mask, hs, c->d_cell_start, c->d_node_idx, c->d_cols,
+                                                 c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff,
+                                                 c->d_item_cell, c->d_item_lo, c->d_item_hi, mu, out);
+  };
+  // Three concurrent branches when not profiling: the near field (needs only mu) from the start,
+  // and after the projection the H and V convolutions; the far-field/mode kernel joins them.
+  const bool branches = !c->profiling && c->side && c->side2;
+  if (branches) {
+    cudaEventRecord(c->ev_fork0, s);
+    cudaStreamWaitEvent(c->side2, c->ev_fork0, 0);
+    near_rows(c->side2);
+    cudaEventRecord(c->ev_join2, c->side2);
+  }
   if (c->profiling) cudaEventRecord(c->ev[0], s);
   cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(cplx<T>), s);
   cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(cplx<T>), s);
   k_project<T><<<c->n_items + c->nm * c->mode_chunks, 128, (size_t)32 * sizeof(cplx<T>), s>>>(
       c->n_occ, c->neq, c->nm, c->N, c->d_cell_start, c->d_node_idx, mu, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
-      szH, od.grid[1], szV, c->d_MS, c->d_MSff, c->d_mpart, c->d_mpart_ff, sizeof(T) == 4 ? c->d_muff : nullptr,
-      c->mode_chunks, c->n_items, c->d_item_cell, c->d_item_lo, c->d_item_hi);
+      szH, od.grid[1], szV, c->d_MS, c->d_MSff, c->d_mpart, c->d_mpart_ff, nullptr, c->mode_chunks, c->n_items,
+      c->d_item_cell, c->d_item_lo, c->d_item_hi);
   if (c->profiling) cudaEventRecord(c->ev[1], s);
   cudaError_t e;
   if (!c->profiling && c->side) {
@@ -1154,14 +1214,14 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
     }
   }
   if (c->profiling) cudaEventRecord(c->ev[4], s);
-  double hs = c->bc == 0 ? 0.5 : -0.5;
-  size_t smi = (size_t)(c->maxW + 32) * sizeof(zd);
-  cudaFuncSetAttribute(k_interp_near<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
-  k_interp_near<T><<<c->n_items, 256, smi, s>>>(c->debug_mask, c->nfit, c->nm, hs, c->d_cell_start, c->d_node_idx,
-                                              c->d_samp_gidx, c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_cols,
-                                              c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff, c->d_muff,
-                                              c->d_MT, c->d_MTff, c->d_mpart, c->d_mpart_ff, c->mode_chunks, c->d_item_cell,
-                                              c->d_item_lo, c->d_item_hi, mu, out);
+  if (branches)
+    cudaStreamWaitEvent(s, c->ev_join2, 0);
+  else
+    near_rows(s);
+  k_interp_far<T><<<c->n_items, 128, 0, s>>>(c->debug_mask, c->nfit, c->nm, c->d_cell_start, c->d_node_idx,
+                                             c->d_samp_gidx, c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_MT, c->d_MTff,
+                                             c->d_mpart, c->d_mpart_ff, c->mode_chunks, c->d_item_cell, c->d_item_lo,
+                                             c->d_item_hi, out);
   if (c->profiling) cudaEventRecord(c->ev[5], s);
   return cudaGetLastError();
 }
@@ -1443,7 +1503,8 @@ cudaError_t launch_apply_adj32(sgf_ctx* c, const zd* v, zd* out) { return apply_
 // ------------------------------------------------------------------ CUDA graph of the forward map
 // Argument positions of mu / out in k_project and k_interp_near (kept in step with their signatures).
 static const int kProjArgs = 24, kProjMu = 6;
-static const int kInterpArgs = 28, kInterpMu = 26, kInterpOut = 27;
+static const int kNearArgs = 15, kNearMu = 13, kNearOut = 14;
+static const int kFarArgs = 19, kFarOut = 18;
 
 void destroy_graphs(sgf_ctx* c) {
   for (auto& gs : c->gs) {
@@ -1459,7 +1520,11 @@ void destroy_graphs(sgf_ctx* c) {
 cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
   GraphSlot& gs = c->gs[prec == 64 ? 0 : 1];
   cudaStream_t orig = c->stream, cap = nullptr;
-  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  // the projection / convolution chain is the critical path: its nodes get the highest priority,
+  // the near-field branch (side2) the lowest, so that it fills the SMs the chain leaves idle
+  cudaError_t e = cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, prio_hi);
   if (e != cudaSuccess) return e;
   const bool prof = c->profiling;
   const int mask = c->debug_mask;
@@ -1487,7 +1552,8 @@ cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
   std::vector<cudaGraphNode_t> nodes(nn);
   cudaGraphGetNodes(g, nodes.data(), &nn);
   void* fp = prec == 64 ? (void*)k_project<double> : (void*)k_project<float>;
-  void* fi = prec == 64 ? (void*)k_interp_near<double> : (void*)k_interp_near<float>;
+  void* fi = prec == 64 ? (void*)k_interp_far<double> : (void*)k_interp_far<float>;
+  void* fn = prec == 64 ? (void*)k_near_rows<double> : (void*)k_near_rows<float>;
   for (auto nd : nodes) {
     cudaGraphNodeType t;
     cudaGraphNodeGetType(nd, &t);
@@ -1496,13 +1562,14 @@ cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
     cudaGraphKernelNodeGetParams(nd, &kp);
     if (kp.func == fp) { gs.n_proj = nd; gs.kp_proj = kp; }
     if (kp.func == fi) { gs.n_interp = nd; gs.kp_interp = kp; }
+    if (kp.func == fn) { gs.n_near = nd; gs.kp_near = kp; }
   }
-  if (!gs.n_proj || !gs.n_interp) {
+  if (!gs.n_proj || !gs.n_interp || !gs.n_near) {
     cudaGraphDestroy(g);
     gs = GraphSlot();
     return cudaErrorInvalidValue;
   }
-  e = cudaGraphInstantiate(&gs.exec, g, 0);
+  e = cudaGraphInstantiate(&gs.exec, g, cudaGraphInstantiateFlagUseNodePriority);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
     gs = GraphSlot();
@@ -1516,19 +1583,25 @@ cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
 cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out) {
   GraphSlot& gs = c->gs[prec == 64 ? 0 : 1];
   void* pa[kProjArgs];
-  void* pb[kInterpArgs];
+  void* pb[kFarArgs];
+  void* pc[kNearArgs];
   for (int i = 0; i < kProjArgs; ++i) pa[i] = gs.kp_proj.kernelParams[i];
-  for (int i = 0; i < kInterpArgs; ++i) pb[i] = gs.kp_interp.kernelParams[i];
+  for (int i = 0; i < kFarArgs; ++i) pb[i] = gs.kp_interp.kernelParams[i];
+  for (int i = 0; i < kNearArgs; ++i) pc[i] = gs.kp_near.kernelParams[i];
   pa[kProjMu] = (void*)&mu;
-  pb[kInterpMu] = (void*)&mu;
-  pb[kInterpOut] = (void*)&out;
-  cudaKernelNodeParams p1 = gs.kp_proj, p2 = gs.kp_interp;
+  pb[kFarOut] = (void*)&out;
+  pc[kNearMu] = (void*)&mu;
+  pc[kNearOut] = (void*)&out;
+  cudaKernelNodeParams p1 = gs.kp_proj, p2 = gs.kp_interp, p3 = gs.kp_near;
   p1.kernelParams = pa;
   p1.extra = nullptr;
   p2.kernelParams = pb;
   p2.extra = nullptr;
+  p3.kernelParams = pc;
+  p3.extra = nullptr;
   cudaError_t e = cudaGraphExecKernelNodeSetParams(gs.exec, gs.n_proj, &p1);
   if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(gs.exec, gs.n_interp, &p2);
+  if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(gs.exec, gs.n_near, &p3);
   if (e == cudaSuccess) e = cudaGraphLaunch(gs.exec, c->stream);
   return e;
 }
