@@ -191,29 +191,66 @@ __global__ void __launch_bounds__(1024) k_fft_y_full(cplx<T>* __restrict__ g, in
 //   phi^(kx) = IFFT_y( Km^(kx) . FFT_y(xi^(kx)) + Kd^(kx) . FFT_y(zeta^(kx)) )
 // xi, zeta hold nrow rows (zero padded to Py here); the first nrow outputs overwrite xi.
 // K* hold the Py-point spectra per kx, already scaled by 1/(Px Py).
+// Asynchronous global -> shared copy of one element (8 or 16 bytes; cp.async, sm_80 and later) and
+// the wait for all of this thread's outstanding copies.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(cplx<T>* dst_smem, const cplx<T>* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if (sizeof(cplx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// MAXR values per thread (the FFT stages' and the registers' share of the column). ACCG: the
+// partial product K_m FFT(xi) waits in a global scratch column (when shared memory cannot hold a
+// twiddle table next to the column and registers cannot hold the product next to the FFT's own
+// values); otherwise it stays in registers and the twiddles are staged in shared memory. With
+// MAXR = 8 (PF) every global read is issued up front: the spectra K_m, K_d go to registers and the
+// zeta column to a second shared buffer by asynchronous copies, both in flight during the first
+// transform.
 template <typename T, int MAXR, bool ACCG>
 __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ zeta,
                          const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int Py, int la, int lb,
                          int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg) {
-  // Py = 2^la 3^lb; twy: full-circle table of length Py. ACCG: the partial product K_m FFT(xi) waits
-  // in a global scratch column (when shared memory cannot hold a twiddle table next to the column
-  // and registers cannot hold the product next to the FFT's own values); otherwise it stays in
-  // registers and the twiddles are staged in shared memory.
+  constexpr bool PF = !ACCG && MAXR <= 8;
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const long kx = blockIdx.x;
   cplx<T> acc[ACCG ? 1 : MAXR];
+  cplx<T> pkm[PF ? MAXR : 1], pkd[PF ? MAXR : 1];
+  cplx<T>* col = xi + kx * nrow;
+  const cplx<T>* colz = zeta + kx * nrow;
+  const cplx<T>* km = Km + kx * Py;
+  const cplx<T>* kd = Kd + kx * Py;
+  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
+  cplx<T>* s2 = s + 2 * Py;  // PF: the zeta column (after the twiddle table)
+  if (PF) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) {
+      if (i < nrow)
+        cp_async_elem(s2 + i, colz + i);
+      else
+        s2[i] = cplx<T>(0, 0);
+    }
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+      int i = threadIdx.x + r * blockDim.x;
+      if (i < Py) {
+        pkm[PF ? r : 0] = km[i];
+        pkd[PF ? r : 0] = kd[i];
+      }
+    }
+  }
   const cplx<T>* twf = twy;
   if (!ACCG) {
     cplx<T>* tws = s + Py;
     for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
     twf = tws;
   }
-  cplx<T>* col = xi + kx * nrow;
-  const cplx<T>* colz = zeta + kx * nrow;
-  const cplx<T>* km = Km + kx * Py;
-  const cplx<T>* kd = Kd + kx * Py;
-  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
@@ -223,25 +260,31 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
-      if (i < Py) acc[ACCG ? 0 : r] = s[i] * km[i];
+      if (i < Py) acc[ACCG ? 0 : r] = s[i] * (PF ? pkm[PF ? r : 0] : km[i]);
     }
   }
+  cplx<T>* sz = s;
+  if (PF) {
+    cp_async_commit_wait_all();
+    sz = s2;
+  } else {
+    __syncthreads();
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
-  __syncthreads();
-  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
+  smem_fftn<T, MAXR>(sz, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = s[i] * kd[i] + ag[i];
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) sz[i] = sz[i] * kd[i] + ag[i];
   } else {
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
-      if (i < Py) s[i] = s[i] * kd[i] + acc[ACCG ? 0 : r];
+      if (i < Py) sz[i] = sz[i] * (PF ? pkd[PF ? r : 0] : kd[i]) + acc[ACCG ? 0 : r];
     }
   }
   __syncthreads();
-  smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
+  smem_fftn<T, MAXR>(sz, Py, la, lb, 1, 1, 0, twf, Py, +1);
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = sz[i];
 }
 
 // Adjoint of k_conv_y (one block per kx). The forward column map is xi, zeta -> restrict(IFFT(Km

@@ -1081,14 +1081,16 @@ static int conv_regs() {
   return r;
 }
 
-// 3: 8 values per thread, product in registers, twiddles in shared memory (the widest blocks);
+// 3: 8 values per thread, product in registers, twiddles in shared memory (the widest blocks; the
+//    forward kernel also prefetches the spectra and the zeta column);
 // 1: the same with 16 values per thread; 2: 16 values per thread, product in global scratch;
 // 0: no variant fits one block.
 template <typename T, bool ADJ>
 static int conv_y_variant(const Orient& o) {
   const size_t sm = (size_t)o.Py * sizeof(cplx<T>);
   const int t8 = conv_threads(o.Py, 8, o.lb), t16 = conv_threads(o.Py, 16, o.lb);
-  if (t8 <= 1024 && 2 * sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 8, false>() * t8 <= 65536) return 3;
+  const size_t sm8 = (ADJ ? 2 : 3) * sm;  // forward: column, twiddles, prefetched zeta column
+  if (t8 <= 1024 && sm8 <= 200 * 1024 && (long)conv_regs<T, ADJ, 8, false>() * t8 <= 65536) return 3;
   if (t16 > 1024) return 0;
   if (2 * sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, false>() * t16 <= 65536) return 1;
   if (sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, true>() * t16 <= 65536) return 2;
@@ -1104,7 +1106,8 @@ int conv_y_variant_of(const Orient& o, int precision, bool adjoint) {
 template <typename T, bool ADJ, int VPT, bool ACCG>
 static void conv_launch(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
                         const cplx<T>* twy, cplx<T>* accg, int threads, cudaStream_t s) {
-  size_t sm = (size_t)o.Py * sizeof(cplx<T>) * (ACCG ? 1 : 2);  // column (+ twiddle table)
+  // column (+ twiddle table) (+ the prefetched zeta column of the forward 8-value variant)
+  size_t sm = (size_t)o.Py * sizeof(cplx<T>) * (ACCG ? 1 : (!ADJ && VPT <= 8 ? 3 : 2));
   if (ADJ) {
     cudaFuncSetAttribute(k_conv_y_adj<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_conv_y_adj<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
