@@ -51,6 +51,7 @@ static void free_all(sgf_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->o64 = OpData<double>();
+  ctx->keep = BuildKeep();
   ctx->o32 = OpData<float>();
   ctx->built = false;
 }
@@ -596,6 +597,16 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   TRY(dalloc(ctx, &d_phi, (size_t)3 * n_dcy * nfit * 2 * neq));
   CU(launch_phi_off(c, d_phi, dcy_min, n_dcy, d_samp_rel, d_src_rel));
   CU(launch_near(c, d_phi, dcy_min, n_dcy, d_Iplain, pp, d_kress));
+  c->keep.coll_rel = d_coll_rel;
+  c->keep.samp_rel = d_samp_rel;
+  c->keep.kress = d_kress;
+  c->keep.pinv_eq = d_pinv_eq;
+  c->keep.pinv_fb = d_pinv_fb;
+  c->keep.phi = d_phi;
+  c->keep.Iplain = d_Iplain;
+  c->keep.dcy_min = dcy_min;
+  c->keep.n_dcy = n_dcy;
+  c->keep.pp = pp;
 
   // ---------------- adjoint near layout: the rows of cell r collect conj(C) of every block (q, r),
   // blocks in block order, so each adjoint row is again one contiguous stream
@@ -633,6 +644,8 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
       TRY(dalloc(ctx, &d_dst_ld, c->n_blk));
       CU(cudaMemcpy(d_dst_off, dst_off.data(), c->n_blk * sizeof(long), cudaMemcpyHostToDevice));
       CU(cudaMemcpy(d_dst_ld, dst_ld.data(), c->n_blk * sizeof(int), cudaMemcpyHostToDevice));
+      c->keep.tr_off = d_dst_off;
+      c->keep.tr_ld = d_dst_ld;
       TRY(dalloc(ctx, &c->d_cell_offT, c->n_occ + 1));
       TRY(dalloc(ctx, &c->d_cell_WT, c->n_occ));
       TRY(dalloc(ctx, &c->d_colsT, colsT.size()));
@@ -658,6 +671,7 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   }
   double* d_mn;
   TRY(dalloc(ctx, &d_mn, mn.size()));
+  c->keep.modes_n = d_mn;
   CU(cudaMemcpy(d_mn, mn.data(), mn.size() * sizeof(double), cudaMemcpyHostToDevice));
   TRY(dalloc(ctx, &c->d_MT, (size_t)c->N * std::max(1, c->nm)));
   TRY(dalloc(ctx, &c->d_MS, (size_t)c->N * std::max(1, c->nm)));
@@ -1104,5 +1118,195 @@ extern "C" sgf_status sgf_debug_table(const sgf_ctx* ctx_, int lam, int kind, vo
   cudaStreamSynchronize(ctx->stream);
   cudaFree(tmp);
   if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "debug table: %s", cudaGetErrorString(e));
+  return SGF_OK;
+}
+
+// ------------------------------------------------------------------ gradient (discrete adjoint)
+// Derivative of B_n (eq. rayexp) and e_n = beta_n/beta |B_n|^2 with respect to the profile's
+// Fourier coefficients, through the adjoint of the accelerated system A(f) mu = b(f), B_n = w^T mu:
+//   dB_n = (dw)^T mu + lam^T (db - dA mu),   A^T lam = w   (solved as A^H conj(lam) = conj(w)).
+// Each factor of A is node-local: row i of the reconstruction rows, the right-hand side, the target
+// mode factors and the target side of the near operator depend on node i alone; column l of the
+// projection, the source mode factors, w and the source side of the near operator on node l alone;
+// the kernel tables and the FFT convolution on no node. Moving ALL target positions by +-eps thus
+// gives, row by row, the derivative of (A mu)_i with respect to node i's own position, and moving
+// all source positions the derivative of (A^T lam)_l with respect to node l's. The node-local
+// factors are rebuilt at the moved positions with the operator's own kernels and differenced
+// centrally; the f'' dependence (the K_r diagonal) is analytic. Node sensitivities then go to the
+// coefficients through f(x) = a_0 + sum a_m cos(2 pi m x/d) + b_m sin(2 pi m x/d).
+extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
+                                   double* e_n, double* grad_a, double* grad_b, int* adj_iters) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!mu_dev || !grad_a || !grad_b || !(tol > 0) || maxit < 1) return set_err(ctx, SGF_EINVAL, "bad gradient arguments");
+  if (!ctx->adj_ok || !ctx->keep.tr_off) return apply_adj_prec(ctx, nullptr, nullptr, 64);
+  sgf_ctx* c = ctx;
+  const long N = c->N;
+  const int M = (int)c->fa.size() - 1;
+  const int neq = c->neq, nfit = c->nfit;
+  const size_t nmN = (size_t)N * std::max(1, c->nm);
+  // mode parameters of n (as sgf_rayleigh)
+  std::vector<int> ue = ueta_set(c);
+  double an = c->alpha + 2 * SGF_PI * n_mode / c->d;
+  cd bn = beta_host(c->k, an);
+  cd Qn = Qj_host(bn, c->prm.h, c->prm.j);
+  bool inU = std::find(ue.begin(), ue.end(), n_mode) != ue.end();
+  double mp[6] = {an, bn.real(), bn.imag(), Qn.real(), Qn.imag(), inU ? 1.0 : 0.0};
+
+  std::vector<void*> mine;
+  auto al = [&](void** p, size_t bytes) -> sgf_status {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    mine.push_back(*p);
+    return SGF_OK;
+  };
+  double *d_mp, *fp, *f1p;
+  zd *w, *wc, *wp, *lam, *lamc, *y, *bp, *g0, *g1, *Ip2, *Ipl2, *C2, *CT2, *MT2, *MS2, *MSh2, *P2, *dots, *part;
+  sgf_status st = SGF_OK;
+  const size_t zN = N * sizeof(zd);
+  void** ptrs[] = {(void**)&w, (void**)&wc, (void**)&wp, (void**)&lam, (void**)&lamc, (void**)&y, (void**)&bp,
+                   (void**)&g0, (void**)&g1};
+  for (void** pp2 : ptrs)
+    if (st == SGF_OK) st = al(pp2, zN);
+  if (st == SGF_OK) st = al((void**)&d_mp, 6 * sizeof(double));
+  if (st == SGF_OK) st = al((void**)&fp, N * sizeof(double));
+  if (st == SGF_OK) st = al((void**)&f1p, N * sizeof(double));
+  if (st == SGF_OK) st = al((void**)&Ip2, (size_t)nfit * N * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&Ipl2, (size_t)nfit * N * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&C2, (size_t)c->nnz * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&CT2, (size_t)c->nnz * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&MT2, nmN * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&MS2, nmN * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&MSh2, nmN * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&P2, (size_t)4 * neq * N * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&dots, 4 * sizeof(zd));
+  if (st == SGF_OK) st = al((void**)&part, 64 * sizeof(zd));
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    for (void* p : mine) cudaFree(p);
+  };
+  if (st != SGF_OK) {
+    cleanup();
+    return st;
+  }
+  const int mask = c->debug_mask;
+  c->debug_mask = 15;
+  cudaError_t e = cudaSuccess;
+  auto ck = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  const zd* mu = (const zd*)mu_dev;
+  ck(cudaMemcpyAsync(d_mp, mp, sizeof(mp), cudaMemcpyHostToDevice, c->stream));
+  // B_n = sum_l w_l mu_l
+  ck(launch_rayleigh_weights(c, d_mp, c->d_f, c->d_f1, w));
+  ck(launch_conj(w, wc, N, c->stream));
+  ck(launch_dots(wc, 1, N, mu, N, part, 32, dots, c->stream));
+  zd hB;
+  ck(cudaMemcpyAsync(&hB, dots, sizeof(zd), cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  if (e != cudaSuccess) {
+    c->debug_mask = mask;
+    cleanup();
+    return set_err(ctx, SGF_ECUDA, "gradient: %s", cudaGetErrorString(e));
+  }
+  // adjoint system A^H conj(lam) = conj(w)
+  int its = 0;
+  double rr = 1;
+  st = solve_impl(c, wc, true, tol, maxit, y, &its, &rr);
+  if (adj_iters) *adj_iters = its;
+  if (st != SGF_OK) {
+    c->debug_mask = mask;
+    cleanup();
+    return st;
+  }
+  ck(launch_conj(y, lam, N, c->stream));
+  ck(cudaMemcpyAsync(lamc, y, zN, cudaMemcpyDeviceToDevice, c->stream));
+  ck(cudaMemsetAsync(g0, 0, zN, c->stream));
+  ck(cudaMemsetAsync(g1, 0, zN, c->stream));
+  // node sensitivities of f (v = 0) and f' (v = 1) by moved target / source positions
+  const BuildKeep& K = c->keep;
+  for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    double vmax = 1.0;
+    for (long i = 0; i < N; ++i) vmax = std::max(vmax, std::fabs(v == 0 ? c->hf[i] : c->hf1[i]));
+    const double eps = 1e-6 * vmax;
+    zd* g = v == 0 ? g0 : g1;
+    for (int sgn = 1; sgn >= -1 && e == cudaSuccess; sgn -= 2) {
+      const double sc = sgn / (2 * eps);
+      ck(launch_offset(c->d_f, v == 0 ? sgn * eps : 0.0, N, fp, c->stream));
+      ck(launch_offset(c->d_f1, v == 1 ? sgn * eps : 0.0, N, f1p, c->stream));
+      // target side: rows of A mu and b at moved targets
+      ck(launch_build_I_geo(c, K.pinv_fb, Ipl2, K.samp_rel, fp, f1p, Ip2));
+      ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, Ipl2, c->o64.P, K.pp, K.kress, fp, f1p, c->d_f2, c->d_f, c->d_f1,
+                         C2));
+      ck(launch_modes_geo(c, K.modes_n, fp, f1p, MT2, MS2));
+      ck(launch_rhs_geo(c, fp, f1p, bp));
+      std::swap(c->o64.Ip, Ip2);
+      std::swap(c->d_C, C2);
+      std::swap(c->d_MT, MT2);
+      ck(launch_apply64(c, mu, y));
+      std::swap(c->o64.Ip, Ip2);
+      std::swap(c->d_C, C2);
+      std::swap(c->d_MT, MT2);
+      ck(launch_grad_acc(g, sc, lam, bp, y, N, c->stream));
+      // source side: columns of A^T lam and w at moved sources
+      ck(launch_build_P_geo(c, K.pinv_eq, K.coll_rel, fp, f1p, P2));
+      ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, K.Iplain, P2, K.pp, K.kress, c->d_f, c->d_f1, c->d_f2, fp, f1p,
+                         C2));
+      ck(launch_near_transpose(c->n_blk, K.pp.q, K.pp.r, K.pp.off, K.pp.ld, K.tr_off, K.tr_ld, c->d_cell_start, C2,
+                               CT2, c->stream));
+      ck(launch_modes_geo(c, K.modes_n, fp, f1p, MT2, MS2));
+      ck(launch_conj_transpose(MS2, c->nm, N, MSh2, c->stream));
+      ck(launch_rayleigh_weights(c, d_mp, fp, f1p, wp));
+      std::swap(c->o64.P, P2);
+      std::swap(c->d_CT, CT2);
+      std::swap(c->d_MSh, MSh2);
+      ck(launch_apply_adj64(c, lamc, y));
+      std::swap(c->o64.P, P2);
+      std::swap(c->d_CT, CT2);
+      std::swap(c->d_MSh, MSh2);
+      ck(launch_conj(y, y, N, c->stream));
+      ck(launch_grad_acc(g, sc, mu, wp, y, N, c->stream));
+    }
+  }
+  std::vector<zd> h0(N), h1(N), hl(N), hm(N);
+  ck(cudaMemcpyAsync(h0.data(), g0, zN, cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaMemcpyAsync(h1.data(), g1, zN, cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaMemcpyAsync(hl.data(), lam, zN, cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaMemcpyAsync(hm.data(), mu, zN, cudaMemcpyDeviceToHost, c->stream));
+  ck(cudaStreamSynchronize(c->stream));
+  c->debug_mask = mask;
+  cleanup();
+  if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "gradient: %s", cudaGetErrorString(e));
+  // f'' (K_r diagonal, dx f''/(4 pi (1 + f'^2))): analytic; chain rule to the coefficients
+  std::vector<cd> g2(N);
+  for (long i = 0; i < N; ++i) {
+    cd li(hl[i].re, hl[i].im), mi(hm[i].re, hm[i].im);
+    g2[i] = -li * mi * (c->dx / (4 * SGF_PI * (1 + c->hf1[i] * c->hf1[i])));
+  }
+  std::vector<cd> dBa(M + 1, cd(0)), dBb(M + 1, cd(0));
+  for (int m = 0; m <= M; ++m) {
+    double km = 2 * SGF_PI * m / c->d;
+    cd sa(0), sb(0);
+    for (long i = 0; i < N; ++i) {
+      double cs = std::cos(km * c->hx[i]), sn = std::sin(km * c->hx[i]);
+      cd a0(h0[i].re, h0[i].im), a1(h1[i].re, h1[i].im);
+      sa += a0 * cs - a1 * (km * sn) - g2[i] * (km * km * cs);
+      sb += a0 * sn + a1 * (km * cs) - g2[i] * (km * km * sn);
+    }
+    dBa[m] = sa;
+    dBb[m] = m == 0 ? cd(0) : sb;
+  }
+  cd Bn(hB.re, hB.im);
+  bool prop = c->k * c->k - an * an > 0;
+  double pref = prop ? bn.real() / c->beta : 0.0;
+  if (B) {
+    B[0] = Bn.real();
+    B[1] = Bn.imag();
+  }
+  if (e_n) *e_n = pref * std::norm(Bn);
+  for (int m = 0; m <= M; ++m) {
+    grad_a[m] = pref * 2 * std::real(std::conj(Bn) * dBa[m]);
+    grad_b[m] = pref * 2 * std::real(std::conj(Bn) * dBb[m]);
+  }
   return SGF_OK;
 }

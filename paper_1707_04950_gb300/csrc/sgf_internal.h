@@ -39,6 +39,23 @@ struct GraphSlot {
   bool ok = false;
 };
 
+struct NearPairs {  // device arrays of the (q, r) block list
+  int n = 0;
+  int *q = nullptr, *r = nullptr, *wrap = nullptr, *dcx = nullptr, *ld = nullptr;
+  long* off = nullptr;
+};
+
+// Build-time operands kept after sgf_build_operator so that the node-dependent factors (P, I, the
+// near operator, mode factors) can be rebuilt at moved node positions by sgf_gradient.
+struct BuildKeep {
+  double *coll_rel = nullptr, *samp_rel = nullptr, *kress = nullptr, *modes_n = nullptr;
+  zd *pinv_eq = nullptr, *pinv_fb = nullptr, *phi = nullptr, *Iplain = nullptr;
+  long* tr_off = nullptr;  // adjoint near layout: destination offset and leading dimension per block
+  int* tr_ld = nullptr;
+  int dcy_min = 0, n_dcy = 0;
+  NearPairs pp;
+};
+
 struct sgf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -122,6 +139,7 @@ struct sgf_ctx {
   double stage_ms[8] = {0};
   int launches_per_apply = 0;
   double bytes64 = 0, bytes32 = 0;
+  BuildKeep keep;
 };
 
 sgf_status set_err(sgf_ctx* ctx, sgf_status st, const char* fmt, ...);
@@ -137,17 +155,28 @@ cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const do
 cudaError_t launch_tables(sgf_ctx* c);
 cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const double* d_samp_rel,
                            const double* d_src_rel);
-struct NearPairs {  // device arrays of the (q, r) block list
-  int n = 0;
-  int *q = nullptr, *r = nullptr, *wrap = nullptr, *dcx = nullptr, *ld = nullptr;
-  long* off = nullptr;
-};
 cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
                         const double* d_kress);
 cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n);
 cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s);
 cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s);
 cudaError_t launch_rhs(sgf_ctx* c, zd* out);
+// the same builders at given node positions and into given buffers (gradient)
+cudaError_t launch_build_P_geo(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel, const double* f,
+                              const double* f1, zd* P);
+cudaError_t launch_build_I_geo(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel, const double* f,
+                              const double* f1, zd* Ip);
+cudaError_t launch_near_geo(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const zd* P,
+                            const NearPairs& pp, const double* d_kress, const double* ft, const double* f1t,
+                            const double* f2t, const double* fs, const double* f1s, zd* C);
+cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS);
+cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out);
+// w[i] = weight of mu_i in B_n (mp: the 6 mode parameters of sgf_rayleigh) at node positions f, f1
+cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w);
+// gradient helpers: dst = src + eps; y = conj(x); g += s * a .* (u - v)
+cudaError_t launch_offset(const double* src, double eps, long n, double* dst, cudaStream_t s);
+cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s);
+cudaError_t launch_grad_acc(zd* g, double s, const zd* a, const zd* u, const zd* v, long n, cudaStream_t st);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply_adj64(sgf_ctx* c, const zd* v, zd* out);

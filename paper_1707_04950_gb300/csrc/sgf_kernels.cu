@@ -265,13 +265,17 @@ static GeoArgs geo_args(sgf_ctx* c) {
 }
 
 
-cudaError_t launch_build_P(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel) {
+cudaError_t launch_build_P_geo(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel, const double* f,
+                              const double* f1, zd* P) {
   GeoArgs g = geo_args(c);
   size_t sm = (size_t)8 * g.ncoll * sizeof(zd);
   cudaFuncSetAttribute(k_build_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_build_P<<<c->n_occ, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x, c->d_f,
-                                                c->d_f1, d_coll_rel, pinv_eq, c->o64.P);
+  k_build_P<<<c->n_occ, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x, f, f1,
+                                                d_coll_rel, pinv_eq, P);
   return cudaGetLastError();
+}
+cudaError_t launch_build_P(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel) {
+  return launch_build_P_geo(c, pinv_eq, d_coll_rel, c->d_f, c->d_f1, c->o64.P);
 }
 
 // ============================================================== reconstruction rows I
@@ -313,11 +317,15 @@ __global__ void k_build_I(GeoArgs g, const int* __restrict__ node_cell, const in
   }
 }
 
-cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel) {
+cudaError_t launch_build_I_geo(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel, const double* f,
+                              const double* f1, zd* Ip) {
   GeoArgs g = geo_args(c);
   k_build_I<<<ceil_div(c->N, 64), 64, 0, c->stream>>>(g, c->d_node_cell, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x,
-                                                       c->d_f, c->d_f1, d_samp_rel, pinv_fb, d_Iplain, c->o64.Ip);
+                                                       f, f1, d_samp_rel, pinv_fb, d_Iplain, Ip);
   return cudaGetLastError();
+}
+cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel) {
+  return launch_build_I_geo(c, pinv_fb, d_Iplain, d_samp_rel, c->d_f, c->d_f1, c->o64.Ip);
 }
 
 // ============================================================== periodised kernel table
@@ -646,9 +654,12 @@ cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const 
 // ============================================================== near operator blocks
 // Block per (q, r) pair: C_qr[i][l] = phase_r * ( exact (1 - S^f) dG_j/dnu w_l
 //   + S^f (R_s K_s + dx K_r)  [only where S^f > 0]  -  sum_t I_q[i][t] sum_s Phi_off[t][s] P_r[s][l] )
+// Target nodes read (f, f1, f2), source nodes (fs, f1s): the same arrays for the operator itself;
+// a gradient moves the two roles separately (the diagonal belongs to the target).
 __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int* __restrict__ node_idx,
                        const int* __restrict__ occ_cy, const double* __restrict__ x, const double* __restrict__ f,
-                       const double* __restrict__ f1, const double* __restrict__ f2, const zd* __restrict__ phi,
+                       const double* __restrict__ f1, const double* __restrict__ f2, const double* __restrict__ fs,
+                       const double* __restrict__ f1s, const zd* __restrict__ phi,
                        int dcy_min, int n_dcy, const zd* __restrict__ Iplain, const zd* __restrict__ P,
                        const int* __restrict__ pq, const int* __restrict__ pr, const int* __restrict__ pw,
                        const long* __restrict__ poff, const int* __restrict__ pld, const int* __restrict__ pdcx,
@@ -682,7 +693,7 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
     int il = idx / nr, l = idx % nr;
     int i = node_idx[qs + il], ls = node_idx[rs + l];
     double xi = x[i], fi = f[i], f1i = f1[i], si = sqrt(1 + f1i * f1i);
-    double xl = x[ls] + wrap * g.d, fl = f[ls], f1l = f1[ls], sl = sqrt(1 + f1l * f1l);
+    double xl = x[ls] + wrap * g.d, fl = fs[ls], f1l = f1s[ls], sl = sqrt(1 + f1l * f1l);
     double X = xi - xl, Y = fi - fl;
     double rr = hypot(X, Y);
     double Sf = window_S(rr, g.gam, g.a_s);
@@ -716,6 +727,13 @@ cudaError_t near_hk(sgf_ctx* c, zd* hk);
 
 cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
                         const double* d_kress) {
+  return launch_near_geo(c, d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp, d_kress, c->d_f, c->d_f1, c->d_f2, c->d_f,
+                         c->d_f1, c->d_C);
+}
+
+cudaError_t launch_near_geo(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const zd* P,
+                            const NearPairs& pp, const double* d_kress, const double* ft, const double* f1t,
+                            const double* f2t, const double* fs, const double* f1s, zd* C) {
   GeoArgs g = geo_args(c);
   int maxnr = 0;
   for (int q = 0; q < c->n_occ; ++q) maxnr = std::max(maxnr, c->cell_start[q + 1] - c->cell_start[q]);
@@ -725,9 +743,9 @@ cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, con
   zd hk(0, 0);
   cudaError_t e = near_hk(c, &hk);
   if (e != cudaSuccess) return e;
-  k_near<<<pp.n, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cy, c->d_x, c->d_f, c->d_f1, c->d_f2,
-                                       d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp.q, pp.r, pp.wrap, pp.off, pp.ld, pp.dcx,
-                                       d_kress, c->d_binw, hk, c->d_C);
+  k_near<<<pp.n, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cy, c->d_x, ft, f1t, f2t, fs, f1s,
+                                       d_phi, dcy_min, n_dcy, d_Iplain, P, pp.q, pp.r, pp.wrap, pp.off, pp.ld, pp.dcx,
+                                       d_kress, c->d_binw, hk, C);
   return cudaGetLastError();
 }
 
@@ -766,11 +784,14 @@ __global__ void k_modes(GeoArgs g, int nm, const double* __restrict__ mn, const 
   }
 }
 
-cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n) {
+cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS) {
   if (c->nm == 0) return cudaSuccess;
   GeoArgs g = geo_args(c);
-  k_modes<<<ceil_div(c->N, 128), 128, 0, c->stream>>>(g, c->nm, d_modes_n, c->d_x, c->d_f, c->d_f1, c->d_MT, c->d_MS);
+  k_modes<<<ceil_div(c->N, 128), 128, 0, c->stream>>>(g, c->nm, d_modes_n, c->d_x, f, f1, MT, MS);
   return cudaGetLastError();
+}
+cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n) {
+  return launch_modes_geo(c, d_modes_n, c->d_f, c->d_f1, c->d_MT, c->d_MS);
 }
 
 // ============================================================== right-hand side
@@ -785,11 +806,12 @@ __global__ void k_rhs(GeoArgs g, double beta, const double* x, const double* f, 
     out[i] = zd(0, (g.alpha * f1[i] + beta) / s) * u;
   }
 }
-cudaError_t launch_rhs(sgf_ctx* c, zd* out) {
+cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out) {
   GeoArgs g = geo_args(c);
-  k_rhs<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, c->beta, c->d_x, c->d_f, c->d_f1, out);
+  k_rhs<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, c->beta, c->d_x, f, f1, out);
   return cudaGetLastError();
 }
+cudaError_t launch_rhs(sgf_ctx* c, zd* out) { return launch_rhs_geo(c, c->d_f, c->d_f1, out); }
 
 // ============================================================== forward map
 // Mode-sum partials (eq. D_M_deltax, source factors): block (n, chunk) of the grid tail sums
@@ -1637,6 +1659,51 @@ __global__ void k_rayleigh(GeoArgs g, const double* __restrict__ mp, const doubl
     v = warp_sum(v);
     if (lane == 0) B[n] = g.dx * v;
   }
+}
+
+__global__ void k_rayleigh_weights(GeoArgs g, const double* __restrict__ mp, const double* __restrict__ x,
+                                   const double* __restrict__ f, const double* __restrict__ f1, zd* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const double an = mp[0];
+  const zd bn(mp[1], mp[2]), Q(mp[3], mp[4]);
+  const double ind = mp[5];
+  double s = sqrt(1 + f1[i] * f1[i]);
+  zd e = cexpz(-(zd(0, an * x[i]) + zd(0, 1) * (f[i] * bn)));
+  zd W = g.bc == 0 ? (bn - zd(an * f1[i], 0)) * Q * (0.5 / g.d) + zd(s * ind, 0)
+                   : s * (zd(0, 0.5 / g.d) * Q + zd(ind, 0));
+  w[i] = g.dx * (e * W);
+}
+cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w) {
+  GeoArgs g = geo_args(c);
+  k_rayleigh_weights<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, d_mp, c->d_x, f, f1, w);
+  return cudaGetLastError();
+}
+
+__global__ void k_offset(const double* __restrict__ src, double eps, long n, double* __restrict__ dst) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + eps;
+}
+cudaError_t launch_offset(const double* src, double eps, long n, double* dst, cudaStream_t s) {
+  k_offset<<<ceil_div(n, 256), 256, 0, s>>>(src, eps, n, dst);
+  return cudaGetLastError();
+}
+__global__ void k_conj_vec(const zd* __restrict__ x, zd* __restrict__ y, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = conj(x[i]);
+}
+cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s) {
+  k_conj_vec<<<ceil_div(n, 256), 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+__global__ void k_grad_acc(zd* __restrict__ g, double sc, const zd* __restrict__ a, const zd* __restrict__ u,
+                           const zd* __restrict__ v, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) g[i] += sc * (a[i] * (u[i] - v[i]));
+}
+cudaError_t launch_grad_acc(zd* g, double s, const zd* a, const zd* u, const zd* v, long n, cudaStream_t st) {
+  k_grad_acc<<<ceil_div(n, 256), 256, 0, st>>>(g, s, a, u, v, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B) {

@@ -161,6 +161,20 @@ def wl_gaussian_angles(i, N=2048, d=10.0, nx=32, surface_seed=5000, **kw):
     return make_params(prof, 2 * math.pi, 89.0 * i / 63.0, DIRICHLET, N, nx=nx, **kw)
 
 
+def wl_harmonic_gradient(N=4096, d=20.0, n_harm=64, scale=0.05, nx=64, seed=4, **kw):
+    """Gradient workload: sum_{m <= 64} c_m cos + s_m sin with c_m, s_m ~ N(0, (0.05/m)^2), period 20,
+    k = 2 pi, theta = 20 deg, Dirichlet; the efficiency e_0 is differentiated with respect to the
+    128 coefficients."""
+    prof = harmonic_surface(d, n_harm, scale, seed)
+    return make_params(prof, 2 * math.pi, 20.0, DIRICHLET, N, nx=nx, **kw)
+
+
+def wl_harmonic_gradient_small(N=256, d=2.0, n_harm=3, scale=0.05, nx=8, seed=4, bc=DIRICHLET, **kw):
+    """The same kind of surface at period 2 with 3 harmonics: the small gradient parity case."""
+    prof = harmonic_surface(d, n_harm, scale, seed)
+    return make_params(prof, 2 * math.pi, 20.0, bc, N, nx=nx, **kw)
+
+
 def flat(N=64, d=1.0, k=2 * math.pi, theta_deg=20.0, bc=DIRICHLET, nx=8, **kw):
     prof = {"d": float(d), "a": np.zeros(1), "b": np.zeros(1)}
     kw.setdefault("hmin", -0.5 * d / nx)
