@@ -194,6 +194,10 @@ def run_ours(args):
     for op in ops.values():
         op.close()
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
+    grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
+    st32 = res[32]["stages_ms"]
+    cufft = run_cufft_reference(res[32]["info"], st32["fft_x"] + st32["conv_y"] + st32["ifft_x"], dev, stream, flush,
+                                max(3, min(args.steps, 50))) if rank == 0 else None
 
     ms32 = res[32]["ms"]
     if ws > 1:
@@ -246,9 +250,81 @@ def run_ours(args):
     }
     if batch is not None:
         line["batch"] = batch
+    if grad is not None:
+        line["gradient"] = grad
+    if cufft is not None:
+        line["cufft_reference"] = cufft
     if not args.no_cpu_baseline and ws >= 1:
         line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
     print(json.dumps(line), flush=True)
+
+
+def run_cufft_reference(info, ours_ms, dev, stream, flush, steps):
+    """Reference point for the grid convolution stage (X passes, Y convolution, inverse X passes of
+    both orientations): the same zero-padded 2D convolutions done with torch.fft (cuFFT) in complex64
+    on random data of the same shapes, launched one orientation after the other like the profiled
+    stages. cuFFT is not on the library's path; this only calibrates the hand-written FFT stage."""
+    import torch
+
+    g = torch.Generator(device=dev).manual_seed(3)
+    shapes = [(int(info["PxH"]), int(info["nrowH"]), int(info["PyH"])),
+              (int(info["PxV"]), int(info["nrowV"]), int(info["PyV"]))]
+    data = []
+    for Px, nr, Py in shapes:
+        def rnd(*sh):
+            return torch.complex(torch.randn(*sh, generator=g, device=dev), torch.randn(*sh, generator=g, device=dev))
+        data.append((rnd(Px, nr), rnd(Px, nr), rnd(Px, Py), rnd(Px, Py), Py, nr))
+
+    def conv():
+        for xi, ze, km, kd, Py, nr in data:
+            xp = torch.zeros(xi.shape[0], Py, dtype=torch.complex64, device=dev)
+            zp = torch.zeros_like(xp)
+            xp[:, :nr] = xi
+            zp[:, :nr] = ze
+            y = torch.fft.ifft2(km * torch.fft.fft2(xp) + kd * torch.fft.fft2(zp))
+            xi.copy_(y[:, :nr])
+
+    for _ in range(3):
+        conv()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        conv()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    return {"cufft_ms": ms, "ours_ms": ours_ms, "what": "fft_x + conv_y + ifft_x of both orientations, "
+            "complex64, sequential launches (ours: profiled stage events)"}
+
+
+def run_gradient(dev, stream):
+    """The 128-coefficient gradient workload (N = 4096): one forward solve, then sgf_gradient (adjoint
+    solve + node-local rebuilds), against the 2 x 128 solves a difference quotient would need."""
+    import torch
+
+    from paper_1707_04950_gb300 import sgf
+
+    par = inputs.wl_harmonic_gradient()
+    op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=64)
+    mu = torch.zeros(par["N"], dtype=torch.complex128, device=dev)
+    sgf.sgf_solve(op.ctx, 1e-12, 3000, mu.data_ptr())  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 3000, mu.data_ptr())
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    M = len(par["a"]) - 1
+    t0 = time.perf_counter()
+    ga, gb, Bn, en, adj_its = sgf.sgf_gradient(op.ctx, mu.data_ptr(), 0, M)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    op.close()
+    return {"workload": "harmonic64_d20_n4096_theta20_dirichlet", "coefficients": 2 * M, "e0": en,
+            "forward_solve_s": t_solve, "forward_iters": its, "gradient_s": t_grad, "adjoint_iters": adj_its,
+            "grad_norm": float(np.sqrt(np.sum(ga**2) + np.sum(gb**2))),
+            "difference_quotient_equivalent_s": 2 * (2 * M) * t_solve}
 
 
 # GMRES tolerance of the batched solves: the FP64 operator of these rough-surface problems reaches a
@@ -383,6 +459,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
+    ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

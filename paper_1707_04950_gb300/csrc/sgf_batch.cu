@@ -295,9 +295,9 @@ static sgf_status bupdate(sgf_batch* B, BWork& W, zd** wt, int wk, zd** Vt, int 
 
 // Lockstep restarted GMRES from x = 0 on A_p x_p = b_p for every problem, operators of graph slot
 // `slot`, relative tolerance tolv[p]. A problem stops (its iterate freezes) once its residual
-// reaches its tolerance: with true_check, the true residual at the start of a cycle decides (and a
-// cycle that fails to halve it ends the problem: attainable accuracy reached); without, the
-// Arnoldi estimate does (inner solves of the refinement).
+// reaches its tolerance: with true_check the true residual at the start of a cycle decides,
+// without (inner solves of the refinement) the Arnoldi estimate does. A cycle that reduces the true
+// residual by less than 10% also ends the problem (attainable accuracy or stagnation).
 static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, const std::vector<zd*>& xs,
                          const std::vector<double>& tolv, bool true_check, int maxit, std::vector<int>& its,
                          std::vector<double>& rr) {
@@ -334,7 +334,7 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
       double beta = std::sqrt(tmp[p].real());
       res[p] = beta;
       if (!done[p] && beta / bn[p] <= tolv[p]) done[p] = 1;
-      if (!done[p] && true_check && cycles > 0 && beta > 0.5 * prev_true[p]) done[p] = 1;
+      if (!done[p] && cycles > 0 && beta > 0.9 * prev_true[p]) done[p] = 1;  // under 10% progress per cycle
       prev_true[p] = beta;
       sc[p] = done[p] || beta == 0 ? 0.0 : 1.0 / beta;
       for (int i = 0; i <= m; ++i) g[(size_t)p * (m + 1) + i] = 0;

@@ -840,9 +840,9 @@ static sgf_status apply_op(sgf_ctx* ctx, const zd* x, zd* out, int prec, bool ad
 
 // Solves A x = b from x = 0 with operator precision prec; returns applications in *its. With
 // true_check (outer and FP64 solves) a cycle whose Arnoldi estimate reaches tol is followed by the
-// true residual b - A x: if that is still above tol another cycle runs, unless the true residual
-// fell by less than half over the last cycle (stagnation at the attainable accuracy). Without it
-// (inner solves of the refinement) the estimate decides.
+// true residual b - A x: if that is still above tol another cycle runs. Without it (inner solves
+// of the refinement) the estimate decides. Either way a cycle that reduces the true residual by
+// less than 10% ends the solve (attainable accuracy reached, or GMRES(200) stagnating).
 static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b, zd* x, double tol, int maxit,
                         int* its, double* relres, bool true_check = true) {
   const long N = ctx->N;
@@ -865,7 +865,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     double beta = std::sqrt(tmp[0].real());
     res = beta;
     if (beta / bn <= tol) break;
-    if (cycles > 0 && beta > 0.5 * prev_true) break;  // no progress over a whole cycle
+    if (cycles > 0 && beta > 0.9 * prev_true) break;  // under 10% progress over a whole cycle
     prev_true = beta;
     ++cycles;
     CU(cudaMemcpyAsync(K.V, K.r, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));

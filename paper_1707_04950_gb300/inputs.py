@@ -144,7 +144,7 @@ def wl_deep_corrugation_neumann_small(N=1024, nx=32, **kw):
     return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
 
 
-def wl_gaussian_wood(N=8192, nx=40, seed=2, **kw):
+def wl_gaussian_wood(N=8192, nx=64, seed=2, **kw):
     """Gaussian rough surface rms 0.5, correlation length 2, period 40, theta = 85 deg at the
     Wood wavenumber k = 2 pi 80 /(40 (1 + sin 85 deg)) (alpha_-80 = -k)."""
     prof = gaussian_surface(40.0, 0.5, 2.0, seed)

@@ -88,3 +88,26 @@ def test_gradient_full_size_directional_derivative():
     fd = (vals[0] - vals[1]) / (2 * eps)
     dd = float(np.dot(ga, ua) + np.dot(gb, ub))
     assert abs(dd - fd) < 1e-4 * np.sqrt(np.sum(ga**2) + np.sum(gb**2)), (dd, fd)
+
+
+def test_autograd_function_matches_gradient_and_difference_quotient():
+    from paper_1707_04950_gb300.autograd import efficiency
+
+    par = I.wl_harmonic_gradient_small()
+    a = torch.tensor(par["a"], dtype=torch.float64, requires_grad=True)
+    b = torch.tensor(par["b"], dtype=torch.float64, requires_grad=True)
+    e = efficiency(a, b, par, 0)
+    e.backward()
+    ga, gb, en, _ = _gpu_gradient(par)
+    assert abs(float(e) - en) < 1e-12
+    assert np.max(np.abs(a.grad.numpy() - ga)) < 1e-7 * np.max(np.abs(ga))
+    assert np.max(np.abs(b.grad.numpy() - gb)) < 1e-7 * np.max(np.abs(ga))
+    # the forward map of the Function, differenced along a1
+    eps = 1e-6
+    da = torch.zeros_like(a)
+    da[1] = eps
+    with torch.no_grad():
+        ep = efficiency(a + da, b, par, 0)
+        em = efficiency(a - da, b, par, 0)
+    fd = float(ep - em) / (2 * eps)
+    assert abs(fd - ga[1]) < 2e-5 * np.max(np.abs(ga))
