@@ -110,6 +110,11 @@ def stage_bytes(info, s):
 
 
 STAGES = ["project", "fft_x", "conv_y", "ifft_x", "interp_near"]
+# DRAM bytes per launch (read + write) of the mixed-path kernels of each stage, from one ncu capture
+# of the current kernels (profiles/forward_map_deep_corrugation_n16384.md): mean of the H and V
+# launches where a stage has two. None where no capture of the current kernel exists.
+DRAM_BYTES_PER_LAUNCH = {"project": 13.20e6, "fft_x": 4.26e6, "conv_y": 13.75e6, "ifft_x": 2.15e6,
+                         "interp_near": 27.35e6}
 LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "interp_near": 2}
 
 
@@ -241,7 +246,7 @@ def run_ours(args):
         "mixed_rel_err_vs_fp64": mixed_err,
         "stages_ms": stg,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "traffic": None, "peak_kind": kind,
+                     "frac": ach / hbm, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom), "peak_kind": kind,
                      "algorithmic_bytes_per_launch": sb[dom] / LAUNCHES[dom]},
         "e2e": {"value": ws / e2e_s, "unit": "matvecs/s", "h2d_bytes_per_step": 16 * 16384,
                 "d2h_bytes_per_step": 16 * 16384},
