@@ -98,7 +98,8 @@ sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* out_host, int
 /* Right-hand side of eq. discrete_eq at the nodes into out_dev (device complex128, length N). */
 sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev);
 
-/* Algorithm 1: GMRES (restart 200, zero initial guess, CGS2 Arnoldi in FP64) on the system with
+/* Algorithm 1: GMRES (restarted after min(1000, maxit) vectors, fewer if the basis would exceed
+ * 2 GiB; zero initial guess, CGS2 Arnoldi in FP64) on the system with
  * the right-hand side of sgf_rhs; with precision 32 an FP64 residual-refinement loop wraps inner
  * GMRES solves on the mixed operator. Writes the solution to mu_dev; *iters = operator
  * applications, *relres = final ||b - A mu|| / ||b|| with the FP64 operator. Synchronises. */
@@ -171,7 +172,7 @@ const char* sgf_batch_last_error(const sgf_batch* batch);
 sgf_status sgf_batch_apply(sgf_batch* batch, const void* const* mu_devs, void* const* out_devs);
 
 /* Algorithm 1 for every problem on its incident-wave right-hand side (as sgf_solve): restarted GMRES
- * (restart 200, CGS2) in lockstep, one graph launch per Arnoldi step for all problems, one batched
+ * (restart length as sgf_solve, bases within 4 GiB for the batch; CGS2) in lockstep, one graph launch per Arnoldi step for all problems, one batched
  * kernel per Gram-Schmidt pass. If any context uses precision 32, every problem runs FP64 residual
  * refinement around inner solves (tolerance 1e-6) on its own operator. Solutions go to mu_devs[p];
  * host iters[n] and relres[n] (may be NULL) receive operator applications and the final FP64

@@ -444,7 +444,10 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
   for (int p = 0; p < n; ++p)
     if (!mu_devs[p]) return berr(B, SGF_EINVAL, "null buffer for problem %d", p);
   BWork W;
-  W.m = std::min(200, maxit);
+  // restart length: up to 1000 Krylov vectors per problem, within 4 GiB of bases for the batch
+  long sumN = 0;
+  for (int p = 0; p < n; ++p) sumN += B->N[p];
+  W.m = (int)std::max(20L, std::min({1000L, (long)maxit, (4L << 30) / (16L * sumN) - 1}));
   std::vector<void*> mine;
   auto al = [&](zd** ptr, size_t cnt) -> sgf_status {
     cudaError_t e = cudaMalloc((void**)ptr, cnt * sizeof(zd));

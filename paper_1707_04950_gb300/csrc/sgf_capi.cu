@@ -842,7 +842,7 @@ static sgf_status apply_op(sgf_ctx* ctx, const zd* x, zd* out, int prec, bool ad
 // true_check (outer and FP64 solves) a cycle whose Arnoldi estimate reaches tol is followed by the
 // true residual b - A x: if that is still above tol another cycle runs. Without it (inner solves
 // of the refinement) the estimate decides. Either way a cycle that reduces the true residual by
-// less than 10% ends the solve (attainable accuracy reached, or GMRES(200) stagnating).
+// less than 10% ends the solve (attainable accuracy reached, or restarted GMRES stagnating).
 static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b, zd* x, double tol, int maxit,
                         int* its, double* relres, bool true_check = true) {
   const long N = ctx->N;
@@ -944,7 +944,8 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
   if (adj && !ctx->adj_ok) return apply_adj_prec(ctx, nullptr, nullptr, 64);
   const long N = ctx->N;
   Krylov K;
-  K.m = std::min(200, maxit);
+  // restart length: up to 1000 Krylov vectors (unrestarted below that), within 2 GiB of basis
+  K.m = (int)std::max(20L, std::min({1000L, (long)maxit, (2L << 30) / (16L * N) - 1}));
   std::vector<void*> mine;
   auto al = [&](zd** p, size_t n) -> sgf_status {
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(zd));
@@ -954,7 +955,8 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
   };
   sgf_status st = SGF_OK;
   zd *b, *x, *dlt;
-  if ((st = al(&K.V, (size_t)(K.m + 1) * N)) || (st = al(&K.h, 256)) || (st = al(&K.partial, 256 * 32)) ||
+  if ((st = al(&K.V, (size_t)(K.m + 1) * N)) || (st = al(&K.h, (size_t)K.m + 2)) ||
+      (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
       (st = al(&K.r, N)) || (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
     for (void* p : mine) cudaFree(p);
     return st;
