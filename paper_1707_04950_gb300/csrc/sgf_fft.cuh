@@ -156,13 +156,31 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Px = 1 << logPx;
   cplx<T>* tws = s + Px * ty;  // twiddles of this length, staged once per block
-  for (int i = threadIdx.x; i < Px; i += blockDim.x) tws[i] = tw[i << (twlog - logPx)];
   cplx<T>* a = g + blockIdx.y * arr_stride;
   const int iy0 = blockIdx.x * ty;
-  for (int idx = threadIdx.x; idx < Px * ty; idx += blockDim.x) {
-    int t = idx % ty, ix = idx / ty;
-    int iy = iy0 + t;
-    s[ix * ty + t] = (iy < nrow) ? a[(long)ix * nrow + iy] : cplx<T>(0, 0);
+  const int tot = Px * ty;  // <= VPT * blockDim.x (launch rule), as is Px
+  // every global load of the thread (tile element s[ix * ty + t] = s[idx], and twiddles) is
+  // issued before any shared-memory store, so their latencies overlap
+  constexpr int C = VPT < 8 ? VPT : 8;  // values staged per round (bounds the registers)
+#pragma unroll
+  for (int base = 0; base < VPT; base += C) {
+    cplx<T> v[C], tv[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const int idx = threadIdx.x + (base + r) * blockDim.x;
+      v[r] = cplx<T>(0, 0);
+      if (idx < tot) {
+        const int iy = iy0 + idx % ty;
+        if (iy < nrow) v[r] = a[(long)(idx / ty) * nrow + iy];
+      }
+      if (idx < Px) tv[r] = tw[idx << (twlog - logPx)];
+    }
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const int idx = threadIdx.x + (base + r) * blockDim.x;
+      if (idx < tot) s[idx] = v[r];
+      if (idx < Px) tws[idx] = tv[r];
+    }
   }
   __syncthreads();
   smem_fft<T, VPT>(s, logPx, ty, ty, 1, tws, logPx, dir);
@@ -246,12 +264,34 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
     }
   }
   const cplx<T>* twf = twy;
-  if (!ACCG) {
+  if (ACCG) {
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
+  } else {
+    // column and twiddle loads all issued before the shared-memory stores (Py <= MAXR * blockDim.x)
     cplx<T>* tws = s + Py;
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
+    constexpr int C = MAXR < 8 ? MAXR : 8;  // values staged per round (bounds the registers)
+#pragma unroll
+    for (int base = 0; base < MAXR; base += C) {
+      cplx<T> v[C], tv[C];
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const int i = threadIdx.x + (base + r) * blockDim.x;
+        if (i < Py) {
+          v[r] = i < nrow ? col[i] : cplx<T>(0, 0);
+          tv[r] = twy[i];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const int i = threadIdx.x + (base + r) * blockDim.x;
+        if (i < Py) {
+          s[i] = v[r];
+          tws[i] = tv[r];
+        }
+      }
+    }
     twf = tws;
   }
-  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {

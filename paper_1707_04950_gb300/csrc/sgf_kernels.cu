@@ -892,20 +892,23 @@ __global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restr
   const cplx<T>* Pq = P + (long)nout * s0;  // [node][output] rows of this chunk
   (void)ncell;
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    cplx<T> acc(0, 0), acc1(0, 0), acc2(0, 0), acc3(0, 0);
-    int l = 0;
-    for (; l + 3 < nq; l += 4) {
-      acc = fma_c(Pq[(long)l * nout + o], mus[l], acc);
-      acc1 = fma_c(Pq[(long)(l + 1) * nout + o], mus[l + 1], acc1);
-      acc2 = fma_c(Pq[(long)(l + 2) * nout + o], mus[l + 2], acc2);
-      acc3 = fma_c(Pq[(long)(l + 3) * nout + o], mus[l + 3], acc3);
+    // UN loads of P in flight per round (the whole chunk of <= 32 nodes in two rounds for FP32)
+    constexpr int UN = sizeof(T) == 4 ? 16 : 8;
+    cplx<T> acc[4] = {cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0)};
+    for (int l0 = 0; l0 < nq; l0 += UN) {
+      cplx<T> pv[UN];
+#pragma unroll
+      for (int u = 0; u < UN; ++u)
+        if (l0 + u < nq) pv[u] = Pq[(long)(l0 + u) * nout + o];
+#pragma unroll
+      for (int u = 0; u < UN; ++u)
+        if (l0 + u < nq) acc[u & 3] = fma_c(pv[u], mus[l0 + u], acc[u & 3]);
     }
-    for (; l < nq; ++l) acc = fma_c(Pq[(long)l * nout + o], mus[l], acc);
-    acc = (acc + acc1) + (acc2 + acc3);
+    cplx<T> accs = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     int lam = o / (2 * neq), s = o % (2 * neq);
     int si = s % neq;
     long gi = src_gidx[((long)q * 2 + lam) * neq + si];
-    cplx<T> v = acc * src_tw[((long)q * 2 + lam) * neq + si];
+    cplx<T> v = accs * src_tw[((long)q * 2 + lam) * neq + si];
     cplx<T>* base = lam == 0 ? gH + (s < neq ? 0 : gH_stride) : gV + (s < neq ? 0 : gV_stride);
     atomicAdd(&base[gi].re, v.re);
     atomicAdd(&base[gi].im, v.im);

@@ -21,7 +21,7 @@ torch = pytest.importorskip("torch")
 COEFFS = [("a", 0), ("a", 1), ("b", 2), ("a", 3)]
 
 
-def _solve(op, tol=1e-13):
+def _solve(op, tol=1e-12):
     mu = torch.zeros(op.par["N"], dtype=torch.complex128, device="cuda")
     st, its, rr = sgf.sgf_solve(op.ctx, tol, 3000, mu.data_ptr())
     assert st == 0
