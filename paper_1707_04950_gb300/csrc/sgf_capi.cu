@@ -245,7 +245,7 @@ static sgf_status validate(sgf_ctx* ctx) {
   int nfit = 4 * (p.p + 1), nb = 2 * p.n_fb + 1;
   if (nb > 63 || nb > 2 * (p.p + 1) + 2 * (p.p - 1)) return set_err(ctx, SGF_EINVAL, "n_fb too large for the samples");
   if (2 * (p.p + 1 + 2 * p.e) * 2 > p.n_coll) return set_err(ctx, SGF_EINVAL, "n_coll below the number of unknowns");
-  (void)nfit;
+  if (nfit > 64) return set_err(ctx, SGF_EINVAL, "p = %d gives %d cell samples (at most 64)", p.p, nfit);
   return SGF_OK;
 }
 

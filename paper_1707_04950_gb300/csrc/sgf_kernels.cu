@@ -881,6 +881,41 @@ __global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restr
   const int ncell = cell_start[q + 1] - cell_start[q];
   const int lo = item_lo[blockIdx.x], nq = item_hi[blockIdx.x] - lo;
   const int s0 = cell_start[q] + lo;
+  if (sizeof(T) == 4 && 4 * neq <= (int)blockDim.x && nq <= 32) {
+    // FP32 with one output per thread: the thread's column of P for the whole chunk, its grid index
+    // and twist are loaded before the densities (which they do not depend on) arrive
+    const int nout = 4 * neq, o = threadIdx.x;
+    const cplx<T>* Pq = P + (long)nout * s0;
+    cplx<T> pv[32];
+    cplx<T> twv(0, 0);
+    cplx<T>* dst = nullptr;
+    if (o < nout) {
+#pragma unroll
+      for (int u = 0; u < 32; ++u)
+        if (u < nq) pv[u] = Pq[(long)u * nout + o];
+      const int lam = o / (2 * neq), sidx = o % (2 * neq), si = sidx % neq;
+      const long idx = ((long)q * 2 + lam) * neq + si;
+      twv = src_tw[idx];
+      dst = (lam == 0 ? gH + (sidx < neq ? 0 : gH_stride) : gV + (sidx < neq ? 0 : gV_stride)) + src_gidx[idx];
+    }
+    for (int l = threadIdx.x; l < nq; l += blockDim.x) {
+      const int nid = node_idx[s0 + l];
+      const zd m = mu[nid];
+      mus[l] = cplx<T>(m);
+      if (muff) muff[nid] = cff_from(m);
+    }
+    __syncthreads();
+    if (o < nout) {
+      cplx<T> acc[4] = {cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0)};
+#pragma unroll
+      for (int u = 0; u < 32; ++u)
+        if (u < nq) acc[u & 3] = fma_c(pv[u], mus[u], acc[u & 3]);
+      const cplx<T> v = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * twv;
+      atomicAdd(&dst->re, v.re);
+      atomicAdd(&dst->im, v.im);
+    }
+    return;
+  }
   for (int l = threadIdx.x; l < nq; l += blockDim.x) {
     const int nid = node_idx[s0 + l];
     const zd m = mu[nid];
@@ -1041,6 +1076,23 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
   const int q = item_cell[blockIdx.x];
   const int rlo = item_lo[blockIdx.x];
   const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  // loads that do not depend on the gathered samples go out first: this thread's share of its
+  // row of Ip (four threads per row, every 4th sample; n_fit <= 64) and, for the first nq threads,
+  // the row's current out value
+  const int il = threadIdx.x / 4, part = threadIdx.x % 4;
+  cplx<T> ir[16];
+  if (il < nq && (mask & 1)) {
+    const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (part + 4 * k < nfit) ir[k] = Ir[part + 4 * k];
+  }
+  int irow = 0;
+  zd outv(0, 0);
+  if ((int)threadIdx.x < nq) {
+    irow = node_idx[s0 + threadIdx.x];
+    outv = out[irow];
+  }
   for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
     long gi = samp_gidx[(long)q * nfit + t];
     ph[t] = t < 2 * (pH + 1) ? phiH[gi] : phiV[gi];
@@ -1066,12 +1118,12 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
     }
   }
   __syncthreads();
-  {  // four threads per row (blockDim = 128 covers the 32 rows at once), every 4th sample each
-    const int il = threadIdx.x / 4, part = threadIdx.x % 4;
+  {  // four threads per row (blockDim = 128 covers the 32 rows at once)
     cplx<T> far(0, 0);
     if (il < nq && (mask & 1)) {
-      const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
-      for (int t = part; t < nfit; t += 4) far = fma_c(Ir[t], ph[t], far);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (part + 4 * k < nfit) far = fma_c(ir[k], ph[part + 4 * k], far);
     }
     for (int o = 2; o > 0; o >>= 1) {
       far.re += __shfl_down_sync(0xffffffffu, far.re, o);
@@ -1080,9 +1132,9 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
     if (part == 0 && il < nq) far_s[il] = far;
   }
   __syncthreads();
-  for (int il = threadIdx.x; il < nq; il += blockDim.x) {
-    const int i = node_idx[s0 + il];
-    zd v = out[i] + zd((double)far_s[il].re, (double)far_s[il].im);
+  if ((int)threadIdx.x < nq) {
+    const int i = irow;
+    zd v = outv + zd((double)far_s[threadIdx.x].re, (double)far_s[threadIdx.x].im);
     if (mask & 4) {
       if (FF) {
         ff vr = {0.f, 0.f}, vi = {0.f, 0.f};
