@@ -65,10 +65,41 @@ struct StageItems {
 
 // One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences;
 // each thread takes up to U butterflies (every item of the stage is loaded before any store).
+// Index of butterfly idx of a stage: sequence b, position j in it, and j = jq Ns + k. Ns = 2^ns2 3^ns3;
+// shifts and masks replace the divisions wherever the sizes are powers of two (all batched
+// transforms and every radix-8/4/2 stage), and the single factor 3 divides by a constant.
+__device__ __forceinline__ void stage_index(int idx, int nR, int lognR, int batch, int ns2, int ns3, int Ns, int& b,
+                                            int& j, int& jq, int& k) {
+  if (batch == 1) {
+    b = 0;
+    j = idx;
+  } else if (lognR >= 0) {
+    b = idx >> lognR;
+    j = idx & (nR - 1);
+  } else {
+    b = idx / nR;
+    j = idx - b * nR;
+  }
+  if (ns3 == 0) {
+    jq = j >> ns2;
+    k = j & ((1 << ns2) - 1);
+  } else if (ns3 == 1) {
+    jq = (int)((unsigned)(j >> ns2) / 3u);
+    k = j - jq * Ns;
+  } else {
+    jq = j / Ns;
+    k = j - jq * Ns;
+  }
+}
+
+// One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences;
+// each thread takes up to U butterflies (every item of the stage is loaded before any store).
+// Ns = 2^ns2 3^ns3 is the length already transformed; lognR = log2(n/R) when that is an integer.
 template <typename T, int R, int U>
-__device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es, int batch, int bs,
-                                               const cplx<T>* __restrict__ tw, int twlen, int dir) {
-  const int nR = n / R;
+__device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int lognR, int ns2, int ns3, int es, int batch,
+                                               int bs, const cplx<T>* __restrict__ tw, int twlen, int dir) {
+  const int nR = lognR >= 0 ? (1 << lognR) : n / R;
+  const int Ns = (1 << ns2) * (ns3 == 0 ? 1 : (ns3 == 1 ? 3 : 9));
   const int tot = batch * nR;
   const int tstep = twlen / (Ns * R);  // table stride of e^{-2 pi i / (Ns R)} in a table of twlen
   cplx<T> a[U][R];
@@ -76,8 +107,8 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es
   for (int u = 0; u < U; ++u) {
     const int idx = u * blockDim.x + threadIdx.x;
     if (idx < tot) {
-      const int b = idx / nR, j = idx - b * nR;
-      const int k = j % Ns;
+      int b, j, jq, k;
+      stage_index(idx, nR, lognR, batch, ns2, ns3, Ns, b, j, jq, k);
       const cplx<T>* sb = s + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) a[u][r] = sb[(j + r * nR) * es];
@@ -97,9 +128,9 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es
   for (int u = 0; u < U; ++u) {
     const int idx = u * blockDim.x + threadIdx.x;
     if (idx < tot) {
-      const int b = idx / nR, j = idx - b * nR;
-      const int k = j % Ns;
-      const int od = (j / Ns) * Ns * R + k;
+      int b, j, jq, k;
+      stage_index(idx, nR, lognR, batch, ns2, ns3, Ns, b, j, jq, k);
+      const int od = jq * Ns * R + k;
       cplx<T>* sb = s + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) sb[(od + r * Ns) * es] = a[u][r];
@@ -118,23 +149,25 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int Ns, int es
 template <typename T, int VPT = 16>
 __device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, int bs,
                           const cplx<T>* __restrict__ tw, int twlen, int dir) {
-  int Ns = 1, rem = la;
+  int ns2 = 0, ns3 = 0, rem = la;
+  // log2(n / R) for the power-of-two lengths (lb = 0), -1 otherwise
+  auto lognR = [&](int logR) { return lb == 0 ? la - logR : -1; };
   while (rem >= 3) {
-    stockham_stage<T, 8, StageItems<VPT, 8>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
-    Ns <<= 3;
+    stockham_stage<T, 8, StageItems<VPT, 8>::value>(s, n, lognR(3), ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns2 += 3;
     rem -= 3;
   }
   if (rem == 2) {
-    stockham_stage<T, 4, StageItems<VPT, 4>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
-    Ns <<= 2;
+    stockham_stage<T, 4, StageItems<VPT, 4>::value>(s, n, lognR(2), ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns2 += 2;
   }
   if (rem == 1) {
-    stockham_stage<T, 2, StageItems<VPT, 2>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
-    Ns <<= 1;
+    stockham_stage<T, 2, StageItems<VPT, 2>::value>(s, n, lognR(1), ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns2 += 1;
   }
   for (int t = 0; t < lb; ++t) {
-    stockham_stage<T, 3, StageItems<VPT, 3>::value>(s, n, Ns, es, batch, bs, tw, twlen, dir);
-    Ns *= 3;
+    stockham_stage<T, 3, StageItems<VPT, 3>::value>(s, n, -1, ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns3 += 1;
   }
   if (n == 1) __syncthreads();
 }
