@@ -991,15 +991,17 @@ __global__ void k_near_rows(int mask, double half_sigma, const int* __restrict__
       if (mask & 2) {
         const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
         dot2c b = {0.f, 0.f, 0.f, 0.f}, c2 = {0.f, 0.f, 0.f, 0.f}, d2 = {0.f, 0.f, 0.f, 0.f};
-        int cc = lane;
-        for (; cc + 96 < W; cc += 128) {  // four loads in flight per lane
-          float4 v0 = Cr[cc], v1 = Cr[cc + 32], v2 = Cr[cc + 64], v3 = Cr[cc + 96];
-          dot2_mac(v0, musf[cc], a);
-          dot2_mac(v1, musf[cc + 32], b);
-          dot2_mac(v2, musf[cc + 64], c2);
-          dot2_mac(v3, musf[cc + 96], d2);
+        for (int c0 = lane; c0 < W; c0 += 256) {  // up to eight loads in flight per lane
+          float4 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + 32 * u < W) v[u] = Cr[c0 + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int cc = c0 + 32 * u;
+            if (cc < W) dot2_mac(v[u], musf[cc], (u & 3) == 0 ? a : (u & 3) == 1 ? b : (u & 3) == 2 ? c2 : d2);
+          }
         }
-        for (; cc < W; cc += 32) dot2_mac(Cr[cc], musf[cc], a);
         dot2_merge(a, b);
         dot2_merge(c2, d2);
         dot2_merge(a, c2);
