@@ -4,6 +4,12 @@
 #pragma once
 #include "sgf_common.cuh"
 
+// Shared-memory address of element e of a transform buffer: one element of padding after every 16
+// keeps the stride-R stores of the first Stockham stages (and the stride-ty tiles of the X passes)
+// off a single bank group. splen(n) elements hold a padded buffer of n.
+__host__ __device__ __forceinline__ int spad(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int splen(int n) { return n + (n >> 4) + 1; }
+
 // Radix-R DFT in registers, R in {2, 3, 4, 8}; dir = -1 forward, +1 inverse.
 template <typename T, int R>
 __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
@@ -109,9 +115,8 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int lognR, int
     if (idx < tot) {
       int b, j, jq, k;
       stage_index(idx, nR, lognR, batch, ns2, ns3, Ns, b, j, jq, k);
-      const cplx<T>* sb = s + b * bs;
 #pragma unroll
-      for (int r = 0; r < R; ++r) a[u][r] = sb[(j + r * nR) * es];
+      for (int r = 0; r < R; ++r) a[u][r] = s[spad(b * bs + (j + r * nR) * es)];
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -131,9 +136,8 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int lognR, int
       int b, j, jq, k;
       stage_index(idx, nR, lognR, batch, ns2, ns3, Ns, b, j, jq, k);
       const int od = jq * Ns * R + k;
-      cplx<T>* sb = s + b * bs;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sb[(od + r * Ns) * es] = a[u][r];
+      for (int r = 0; r < R; ++r) s[spad(b * bs + (od + r * Ns) * es)] = a[u][r];
     }
   }
   __syncthreads();
@@ -188,7 +192,7 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Px = 1 << logPx;
-  cplx<T>* tws = s + Px * ty;  // twiddles of this length, staged once per block
+  cplx<T>* tws = s + splen(Px * ty);  // twiddles of this length, staged once per block
   cplx<T>* a = g + blockIdx.y * arr_stride;
   const int iy0 = blockIdx.x * ty;
   const int tot = Px * ty;  // <= VPT * blockDim.x (launch rule), as is Px
@@ -211,7 +215,7 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
 #pragma unroll
     for (int r = 0; r < C; ++r) {
       const int idx = threadIdx.x + (base + r) * blockDim.x;
-      if (idx < tot) s[idx] = v[r];
+      if (idx < tot) s[spad(idx)] = v[r];
       if (idx < Px) tws[idx] = tv[r];
     }
   }
@@ -220,7 +224,7 @@ __global__ void k_fft_x(cplx<T>* __restrict__ g, int logPx, int nrow, int ty, lo
   for (int idx = threadIdx.x; idx < Px * ty; idx += blockDim.x) {
     int t = idx % ty, ix = idx / ty;
     int iy = iy0 + t;
-    if (iy < nrow) a[(long)ix * nrow + iy] = s[ix * ty + t];
+    if (iy < nrow) a[(long)ix * nrow + iy] = s[spad(ix * ty + t)];
   }
 }
 
@@ -232,10 +236,10 @@ __global__ void __launch_bounds__(1024) k_fft_y_full(cplx<T>* __restrict__ g, in
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* a = g + (long)blockIdx.x * Py;
-  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = a[i];
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = a[i];
   __syncthreads();
   smem_fftn<T>(s, Py, la, lb, 1, 1, 0, twy, Py, dir);
-  for (int i = threadIdx.x; i < Py; i += blockDim.x) a[i] = s[i];
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) a[i] = s[spad(i)];
 }
 
 // Y-direction convolution of one X-frequency column (one block per kx):
@@ -279,13 +283,13 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   const cplx<T>* km = Km + kx * Py;
   const cplx<T>* kd = Kd + kx * Py;
   cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
-  cplx<T>* s2 = s + 2 * Py;  // PF: the zeta column (after the twiddle table)
+  cplx<T>* s2 = s + splen(Py) + Py;  // PF: the zeta column (after the twiddle table)
   if (PF) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) {
       if (i < nrow)
-        cp_async_elem(s2 + i, colz + i);
+        cp_async_elem(s2 + spad(i), colz + i);
       else
-        s2[i] = cplx<T>(0, 0);
+        s2[spad(i)] = cplx<T>(0, 0);
     }
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
@@ -298,10 +302,10 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   }
   const cplx<T>* twf = twy;
   if (ACCG) {
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   } else {
     // column and twiddle loads all issued before the shared-memory stores (Py <= MAXR * blockDim.x)
-    cplx<T>* tws = s + Py;
+    cplx<T>* tws = s + splen(Py);
     constexpr int C = MAXR < 8 ? MAXR : 8;  // values staged per round (bounds the registers)
 #pragma unroll
     for (int base = 0; base < MAXR; base += C) {
@@ -318,7 +322,7 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
       for (int r = 0; r < C; ++r) {
         const int i = threadIdx.x + (base + r) * blockDim.x;
         if (i < Py) {
-          s[i] = v[r];
+          s[spad(i)] = v[r];
           tws[i] = tv[r];
         }
       }
@@ -328,12 +332,12 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) ag[i] = s[i] * km[i];
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) ag[i] = s[spad(i)] * km[i];
   } else {
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
-      if (i < Py) acc[ACCG ? 0 : r] = s[i] * (PF ? pkm[PF ? r : 0] : km[i]);
+      if (i < Py) acc[ACCG ? 0 : r] = s[spad(i)] * (PF ? pkm[PF ? r : 0] : km[i]);
     }
   }
   cplx<T>* sz = s;
@@ -342,22 +346,22 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
     sz = s2;
   } else {
     __syncthreads();
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = (i < nrow) ? colz[i] : cplx<T>(0, 0);
   }
   __syncthreads();
   smem_fftn<T, MAXR>(sz, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) sz[i] = sz[i] * kd[i] + ag[i];
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) sz[spad(i)] = sz[spad(i)] * kd[i] + ag[i];
   } else {
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
-      if (i < Py) sz[i] = sz[i] * (PF ? pkd[PF ? r : 0] : kd[i]) + acc[ACCG ? 0 : r];
+      if (i < Py) sz[spad(i)] = sz[spad(i)] * (PF ? pkd[PF ? r : 0] : kd[i]) + acc[ACCG ? 0 : r];
     }
   }
   __syncthreads();
   smem_fftn<T, MAXR>(sz, Py, la, lb, 1, 1, 0, twf, Py, +1);
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = sz[i];
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = sz[spad(i)];
 }
 
 // Adjoint of k_conv_y (one block per kx). The forward column map is xi, zeta -> restrict(IFFT(Km
@@ -377,7 +381,7 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
   cplx<T> acc[ACCG ? 1 : MAXR];
   const cplx<T>* twf = twy;
   if (!ACCG) {
-    cplx<T>* tws = s + Py;
+    cplx<T>* tws = s + splen(Py);
     for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
     twf = tws;
   }
@@ -386,39 +390,39 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
   const cplx<T>* km = Km + kx * Py;
   const cplx<T>* kd = Kd + kx * Py;
   cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
-  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = (i < nrow) ? col[i] : cplx<T>(0, 0);
+  for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);
   if (ACCG) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) {
-      cplx<T> v = s[i];
+      cplx<T> v = s[spad(i)];
       ag[i] = v;
-      s[i] = mulc(v, km[i]);
+      s[spad(i)] = mulc(v, km[i]);
     }
   } else {
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
       if (i < Py) {
-        acc[ACCG ? 0 : r] = s[i];
-        s[i] = mulc(acc[ACCG ? 0 : r], km[i]);
+        acc[ACCG ? 0 : r] = s[spad(i)];
+        s[spad(i)] = mulc(acc[ACCG ? 0 : r], km[i]);
       }
     }
   }
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[i];
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) col[i] = s[spad(i)];
   __syncthreads();
   if (ACCG) {
-    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[i] = mulc(ag[i], kd[i]);
+    for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = mulc(ag[i], kd[i]);
   } else {
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) {
       int i = threadIdx.x + r * blockDim.x;
-      if (i < Py) s[i] = mulc(acc[ACCG ? 0 : r], kd[i]);
+      if (i < Py) s[spad(i)] = mulc(acc[ACCG ? 0 : r], kd[i]);
     }
   }
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, +1);
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) colz[i] = s[i];
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) colz[i] = s[spad(i)];
 }

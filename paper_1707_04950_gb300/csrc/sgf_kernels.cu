@@ -486,7 +486,7 @@ cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static size_t fftx_smem(int Px, int ty, size_t esz) { return (size_t)Px * (ty + 1) * esz; }
+static size_t fftx_smem(int Px, int ty, size_t esz) { return ((size_t)splen(Px * ty) + Px) * esz; }
 // Rows per block of the X passes: at least 16 contiguous bytes per column read, enough blocks for
 // two waves of the 152 SMs where the row count allows; threads = Px * ty / 16 (16 values each).
 static int fftx_ty(int Px, int nrow, size_t esz) {
@@ -571,7 +571,7 @@ cudaError_t launch_tables(sgf_ctx* c) {
     // Y transform into the spectra, scaled by 1/(Px Py)
     cudaMemcpyAsync(Tlm, Txm, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
     cudaMemcpyAsync(Tld, Txd, n * sizeof(zd), cudaMemcpyDeviceToDevice, c->stream);
-    size_t sm = (size_t)o.Py * sizeof(zd);
+    size_t sm = (size_t)splen(o.Py) * sizeof(zd);
     cudaFuncSetAttribute(k_fft_y_full<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int ty_threads = conv_threads(o.Py, 16, o.lb);
     k_fft_y_full<double><<<o.Px, ty_threads, sm, c->stream>>>(Tlm, o.Py, o.la, o.lb, c->o64.twy[lam], -1);
@@ -1166,13 +1166,14 @@ static int conv_regs() {
 // 0: no variant fits one block.
 template <typename T, bool ADJ>
 static int conv_y_variant(const Orient& o) {
-  const size_t sm = (size_t)o.Py * sizeof(cplx<T>);
+  // padded column, twiddle table (and the forward 8-value kernel's padded zeta column)
+  const size_t col = (size_t)splen(o.Py) * sizeof(cplx<T>), twb = (size_t)o.Py * sizeof(cplx<T>);
   const int t8 = conv_threads(o.Py, 8, o.lb), t16 = conv_threads(o.Py, 16, o.lb);
-  const size_t sm8 = (ADJ ? 2 : 3) * sm;  // forward: column, twiddles, prefetched zeta column
+  const size_t sm8 = col + twb + (ADJ ? 0 : col);
   if (t8 <= 1024 && sm8 <= 200 * 1024 && (long)conv_regs<T, ADJ, 8, false>() * t8 <= 65536) return 3;
   if (t16 > 1024) return 0;
-  if (2 * sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, false>() * t16 <= 65536) return 1;
-  if (sm <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, true>() * t16 <= 65536) return 2;
+  if (col + twb <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, false>() * t16 <= 65536) return 1;
+  if (col <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, true>() * t16 <= 65536) return 2;
   return 0;
 }
 
@@ -1186,7 +1187,8 @@ template <typename T, bool ADJ, int VPT, bool ACCG>
 static void conv_launch(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
                         const cplx<T>* twy, cplx<T>* accg, int threads, cudaStream_t s) {
   // column (+ twiddle table) (+ the prefetched zeta column of the forward 8-value variant)
-  size_t sm = (size_t)o.Py * sizeof(cplx<T>) * (ACCG ? 1 : (!ADJ && VPT <= 8 ? 3 : 2));
+  const size_t col = (size_t)splen(o.Py) * sizeof(cplx<T>), twb = (size_t)o.Py * sizeof(cplx<T>);
+  size_t sm = ACCG ? col : col + twb + (!ADJ && VPT <= 8 ? col : 0);
   if (ADJ) {
     cudaFuncSetAttribute(k_conv_y_adj<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_conv_y_adj<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
