@@ -8,6 +8,7 @@
 #include <complex>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include "sgf_internal.h"
 
@@ -312,7 +313,11 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
     its[p] = 0;
     if (bn[p] == 0) done[p] = 1;
   }
-  std::vector<cd> H((size_t)n * (m + 1) * m), cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
+  // Hessenberg matrices: every entry is written before it is read, so the (large, mostly untouched
+  // for short solves) storage is left uninitialised; std::complex<double> is laid out as double[2]
+  std::unique_ptr<double[]> Hraw(new double[(size_t)2 * n * (m + 1) * m]);
+  cd* H = reinterpret_cast<cd*>(Hraw.get());
+  std::vector<cd> cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
   std::vector<int> jdone(n, 0);
   std::vector<double> sc(n), prev_true(n, 0.0);
   int total = 0, cycles = 0;

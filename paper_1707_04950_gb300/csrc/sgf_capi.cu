@@ -7,6 +7,7 @@
 #include <cstring>
 #include <set>
 #include <cstdlib>
+#include <memory>
 
 #include "sgf_internal.h"
 
@@ -854,7 +855,11 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   if (bn == 0) { *relres = 0; return SGF_OK; }
   int total = 0;
   double res = bn;
-  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  // Hessenberg matrix: every entry is written before it is read, so its storage stays uninitialised
+  // (std::complex<double> is laid out as double[2])
+  std::unique_ptr<double[]> Hraw(new double[(size_t)2 * (m + 1) * m]);
+  cd* H = reinterpret_cast<cd*>(Hraw.get());
+  std::vector<cd> cs(m), sn(m), g(m + 1), y(m);
   double prev_true = 0;
   int cycles = 0;
   while (total < maxit) {
