@@ -113,7 +113,7 @@ STAGES = ["project", "fft_x", "conv_y", "ifft_x", "interp_near"]
 # DRAM bytes per launch (read + write) of the mixed-path kernels of each stage, from one ncu capture
 # of the current kernels (profiles/forward_map_deep_corrugation_n16384.md): mean of the H and V
 # launches where a stage has two. None where no capture of the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"project": 13.20e6, "fft_x": 4.26e6, "conv_y": 13.75e6, "ifft_x": 2.15e6,
+DRAM_BYTES_PER_LAUNCH = {"project": 13.24e6, "fft_x": 4.26e6, "conv_y": 13.74e6, "ifft_x": 2.15e6,
                          "interp_near": 27.35e6}
 LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "interp_near": 2}
 
