@@ -180,6 +180,21 @@ sgf_status sgf_batch_apply(sgf_batch* batch, const void* const* mu_devs, void* c
 sgf_status sgf_batch_solve(sgf_batch* batch, double tol, int maxit, void* const* mu_devs, int* iters,
                            double* relres);
 
+/* Copy of the parameters currently set (after sgf_autotune_cells: the ones chosen). */
+sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out);
+
+/* Cell-size autotuner (the paper leaves the cell side L to the user within the constraints of
+ * Section 5.1: a < L, non-resonant cells). For the profile, wave and parameters set, tries each cell
+ * count nx_list[i] (cells of side L = d/nx) with the quantities tied to L re-derived: box bottom
+ * hmin = min f - L/2 and rows ny = floor((max f - hmin)/L) + 1, singular window
+ * Ma = floor(0.75 L/dx), shift h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p and h0 the shift set.
+ * Every candidate that builds is timed over `reps` applications; host ms[i] (may be NULL) receives
+ * its time per application in milliseconds, or minus the build status for a candidate that does
+ * not build. The context is left built with the fastest (*best_nx; sgf_get_params gives its
+ * parameters). SGF_EINVAL if no candidate builds (the context is then unbuilt, parameters
+ * restored). Rebuilds the operator several times: a set-up step, not for a hot loop. */
+sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms);
+
 /* Introspection: fills host info[0..19] with N, number of occupied cells, near-field entries,
  * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
  * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec,

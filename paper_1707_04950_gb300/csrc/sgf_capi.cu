@@ -1317,3 +1317,88 @@ extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode,
   }
   return SGF_OK;
 }
+
+// ------------------------------------------------------------------ parameters and cell-size tuning
+extern "C" sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out) {
+  if (!ctx || !out) return SGF_EINVAL;
+  if (!ctx->have_params) return SGF_ESTATE;
+  *out = ctx->prm;
+  return SGF_OK;
+}
+
+// Cell-size autotuner. For each candidate cell count nx the quantities tied to the cell side
+// L = d/nx are re-derived as for the workloads: box bottom hmin = min f - L/2 and rows
+// ny = floor((max f - hmin)/L) + 1, singular window a = floor(0.75 L/dx) dx, shift
+// h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p and h0 the shift currently set. Every candidate
+// that builds is timed over `reps` applications (CUDA events around the context's own launch
+// path), and the context is left built with the fastest.
+extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms) {
+  if (!ctx) return SGF_EINVAL;
+  if (!nx_list || n < 1 || reps < 1) return set_err(ctx, SGF_EINVAL, "bad autotune arguments");
+  if (!ctx->have_profile || !ctx->have_wave || !ctx->have_params)
+    return set_err(ctx, SGF_ESTATE, "profile, wave and params must be set before tuning");
+  const sgf_params base = ctx->prm;
+  const int N = base.N;
+  const double d = ctx->d, dx = d / N;
+  // profile at the nodes x_l = l d / N, l = 1..N
+  double fmin = 1e300, fmax = -1e300;
+  for (int l = 1; l <= N; ++l) {
+    double x = l * dx, f = ctx->fa[0];
+    for (size_t m = 1; m < ctx->fa.size(); ++m) {
+      double t = 2 * SGF_PI * m * x / d;
+      f += ctx->fa[m] * std::cos(t) + ctx->fb[m] * std::sin(t);
+    }
+    fmin = std::min(fmin, f);
+    fmax = std::max(fmax, f);
+  }
+  auto candidate = [&](int nx) {
+    sgf_params P = base;
+    const double L = d / nx;
+    P.nx = nx;
+    P.hmin = fmin - 0.5 * L;
+    P.ny = (int)std::floor((fmax - P.hmin) / L) + 1;
+    P.Ma = (int)std::floor(0.75 * L / dx + 1e-9);
+    const double dg = L / base.p;
+    P.h = (std::round(base.h / dg) + 1.0 / (base.j + 1)) * dg;
+    return P;
+  };
+  double best = 1e300;
+  int bnx = -1;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = -(double)SGF_EINVAL;
+    if (nx_list[i] < 1 || N % nx_list[i] != 0) continue;
+    ctx->prm = candidate(nx_list[i]);
+    sgf_status st = sgf_build_operator(ctx);
+    if (st != SGF_OK) {
+      if (ms) ms[i] = -(double)st;
+      continue;
+    }
+    CU(cudaMemsetAsync(ctx->d_mu_tmp, 0, (size_t)N * sizeof(zd), ctx->stream));
+    for (int w = 0; w < 3; ++w) TRY(apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision));
+    CU(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < reps; ++r) TRY(apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision));
+    CU(cudaEventRecord(e1, ctx->stream));
+    CU(cudaEventSynchronize(e1));
+    float t = 0;
+    CU(cudaEventElapsedTime(&t, e0, e1));
+    double per = t / reps;
+    if (ms) ms[i] = per;
+    if (per < best) {
+      best = per;
+      bnx = nx_list[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bnx < 0) {
+    ctx->prm = base;
+    ctx->built = false;
+    return set_err(ctx, SGF_EINVAL, "no candidate cell count builds for this problem");
+  }
+  if (best_nx) *best_nx = bnx;
+  ctx->prm = candidate(bnx);
+  return sgf_build_operator(ctx);
+}

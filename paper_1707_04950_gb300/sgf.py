@@ -21,7 +21,7 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
-            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_gradient", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_gradient", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve"]
 
 
@@ -66,6 +66,8 @@ def load():
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
         "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
         "sgf_gradient": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
+        "sgf_get_params": [vp, ctypes.POINTER(sgf_params)],
+        "sgf_autotune_cells": [vp, ctypes.POINTER(i), i, i, ctypes.POINTER(i), dp],
         "sgf_info": [vp, dp],
         "sgf_set_profiling": [vp, i],
         "sgf_stage_times": [vp, dp],
@@ -188,6 +190,21 @@ def sgf_gradient(ctx, mu_ptr, n, M, tol=1e-12, maxit=2000):
     _check(ctx, load().sgf_gradient(ctx, ctypes.c_void_p(mu_ptr), int(n), float(tol), int(maxit), _dptr(B), _dptr(en),
                                     _dptr(ga), _dptr(gb), ctypes.byref(its)))
     return ga, gb, B[0] + 1j * B[1], float(en[0]), its.value
+
+
+def sgf_get_params(ctx):
+    p = sgf_params()
+    _check(ctx, load().sgf_get_params(ctx, ctypes.byref(p)))
+    return p
+
+
+def sgf_autotune_cells(ctx, nx_list, reps=20):
+    """Returns (best nx, per-candidate ms per application or minus the build status)."""
+    arr = (ctypes.c_int * len(nx_list))(*[int(x) for x in nx_list])
+    best = ctypes.c_int(0)
+    ms = np.zeros(len(nx_list))
+    _check(ctx, load().sgf_autotune_cells(ctx, arr, len(nx_list), int(reps), ctypes.byref(best), _dptr(ms)))
+    return best.value, ms
 
 
 def sgf_rayleigh_noalloc(ctx, mu_ptr, n_lo, n_hi):
