@@ -200,6 +200,7 @@ def run_ours(args):
         op.close()
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
+    tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
     st32 = res[32]["stages_ms"]
     cufft = run_cufft_reference(res[32]["info"], st32["fft_x"] + st32["conv_y"] + st32["ifft_x"], dev, stream, flush,
                                 max(3, min(args.steps, 50))) if rank == 0 else None
@@ -257,6 +258,8 @@ def run_ours(args):
         line["batch"] = batch
     if grad is not None:
         line["gradient"] = grad
+    if tune is not None:
+        line["autotune"] = tune
     if cufft is not None:
         line["cufft_reference"] = cufft
     if not args.no_cpu_baseline and ws >= 1:
@@ -330,6 +333,20 @@ def run_gradient(dev, stream):
             "forward_solve_s": t_solve, "forward_iters": its, "gradient_s": t_grad, "adjoint_iters": adj_its,
             "grad_norm": float(np.sqrt(np.sum(ga**2) + np.sum(gb**2))),
             "difference_quotient_equivalent_s": 2 * (2 * M) * t_solve}
+
+
+def run_autotune(dev, stream):
+    """Cell-size candidates for the deep corrugation (the benchmark fixes 128 cell columns, the
+    configured 128 x 256 cells): time per mixed application of each candidate."""
+    from paper_1707_04950_gb300 import sgf
+
+    par = inputs.wl_deep_corrugation_neumann()
+    op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=32)
+    cands = [64, 128, 256]
+    best, ms = sgf.sgf_autotune_cells(op.ctx, cands, reps=50)
+    op.close()
+    return {"workload": "deep corrugation N=16384, mixed", "candidates_nx": cands,
+            "ms_per_application": [float(x) if x > 0 else None for x in ms], "best_nx": best}
 
 
 # GMRES tolerance of the batched solves: the FP64 operator of these rough-surface problems reaches a
