@@ -107,7 +107,7 @@ __global__ void k_badd(zd* const* __restrict__ yt, zd* const* __restrict__ xt, c
 // h[p][j] = sum_i conj(V_p[j0 + j][i]) w_p[i], j < m: block per (j, p)
 __global__ void k_bdots(zd* const* __restrict__ Vt, int j0, int m, zd* const* __restrict__ wt, int wk,
                         const long* __restrict__ N, zd* __restrict__ h) {
-  __shared__ zd red[32];
+  SGF_SHARED_ARRAY(zd, red, 32);
   const int j = blockIdx.x, p = blockIdx.y;
   const long n = N[p];
   const zd* v = Vt[p] + (j0 + j) * n;

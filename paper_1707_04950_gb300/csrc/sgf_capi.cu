@@ -1364,10 +1364,13 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
   };
   double best = 1e300;
   int bnx = -1;
-  cudaEvent_t e0, e1;
-  CU(cudaEventCreate(&e0));
-  CU(cudaEventCreate(&e1));
-  for (int i = 0; i < n; ++i) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_err(ctx, SGF_ECUDA, "autotune: event creation failed");
+  }
+  sgf_status fail = SGF_OK;
+  for (int i = 0; i < n && fail == SGF_OK; ++i) {
     if (ms) ms[i] = -(double)SGF_EINVAL;
     if (nx_list[i] < 1 || N % nx_list[i] != 0) continue;
     ctx->prm = candidate(nx_list[i]);
@@ -1376,14 +1379,16 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
       if (ms) ms[i] = -(double)st;
       continue;
     }
-    CU(cudaMemsetAsync(ctx->d_mu_tmp, 0, (size_t)N * sizeof(zd), ctx->stream));
-    for (int w = 0; w < 3; ++w) TRY(apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision));
-    CU(cudaEventRecord(e0, ctx->stream));
-    for (int r = 0; r < reps; ++r) TRY(apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision));
-    CU(cudaEventRecord(e1, ctx->stream));
-    CU(cudaEventSynchronize(e1));
     float t = 0;
-    CU(cudaEventElapsedTime(&t, e0, e1));
+    if (cudaMemsetAsync(ctx->d_mu_tmp, 0, (size_t)N * sizeof(zd), ctx->stream) != cudaSuccess) fail = SGF_ECUDA;
+    for (int w = 0; w < 3 && fail == SGF_OK; ++w) fail = apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision);
+    if (fail == SGF_OK && cudaEventRecord(e0, ctx->stream) != cudaSuccess) fail = SGF_ECUDA;
+    for (int r = 0; r < reps && fail == SGF_OK; ++r)
+      fail = apply_prec(ctx, ctx->d_mu_tmp, ctx->d_out_tmp, ctx->prm.precision);
+    if (fail == SGF_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+      fail = SGF_ECUDA;
+    if (fail != SGF_OK) break;
     double per = t / reps;
     if (ms) ms[i] = per;
     if (per < best) {
@@ -1393,6 +1398,11 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (fail != SGF_OK) {
+    ctx->prm = base;
+    ctx->built = false;
+    return fail == SGF_ECUDA ? set_err(ctx, SGF_ECUDA, "autotune: timing a candidate failed") : fail;
+  }
   if (bnx < 0) {
     ctx->prm = base;
     ctx->built = false;

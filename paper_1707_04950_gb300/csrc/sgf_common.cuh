@@ -62,6 +62,12 @@ __device__ inline cplx<T> warp_sum(cplx<T> v) {
   return v;
 }
 
+// Shared-memory array of n elements of a complex type without running its constructor (every
+// element is written before it is read; shared variables cannot be dynamically initialised).
+#define SGF_SHARED_ARRAY(T, name, n)                                \
+  __shared__ __align__(16) unsigned char name##_raw[(n) * sizeof(T)]; \
+  T* name = reinterpret_cast<T*>(name##_raw)
+
 typedef cplx<double> zd;
 typedef cplx<float> zf;
 

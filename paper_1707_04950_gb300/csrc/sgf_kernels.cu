@@ -821,7 +821,7 @@ __device__ __forceinline__ void mode_partial(int n, int chunk, int MB, long N, c
                                              const zd* __restrict__ MS, const float4* __restrict__ MSff,
                                              zd* __restrict__ mpart, float4* __restrict__ mpart_ff) {
   __shared__ float4 redf[32];
-  __shared__ zd redd[32];
+  SGF_SHARED_ARRAY(zd, redd, 32);
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const long len = (N + MB - 1) / MB, i0 = chunk * len, i1 = min(N, i0 + len);
   if (sizeof(T) == 4) {
@@ -1070,11 +1070,11 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
                              const int* __restrict__ item_lo, const int* __restrict__ item_hi,
                              zd* __restrict__ out) {
   constexpr bool FF = sizeof(T) == 4;
-  __shared__ cplx<T> ph[64];
-  __shared__ cplx<T> far_s[32];
+  SGF_SHARED_ARRAY(cplx<T>, ph, 64);
+  SGF_SHARED_ARRAY(cplx<T>, far_s, 32);
   __shared__ float4 msf[8];
-  __shared__ zd msd[8];
-  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  SGF_SHARED_ARRAY(zd, msd, 8);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
   const int q = item_cell[blockIdx.x];
   const int rlo = item_lo[blockIdx.x];
   const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
@@ -1371,7 +1371,7 @@ __global__ void k_interp_adj(int mask, int nfit, long N, int pH, const int* __re
                              float4* __restrict__ mpart_ff, float4* __restrict__ vff, int MB, int n_items,
                              const int* __restrict__ item_cell, const int* __restrict__ item_lo,
                              const int* __restrict__ item_hi, const zd* __restrict__ v) {
-  __shared__ cplx<T> vs[32];
+  SGF_SHARED_ARRAY(cplx<T>, vs, 32);
   if ((int)blockIdx.x >= n_items) {
     const int t = blockIdx.x - n_items;
     mode_partial<T>(t / MB, t % MB, MB, N, v, MTh, MThff, mpart, mpart_ff);
@@ -1419,7 +1419,7 @@ __global__ void k_project_adj(int mask, int neq, int nm, double half_sigma, cons
   constexpr bool FF = sizeof(T) == 4;
   extern __shared__ unsigned char smem_raw[];
   __shared__ float4 msf[8];
-  __shared__ zd msd[8];
+  SGF_SHARED_ARRAY(zd, msd, 8);
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const int q = item_cell[blockIdx.x];
   const int rlo = item_lo[blockIdx.x];
@@ -1696,7 +1696,7 @@ cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out) {
 __global__ void k_rayleigh(GeoArgs g, const double* __restrict__ mp, const double* __restrict__ x,
                            const double* __restrict__ f, const double* __restrict__ f1, const zd* __restrict__ mu,
                            zd* B) {
-  __shared__ zd red[32];
+  SGF_SHARED_ARRAY(zd, red, 32);
   const int n = blockIdx.x;
   const double an = mp[6 * n];
   const zd bn(mp[6 * n + 1], mp[6 * n + 2]), Q(mp[6 * n + 3], mp[6 * n + 4]);
@@ -1775,7 +1775,7 @@ cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const doubl
 // partial[j][blk] = sum_{i in chunk blk} conj(V[j][i]) w[i]; then out[j] = sum_blk partial.
 __global__ void k_dots_partial(const zd* __restrict__ V, long ldv, const zd* __restrict__ w, long n, zd* partial,
                                int nblk) {
-  __shared__ zd red[32];
+  SGF_SHARED_ARRAY(zd, red, 32);
   const int j = blockIdx.y, blk = blockIdx.x;
   long chunk = (n + nblk - 1) / nblk;
   long i0 = blk * chunk, i1 = min(n, i0 + chunk);
