@@ -138,16 +138,26 @@ sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int 
  * the profile's Fourier coefficients a_0..a_M, b_1..b_M (as set by sgf_set_profile_fourier), for the
  * accelerated discrete system. The paper solves forward problems only; this is its discrete adjoint:
  * dB_n = (dw)^T mu + lam^T (db - dA mu) with B_n = w^T mu and A^T lam = w, lam from one adjoint GMRES
- * solve (tol, maxit as sgf_solve_rhs). The node-local factors of A, b and w are rebuilt with the
- * operator's own kernels at positions moved by +-1e-6 max(1, max|f|) (and likewise f') and
- * differenced centrally, all nodes at once (each factor depends on one node only); the f'' term
- * of the K_r diagonal is analytic. mu_dev: the solution of sgf_solve (device complex128, length N).
- * Host outputs: grad_a[M+1], grad_b[M+1] (grad_b[0] = 0), B[2] = B_n (may be NULL), *e_n (may be
- * NULL; 0 with a zero gradient for an evanescent n), *adj_iters (may be NULL). The operator's cell
- * assignment is that of the build; the gradient is that of the operator with this assignment.
+ * solve (tol, maxit as sgf_solve_rhs). Every factor of A, b and w depends on one node's position
+ * (f, f'), so their derivatives are built analytically, node by node, with the operator's own
+ * kernels in derivative mode (Hessian of the shifted Green function for the projection and the near
+ * operator, Fourier-Bessel recurrences for the reconstruction rows, derivatives of the window, of the
+ * log-singular coefficient and of the mode, incidence and Rayleigh factors), and applied through
+ * the forward and adjoint maps; the f'' term of the K_r diagonal is analytic; the chain rule maps
+ * node sensitivities to the coefficients. mu_dev: the solution of sgf_solve (device complex128,
+ * length N). Host outputs: grad_a[M+1], grad_b[M+1] (grad_b[0] = 0), B[2] = B_n (may be NULL), *e_n
+ * (may be NULL; 0 with a zero gradient for an evanescent n), *adj_iters (may be NULL). The cell
+ * assignment is that of the build: the gradient is that of the operator with this assignment.
  * Synchronises. */
 sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n, double tol, int maxit, double* B, double* e_n,
                         double* grad_a, double* grad_b, int* adj_iters);
+
+/* The same gradient with the node derivatives taken as central differences of the factors rebuilt
+ * at all target (or all source) positions moved by +-1e-6 max(1, max|v|), v = f, f' (each factor
+ * depends on one node, so one pair of rebuilds gives every node's derivative): a cross-check of
+ * sgf_gradient. Same arguments. */
+sgf_status sgf_gradient_fd(sgf_ctx* ctx, const void* mu_dev, int n, double tol, int maxit, double* B, double* e_n,
+                           double* grad_a, double* grad_b, int* adj_iters);
 
 /* ------------------------------------------------------------------------------------------------
  * Batches of independent problems (different surfaces, wavenumbers or incidence angles, each in its

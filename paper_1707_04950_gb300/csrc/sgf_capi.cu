@@ -1141,8 +1141,8 @@ extern "C" sgf_status sgf_debug_table(const sgf_ctx* ctx_, int lam, int kind, vo
 // factors are rebuilt at the moved positions with the operator's own kernels and differenced
 // centrally; the f'' dependence (the K_r diagonal) is analytic. Node sensitivities then go to the
 // coefficients through f(x) = a_0 + sum a_m cos(2 pi m x/d) + b_m sin(2 pi m x/d).
-extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
-                                   double* e_n, double* grad_a, double* grad_b, int* adj_iters) {
+static sgf_status gradient_impl(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
+                                double* e_n, double* grad_a, double* grad_b, int* adj_iters, bool analytic) {
   if (!ctx) return SGF_EINVAL;
   if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (!mu_dev || !grad_a || !grad_b || !(tol > 0) || maxit < 1) return set_err(ctx, SGF_EINVAL, "bad gradient arguments");
@@ -1205,7 +1205,7 @@ extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode,
   const zd* mu = (const zd*)mu_dev;
   ck(cudaMemcpyAsync(d_mp, mp, sizeof(mp), cudaMemcpyHostToDevice, c->stream));
   // B_n = sum_l w_l mu_l
-  ck(launch_rayleigh_weights(c, d_mp, c->d_f, c->d_f1, w));
+  ck(launch_rayleigh_weights(c, d_mp, c->d_f, c->d_f1, w, 0));
   ck(launch_conj(w, wc, N, c->stream));
   ck(launch_dots(wc, 1, N, mu, N, part, 32, dots, c->stream));
   zd hB;
@@ -1230,49 +1230,62 @@ extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode,
   ck(cudaMemcpyAsync(lamc, y, zN, cudaMemcpyDeviceToDevice, c->stream));
   ck(cudaMemsetAsync(g0, 0, zN, c->stream));
   ck(cudaMemsetAsync(g1, 0, zN, c->stream));
-  // node sensitivities of f (v = 0) and f' (v = 1) by moved target / source positions
+  // node sensitivities of f (v = 0) and f' (v = 1): g_v = lam .* (db - dA_t mu) + mu .* (dw - dA_s^T lam)
   const BuildKeep& K = c->keep;
+  // one evaluation of the target and source terms with the factors in the given buffers (derivative
+  // factors, or the factors at moved positions), accumulated into g with weight sc
+  auto terms = [&](zd* g, double sc, int dm_t, int dm_s, const double* ft, const double* f1t, const double* fs,
+                   const double* f1s, int mask_apply) {
+    ck(launch_build_I_geo(c, K.pinv_fb, Ipl2, K.samp_rel, ft, f1t, Ip2, dm_t));
+    ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, Ipl2, c->o64.P, K.pp, K.kress, ft, f1t, c->d_f2, c->d_f, c->d_f1,
+                       C2, dm_t));
+    ck(launch_modes_geo(c, K.modes_n, ft, f1t, MT2, MS2, dm_t));
+    ck(launch_rhs_geo(c, ft, f1t, bp, dm_t));
+    std::swap(c->o64.Ip, Ip2);
+    std::swap(c->d_C, C2);
+    std::swap(c->d_MT, MT2);
+    c->debug_mask = mask_apply;
+    ck(launch_apply64(c, mu, y));
+    c->debug_mask = 15;
+    std::swap(c->o64.Ip, Ip2);
+    std::swap(c->d_C, C2);
+    std::swap(c->d_MT, MT2);
+    ck(launch_grad_acc(g, sc, lam, bp, y, N, c->stream));
+    ck(launch_build_P_geo(c, K.pinv_eq, K.coll_rel, fs, f1s, P2, dm_s == 0 ? 0 : dm_s - 2));
+    ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, K.Iplain, P2, K.pp, K.kress, c->d_f, c->d_f1, c->d_f2, fs, f1s,
+                       C2, dm_s));
+    ck(launch_near_transpose(c->n_blk, K.pp.q, K.pp.r, K.pp.off, K.pp.ld, K.tr_off, K.tr_ld, c->d_cell_start, C2,
+                             CT2, c->stream));
+    ck(launch_modes_geo(c, K.modes_n, fs, f1s, MT2, MS2, dm_s == 0 ? 0 : dm_s - 2));
+    ck(launch_conj_transpose(MS2, c->nm, N, MSh2, c->stream));
+    ck(launch_rayleigh_weights(c, d_mp, fs, f1s, wp, dm_s == 0 ? 0 : dm_s - 2));
+    std::swap(c->o64.P, P2);
+    std::swap(c->d_CT, CT2);
+    std::swap(c->d_MSh, MSh2);
+    c->debug_mask = mask_apply;
+    ck(launch_apply_adj64(c, lamc, y));
+    c->debug_mask = 15;
+    std::swap(c->o64.P, P2);
+    std::swap(c->d_CT, CT2);
+    std::swap(c->d_MSh, MSh2);
+    ck(launch_conj(y, y, N, c->stream));
+    ck(launch_grad_acc(g, sc, mu, wp, y, N, c->stream));
+  };
   for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    zd* g = v == 0 ? g0 : g1;
+    if (analytic) {
+      // derivative factors at the nodes' positions; the applications leave out the sigma/2 identity,
+      // which does not depend on the nodes
+      terms(g, 1.0, v + 1, v + 3, c->d_f, c->d_f1, c->d_f, c->d_f1, 7);
+      continue;
+    }
     double vmax = 1.0;
     for (long i = 0; i < N; ++i) vmax = std::max(vmax, std::fabs(v == 0 ? c->hf[i] : c->hf1[i]));
     const double eps = 1e-6 * vmax;
-    zd* g = v == 0 ? g0 : g1;
     for (int sgn = 1; sgn >= -1 && e == cudaSuccess; sgn -= 2) {
-      const double sc = sgn / (2 * eps);
       ck(launch_offset(c->d_f, v == 0 ? sgn * eps : 0.0, N, fp, c->stream));
       ck(launch_offset(c->d_f1, v == 1 ? sgn * eps : 0.0, N, f1p, c->stream));
-      // target side: rows of A mu and b at moved targets
-      ck(launch_build_I_geo(c, K.pinv_fb, Ipl2, K.samp_rel, fp, f1p, Ip2));
-      ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, Ipl2, c->o64.P, K.pp, K.kress, fp, f1p, c->d_f2, c->d_f, c->d_f1,
-                         C2));
-      ck(launch_modes_geo(c, K.modes_n, fp, f1p, MT2, MS2));
-      ck(launch_rhs_geo(c, fp, f1p, bp));
-      std::swap(c->o64.Ip, Ip2);
-      std::swap(c->d_C, C2);
-      std::swap(c->d_MT, MT2);
-      ck(launch_apply64(c, mu, y));
-      std::swap(c->o64.Ip, Ip2);
-      std::swap(c->d_C, C2);
-      std::swap(c->d_MT, MT2);
-      ck(launch_grad_acc(g, sc, lam, bp, y, N, c->stream));
-      // source side: columns of A^T lam and w at moved sources
-      ck(launch_build_P_geo(c, K.pinv_eq, K.coll_rel, fp, f1p, P2));
-      ck(launch_near_geo(c, K.phi, K.dcy_min, K.n_dcy, K.Iplain, P2, K.pp, K.kress, c->d_f, c->d_f1, c->d_f2, fp, f1p,
-                         C2));
-      ck(launch_near_transpose(c->n_blk, K.pp.q, K.pp.r, K.pp.off, K.pp.ld, K.tr_off, K.tr_ld, c->d_cell_start, C2,
-                               CT2, c->stream));
-      ck(launch_modes_geo(c, K.modes_n, fp, f1p, MT2, MS2));
-      ck(launch_conj_transpose(MS2, c->nm, N, MSh2, c->stream));
-      ck(launch_rayleigh_weights(c, d_mp, fp, f1p, wp));
-      std::swap(c->o64.P, P2);
-      std::swap(c->d_CT, CT2);
-      std::swap(c->d_MSh, MSh2);
-      ck(launch_apply_adj64(c, lamc, y));
-      std::swap(c->o64.P, P2);
-      std::swap(c->d_CT, CT2);
-      std::swap(c->d_MSh, MSh2);
-      ck(launch_conj(y, y, N, c->stream));
-      ck(launch_grad_acc(g, sc, mu, wp, y, N, c->stream));
+      terms(g, sgn / (2 * eps), 0, 0, fp, f1p, fp, f1p, 15);
     }
   }
   std::vector<zd> h0(N), h1(N), hl(N), hm(N);
@@ -1411,4 +1424,14 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
   if (best_nx) *best_nx = bnx;
   ctx->prm = candidate(bnx);
   return sgf_build_operator(ctx);
+}
+
+extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
+                                   double* e_n, double* grad_a, double* grad_b, int* adj_iters) {
+  return gradient_impl(ctx, mu_dev, n_mode, tol, maxit, B, e_n, grad_a, grad_b, adj_iters, true);
+}
+
+extern "C" sgf_status sgf_gradient_fd(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
+                                      double* e_n, double* grad_a, double* grad_b, int* adj_iters) {
+  return gradient_impl(ctx, mu_dev, n_mode, tol, maxit, B, e_n, grad_a, grad_b, adj_iters, false);
 }

@@ -139,6 +139,32 @@ __device__ inline GreenVal green_j(double k, int j, double h, double X, double Y
   return acc;
 }
 
+// G_j with its gradient and the Y-derivatives of the gradient (G_xy, G_yy), for the analytic node
+// derivatives of the gradient computation. Per source: G = (i/4) H0(kr), G_x = c X, G_y = c Y with
+// c(r) = -(ik/4) H1(kr)/r and c'(r) = -(ik/4)(k H0(kr)/r - 2 H1(kr)/r^2) (H0' = -H1,
+// H1'(z) = H0(z) - H1(z)/z), so G_xy = c' X Y/r and G_yy = c + c' Y^2/r.
+struct GreenHess {
+  zd g, gx, gy, gxy, gyy;
+};
+__device__ inline void green0_hess_add(double k, double X, double Y, double w, GreenHess& a) {
+  double r = hypot(X, Y), kr = k * r;
+  zd h0 = hankel0(kr), h1 = hankel1(kr);
+  zd ih0(-h0.im, h0.re), ih1(-h1.im, h1.re);
+  zd c = (-0.25 * k / r) * ih1;
+  zd dc = (-0.25 * k) * ((k / r) * ih0 - (2.0 / (r * r)) * ih1);
+  a.g += (0.25 * w) * ih0;
+  a.gx += (w * X) * c;
+  a.gy += (w * Y) * c;
+  a.gxy += (w * X * Y / r) * dc;
+  a.gyy += w * (c + (Y * Y / r) * dc);
+}
+__device__ inline GreenHess green_j_hess(double k, int j, double h, double X, double Y, const double* binw) {
+  GreenHess a;
+  a.g = a.gx = a.gy = a.gxy = a.gyy = zd(0, 0);
+  for (int m = 0; m <= j; ++m) green0_hess_add(k, X, Y + m * h, binw[m], a);
+  return a;
+}
+
 // S_{gamma,a}(x) of eq. S_def.
 __host__ __device__ inline double window_S(double x, double gamma, double a) {
   x = fabs(x);
@@ -146,6 +172,17 @@ __host__ __device__ inline double window_S(double x, double gamma, double a) {
   if (x >= a) return 0.0;
   double u = (x - gamma) / (a - gamma);
   return exp(2.0 * exp(-1.0 / u) / (u - 1.0));
+}
+
+// dS_{gamma,a}/dx for x >= 0: with u = (x - gamma)/(a - gamma) and S = exp(2 e^{-1/u}/(u - 1)),
+// dS/dx = S 2 e^{-1/u} ((u - 1)/u^2 - 1)/(u - 1)^2 / (a - gamma) on (gamma, a), 0 elsewhere.
+__host__ __device__ inline double window_S_dx(double x, double gamma, double a) {
+  x = fabs(x);
+  if (x <= gamma || x >= a) return 0.0;
+  double u = (x - gamma) / (a - gamma);
+  double e = exp(-1.0 / u);
+  double S = exp(2.0 * e / (u - 1.0));
+  return S * 2.0 * e * ((u - 1.0) / (u * u) - 1.0) / ((u - 1.0) * (u - 1.0)) / (a - gamma);
 }
 
 // ---------------------------------------------------------------- float-float arithmetic

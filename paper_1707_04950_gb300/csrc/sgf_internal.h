@@ -161,18 +161,22 @@ cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n);
 cudaError_t launch_to_f32(const zd* src, zf* dst, long n, cudaStream_t s);
 cudaError_t launch_split_ff(const zd* src, float4* dst, long n, cudaStream_t s);
 cudaError_t launch_rhs(sgf_ctx* c, zd* out);
-// the same builders at given node positions and into given buffers (gradient)
+// The same builders at given node positions and into given buffers (gradient). dmode 0 builds the
+// factors; 1 / 2 their derivatives with respect to each node's own f / f' (for the near operator
+// 1 / 2 move the target node, 3 / 4 the source node).
 cudaError_t launch_build_P_geo(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel, const double* f,
-                              const double* f1, zd* P);
+                              const double* f1, zd* P, int dmode);
 cudaError_t launch_build_I_geo(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel, const double* f,
-                              const double* f1, zd* Ip);
+                              const double* f1, zd* Ip, int dmode);
 cudaError_t launch_near_geo(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const zd* P,
                             const NearPairs& pp, const double* d_kress, const double* ft, const double* f1t,
-                            const double* f2t, const double* fs, const double* f1s, zd* C);
-cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS);
-cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out);
+                            const double* f2t, const double* fs, const double* f1s, zd* C, int dmode);
+cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS,
+                             int dmode);
+cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out, int dmode);
 // w[i] = weight of mu_i in B_n (mp: the 6 mode parameters of sgf_rayleigh) at node positions f, f1
-cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w);
+cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w,
+                                    int dmode);
 // gradient helpers: dst = src + eps; y = conj(x); g += s * a .* (u - v)
 cudaError_t launch_offset(const double* src, double eps, long n, double* dst, cudaStream_t s);
 cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s);

@@ -218,6 +218,9 @@ struct GeoArgs {
   double k, alpha, d, dx, L, hmin, gam, a_s;
   int N, j, bc, p, neq, nfit, ncoll, nb, nfb, Ma, nx;
   double h;
+  // 0: the factors themselves. Otherwise their derivative with respect to the nodes' own position:
+  // 1 d/df, 2 d/df' (for the near operator of the target node, 3 d/df, 4 d/df' of the source node)
+  int dmode;
 };
 
 __global__ void k_build_P(GeoArgs g, const int* __restrict__ cell_start, const int* __restrict__ node_idx,
@@ -238,10 +241,21 @@ __global__ void k_build_P(GeoArgs g, const int* __restrict__ cell_start, const i
     double xl = x[nid], fl = f[nid], sl = sqrt(1 + f1[nid] * f1[nid]);
     for (int t = lane; t < g.ncoll; t += 32) {
       double X = cx + coll_rel[2 * t] - xl, Y = cy + coll_rel[2 * t + 1] - fl;
-      GreenVal gv;
-      gv.g = zd(0, 0); gv.gx = zd(0, 0); gv.gy = zd(0, 0);
-      green0_add(g.k, X, Y, 1.0, g.bc == 1, gv);
-      T[t] = g.bc == 0 ? g.dx * (f1[nid] * gv.gx - gv.gy) : (sl * g.dx) * gv.g;
+      if (g.dmode == 0) {
+        GreenVal gv;
+        gv.g = zd(0, 0); gv.gx = zd(0, 0); gv.gy = zd(0, 0);
+        green0_add(g.k, X, Y, 1.0, g.bc == 1, gv);
+        T[t] = g.bc == 0 ? g.dx * (f1[nid] * gv.gx - gv.gy) : (sl * g.dx) * gv.g;
+      } else {  // the node is the source: dY/df_l = -1
+        GreenHess hv;
+        hv.g = hv.gx = hv.gy = hv.gxy = hv.gyy = zd(0, 0);
+        green0_hess_add(g.k, X, Y, 1.0, hv);
+        const double f1l = f1[nid];
+        if (g.bc == 0)
+          T[t] = g.dmode == 1 ? g.dx * (hv.gyy - f1l * hv.gxy) : g.dx * hv.gx;
+        else
+          T[t] = g.dmode == 1 ? (-sl * g.dx) * hv.gy : (f1l / sl * g.dx) * hv.g;
+      }
     }
     __syncwarp();
     for (int o = lane; o < nout; o += 32) {
@@ -261,13 +275,15 @@ static GeoArgs geo_args(sgf_ctx* c) {
   g.gam = c->gam; g.a_s = c->a_s; g.N = c->N; g.j = c->prm.j; g.bc = c->bc; g.p = c->prm.p; g.neq = c->neq;
   g.nfit = c->nfit; g.ncoll = c->prm.n_coll; g.nb = c->nb; g.nfb = c->prm.n_fb; g.Ma = c->prm.Ma; g.nx = c->prm.nx;
   g.h = c->prm.h;
+  g.dmode = 0;
   return g;
 }
 
 
 cudaError_t launch_build_P_geo(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel, const double* f,
-                              const double* f1, zd* P) {
+                              const double* f1, zd* P, int dmode) {
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   size_t sm = (size_t)8 * g.ncoll * sizeof(zd);
   cudaFuncSetAttribute(k_build_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_build_P<<<c->n_occ, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x, f, f1,
@@ -275,7 +291,7 @@ cudaError_t launch_build_P_geo(sgf_ctx* c, const zd* pinv_eq, const double* d_co
   return cudaGetLastError();
 }
 cudaError_t launch_build_P(sgf_ctx* c, const zd* pinv_eq, const double* d_coll_rel) {
-  return launch_build_P_geo(c, pinv_eq, d_coll_rel, c->d_f, c->d_f1, c->o64.P);
+  return launch_build_P_geo(c, pinv_eq, d_coll_rel, c->d_f, c->d_f1, c->o64.P, 0);
 }
 
 // ============================================================== reconstruction rows I
@@ -299,13 +315,21 @@ __global__ void k_build_I(GeoArgs g, const int* __restrict__ node_cell, const in
   for (int bi = 0; bi < g.nb; ++bi) {
     int n = bi - g.nfb;
     double inv = 1.0 / fb_norm(n, krho0);
-    if (g.bc == 0) {
-      E[bi] = inv * fb_Z(n, kr, th);
-    } else {
-      zd zm = fb_Z(n - 1, kr, th), zp = fb_Z(n + 1, kr, th);
-      zd dzx = (0.5 * g.k) * (zm - zp);
-      zd dzy = zd(0, 0.5 * g.k) * (zp + zm);
-      E[bi] = inv * (nux * dzx + nuy * dzy);
+    zd zm = fb_Z(n - 1, kr, th), zp = fb_Z(n + 1, kr, th);
+    zd dzx = (0.5 * g.k) * (zm - zp);           // d/dX of J_n(k rho) e^{i n theta}
+    zd dzy = zd(0, 0.5 * g.k) * (zp + zm);      // d/dY
+    if (g.dmode == 0) {
+      E[bi] = g.bc == 0 ? inv * fb_Z(n, kr, th) : inv * (nux * dzx + nuy * dzy);
+    } else if (g.bc == 0) {  // the node's own height moves the sample point: d/dY; f' does not enter
+      E[bi] = g.dmode == 1 ? inv * dzy : zd(0, 0);
+    } else if (g.dmode == 1) {
+      zd zm2 = fb_Z(n - 2, kr, th), zp2 = fb_Z(n + 2, kr, th), z0 = fb_Z(n, kr, th);
+      zd dyx = zd(0, 0.25 * g.k * g.k) * (zm2 - zp2);            // d2/dYdX
+      zd dyy = (-0.25 * g.k * g.k) * (zm2 + 2.0 * z0 + zp2);    // d2/dY2
+      E[bi] = inv * (nux * dyx + nuy * dyy);
+    } else {  // d(unit normal)/df' = (-1, -f')/s^3
+      const double s3 = sn * sn * sn;
+      E[bi] = inv * ((-1.0 / s3) * dzx + (-f1[nid] / s3) * dzy);
     }
   }
   for (int t = 0; t < g.nfit; ++t) {
@@ -318,14 +342,15 @@ __global__ void k_build_I(GeoArgs g, const int* __restrict__ node_cell, const in
 }
 
 cudaError_t launch_build_I_geo(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel, const double* f,
-                              const double* f1, zd* Ip) {
+                              const double* f1, zd* Ip, int dmode) {
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   k_build_I<<<ceil_div(c->N, 64), 64, 0, c->stream>>>(g, c->d_node_cell, c->d_node_idx, c->d_occ_cx, c->d_occ_cy, c->d_x,
                                                        f, f1, d_samp_rel, pinv_fb, d_Iplain, Ip);
   return cudaGetLastError();
 }
 cudaError_t launch_build_I(sgf_ctx* c, const zd* pinv_fb, zd* d_Iplain, const double* d_samp_rel) {
-  return launch_build_I_geo(c, pinv_fb, d_Iplain, d_samp_rel, c->d_f, c->d_f1, c->o64.Ip);
+  return launch_build_I_geo(c, pinv_fb, d_Iplain, d_samp_rel, c->d_f, c->d_f1, c->o64.Ip, 0);
 }
 
 // ============================================================== periodised kernel table
@@ -654,6 +679,64 @@ cudaError_t launch_phi_off(sgf_ctx* c, zd* d_phi, int dcy_min, int n_dcy, const 
 // ============================================================== near operator blocks
 // Block per (q, r) pair: C_qr[i][l] = phase_r * ( exact (1 - S^f) dG_j/dnu w_l
 //   + S^f (R_s K_s + dx K_r)  [only where S^f > 0]  -  sum_t I_q[i][t] sum_s Phi_off[t][s] P_r[s][l] )
+// Derivative of the near-operator value (before the quasi-periodic phase and the folded local
+// subtraction) with respect to the target's (dmode 1: f, 2: f') or the source's (3: f, 4: f') own
+// position. Off the diagonal the value is (1 - S^f) dx K outside the singular band and
+// dx K + S^f K_s (R_s - dx ln 4 sin^2(pi X/(2a))) inside it, K the kernel of the boundary condition
+// and K_s its log coefficient; on the diagonal dx (f''/(4 pi (1 + f'^2)) + const).
+__device__ inline zd near_dval(const GeoArgs& g, bool diag, long sidx, double X, double Y, double f1i, double si,
+                               double f1l, double sl, double f2i, const double* kress, const double* binw) {
+  const int dm = g.dmode;
+  if (diag) {
+    if (dm != 2) return zd(0, 0);
+    double q = 1 + f1i * f1i;
+    return zd(g.dx * (-f2i * 2 * f1i / (4 * SGF_PI * q * q)), 0);
+  }
+  const double sY = dm == 1 ? 1.0 : (dm == 3 ? -1.0 : 0.0);  // dY/dv
+  const double k = g.k, rr = hypot(X, Y);
+  GreenHess H = green_j_hess(k, g.j, g.h, X, Y, binw);
+  zd kern, dkern;
+  if (g.bc == 0) {
+    kern = f1l * H.gx - H.gy;
+    dkern = (dm == 1 || dm == 3) ? sY * (f1l * H.gxy - H.gyy) : (dm == 4 ? H.gx : zd(0, 0));
+  } else {
+    zd a = -f1i * H.gx + H.gy;
+    kern = a * (sl / si);
+    if (dm == 1 || dm == 3)
+      dkern = (sY * sl / si) * (-f1i * H.gxy + H.gyy);
+    else if (dm == 2)
+      dkern = (-sl / si) * H.gx + (-f1i * sl / (si * si * si)) * a;
+    else
+      dkern = (f1l / (sl * si)) * a;
+  }
+  const double Sf = window_S(rr, g.gam, g.a_s);
+  const double dSf = window_S_dx(rr, g.gam, g.a_s) * sY * Y / rr;
+  if (Sf > 0 && sidx > -g.Ma && sidx < g.Ma) {
+    const double q = k * j1(k * rr) / rr;
+    const double dq = k * (k * j0(k * rr) / rr - 2 * j1(k * rr) / (rr * rr));  // d/dr
+    double Ks, dKs;
+    if (g.bc == 0) {
+      const double b = Y - f1l * X;
+      Ks = -q * b / (4 * SGF_PI);
+      dKs = (dm == 1 || dm == 3) ? -(dq * sY * Y / rr * b + q * sY) / (4 * SGF_PI)
+                                 : (dm == 4 ? q * X / (4 * SGF_PI) : 0.0);
+    } else {
+      const double b = -f1i * X + Y;
+      Ks = q * b / (4 * SGF_PI) / si * sl;
+      if (dm == 1 || dm == 3)
+        dKs = (dq * sY * Y / rr * b + q * sY) / (4 * SGF_PI) * sl / si;
+      else if (dm == 2)
+        dKs = q / (4 * SGF_PI) * (-X / si + b * (-f1i / (si * si * si))) * sl;
+      else
+        dKs = q * b / (4 * SGF_PI) / si * (f1l / sl);
+    }
+    const double sn = sin(SGF_PI * X / (2 * g.a_s));
+    const double w = kress[sidx + g.Ma - 1] - g.dx * log(4 * sn * sn);
+    return g.dx * dkern + zd((dSf * Ks + Sf * dKs) * w, 0);
+  }
+  return (-dSf * g.dx) * kern + ((1.0 - Sf) * g.dx) * dkern;
+}
+
 // Target nodes read (f, f1, f2), source nodes (fs, f1s): the same arrays for the operator itself;
 // a gradient moves the two roles separately (the diagonal belongs to the target).
 __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int* __restrict__ node_idx,
@@ -698,7 +781,10 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
     double rr = hypot(X, Y);
     double Sf = window_S(rr, g.gam, g.a_s);
     zd val(0, 0);
-    if (i == ls && wrap == 0) {
+    if (g.dmode != 0) {
+      val = near_dval(g, i == ls && wrap == 0, (long)i - ((long)ls + (long)wrap * g.N), X, Y, f1i, si, f1l, sl, f2[i],
+                      kress, binw);
+    } else if (i == ls && wrap == 0) {
       double kr0 = f2[i] / (4 * SGF_PI * (1 + f1i * f1i));
       val = g.dx * (zd(kr0, 0) + (g.bc == 0 ? hk : -hk));
     } else {
@@ -728,13 +814,14 @@ cudaError_t near_hk(sgf_ctx* c, zd* hk);
 cudaError_t launch_near(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const NearPairs& pp,
                         const double* d_kress) {
   return launch_near_geo(c, d_phi, dcy_min, n_dcy, d_Iplain, c->o64.P, pp, d_kress, c->d_f, c->d_f1, c->d_f2, c->d_f,
-                         c->d_f1, c->d_C);
+                         c->d_f1, c->d_C, 0);
 }
 
 cudaError_t launch_near_geo(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy, const zd* d_Iplain, const zd* P,
                             const NearPairs& pp, const double* d_kress, const double* ft, const double* f1t,
-                            const double* f2t, const double* fs, const double* f1s, zd* C) {
+                            const double* f2t, const double* fs, const double* f1s, zd* C, int dmode) {
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   int maxnr = 0;
   for (int q = 0; q < c->n_occ; ++q) maxnr = std::max(maxnr, c->cell_start[q + 1] - c->cell_start[q]);
   size_t sm = (size_t)c->nfit * maxnr * sizeof(zd);
@@ -777,21 +864,33 @@ __global__ void k_modes(GeoArgs g, int nm, const double* __restrict__ mn, const 
     zd bn(mn[3 * n + 1], mn[3 * n + 2]);
     // i (alpha_n x + beta_n f)
     zd arg = zd(0, an * x[i]) + zd(0, 1) * (f[i] * bn);
-    zd t = cexpz(arg);
-    if (g.bc == 1) t = t * ((zd(0, an * (-f1[i])) + zd(0, 1) * bn) * (1.0 / s));
+    zd e = cexpz(arg), t = e;
+    zd ibn = zd(0, 1) * bn;
+    zd nf = zd(0, an * (-f1[i])) + ibn;  // Neumann factor (-i alpha_n f' + i beta_n), before 1/s
+    if (g.bc == 1) t = e * (nf * (1.0 / s));
+    zd ms = (s * g.dx) * cexpz(-arg);
+    if (g.dmode == 1) {  // d/df: the exponents
+      t = ibn * t;
+      ms = (-1.0) * (ibn * ms);
+    } else if (g.dmode == 2) {  // d/df': the Neumann normal factor and the arc-length weight
+      t = g.bc == 1 ? e * (zd(0, -an / s) + (-f1[i] / (s * s * s)) * nf) : zd(0, 0);
+      ms = (f1[i] / s * g.dx) * cexpz(-arg);
+    }
     MT[(long)i * nm + n] = t;
-    MS[(long)n * g.N + i] = (s * g.dx) * cexpz(-arg);
+    MS[(long)n * g.N + i] = ms;
   }
 }
 
-cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS) {
+cudaError_t launch_modes_geo(sgf_ctx* c, const double* d_modes_n, const double* f, const double* f1, zd* MT, zd* MS,
+                             int dmode) {
   if (c->nm == 0) return cudaSuccess;
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   k_modes<<<ceil_div(c->N, 128), 128, 0, c->stream>>>(g, c->nm, d_modes_n, c->d_x, f, f1, MT, MS);
   return cudaGetLastError();
 }
 cudaError_t launch_modes(sgf_ctx* c, const double* d_modes_n) {
-  return launch_modes_geo(c, d_modes_n, c->d_f, c->d_f1, c->d_MT, c->d_MS);
+  return launch_modes_geo(c, d_modes_n, c->d_f, c->d_f1, c->d_MT, c->d_MS, 0);
 }
 
 // ============================================================== right-hand side
@@ -799,19 +898,20 @@ __global__ void k_rhs(GeoArgs g, double beta, const double* x, const double* f, 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   zd u = expi(g.alpha * x[i] - beta * f[i]);
-  if (g.bc == 0) {
-    out[i] = -u;
-  } else {
-    double s = sqrt(1 + f1[i] * f1[i]);
-    out[i] = zd(0, (g.alpha * f1[i] + beta) / s) * u;
-  }
+  const double s = sqrt(1 + f1[i] * f1[i]);
+  zd v = g.bc == 0 ? -u : zd(0, (g.alpha * f1[i] + beta) / s) * u;
+  if (g.dmode == 1) v = zd(0, -beta) * v;  // d/df of the phase
+  if (g.dmode == 2)                         // d/df' (Neumann only)
+    v = g.bc == 0 ? zd(0, 0) : zd(0, g.alpha / s - (g.alpha * f1[i] + beta) * f1[i] / (s * s * s)) * u;
+  out[i] = v;
 }
-cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out) {
+cudaError_t launch_rhs_geo(sgf_ctx* c, const double* f, const double* f1, zd* out, int dmode) {
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   k_rhs<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, c->beta, c->d_x, f, f1, out);
   return cudaGetLastError();
 }
-cudaError_t launch_rhs(sgf_ctx* c, zd* out) { return launch_rhs_geo(c, c->d_f, c->d_f1, out); }
+cudaError_t launch_rhs(sgf_ctx* c, zd* out) { return launch_rhs_geo(c, c->d_f, c->d_f1, out, 0); }
 
 // ============================================================== forward map
 // Mode-sum partials (eq. D_M_deltax, source factors): block (n, chunk) of the grid tail sums
@@ -1731,10 +1831,17 @@ __global__ void k_rayleigh_weights(GeoArgs g, const double* __restrict__ mp, con
   zd e = cexpz(-(zd(0, an * x[i]) + zd(0, 1) * (f[i] * bn)));
   zd W = g.bc == 0 ? (bn - zd(an * f1[i], 0)) * Q * (0.5 / g.d) + zd(s * ind, 0)
                    : s * (zd(0, 0.5 / g.d) * Q + zd(ind, 0));
+  if (g.dmode == 1) {  // d/df of the phase
+    W = (zd(0, -1) * bn) * W;
+  } else if (g.dmode == 2) {  // d/df' of the weight
+    W = g.bc == 0 ? (-an * 0.5 / g.d) * Q + zd(f1[i] / s * ind, 0) : (f1[i] / s) * (zd(0, 0.5 / g.d) * Q + zd(ind, 0));
+  }
   w[i] = g.dx * (e * W);
 }
-cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w) {
+cudaError_t launch_rayleigh_weights(sgf_ctx* c, const double* d_mp, const double* f, const double* f1, zd* w,
+                                    int dmode) {
   GeoArgs g = geo_args(c);
+  g.dmode = dmode;
   k_rayleigh_weights<<<ceil_div(c->N, 256), 256, 0, c->stream>>>(g, d_mp, c->d_x, f, f1, w);
   return cudaGetLastError();
 }

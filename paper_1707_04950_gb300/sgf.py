@@ -21,7 +21,7 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
-            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_gradient", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve"]
 
 
@@ -66,6 +66,7 @@ def load():
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
         "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
         "sgf_gradient": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
+        "sgf_gradient_fd": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
         "sgf_get_params": [vp, ctypes.POINTER(sgf_params)],
         "sgf_autotune_cells": [vp, ctypes.POINTER(i), i, i, ctypes.POINTER(i), dp],
         "sgf_info": [vp, dp],
@@ -179,16 +180,17 @@ def sgf_rayleigh(ctx, mu_ptr, n_lo, n_hi):
     return B[0::2] + 1j * B[1::2], eff, float(err[0])
 
 
-def sgf_gradient(ctx, mu_ptr, n, M, tol=1e-12, maxit=2000):
+def sgf_gradient(ctx, mu_ptr, n, M, tol=1e-12, maxit=2000, fd=False):
     """d e_n / d(a_m, b_m), m = 0..M (M = number of profile harmonics); returns (grad_a, grad_b, B_n,
-    e_n, adjoint iterations)."""
+    e_n, adjoint iterations). fd=True calls sgf_gradient_fd (difference-quotient node derivatives)."""
     ga = np.zeros(M + 1)
     gb = np.zeros(M + 1)
     B = np.zeros(2)
     en = np.zeros(1)
     its = ctypes.c_int(0)
-    _check(ctx, load().sgf_gradient(ctx, ctypes.c_void_p(mu_ptr), int(n), float(tol), int(maxit), _dptr(B), _dptr(en),
-                                    _dptr(ga), _dptr(gb), ctypes.byref(its)))
+    fn = load().sgf_gradient_fd if fd else load().sgf_gradient
+    _check(ctx, fn(ctx, ctypes.c_void_p(mu_ptr), int(n), float(tol), int(maxit), _dptr(B), _dptr(en), _dptr(ga),
+                   _dptr(gb), ctypes.byref(its)))
     return ga, gb, B[0] + 1j * B[1], float(en[0]), its.value
 
 
