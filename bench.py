@@ -253,7 +253,9 @@ def run_ours(args):
                    "near_field_entries": int(info["nnz"]), "l2": "flushed (256 MiB write) before each timed step",
                    "parallelism": f"replicas x{ws}"},
         "fp64": {"value": ws * 1000.0 / ms64, "unit": "matvecs/s", "ms_per_step": ms64,
-                 "stages_ms": res[64]["stages_ms"]},
+                 "stages_ms": res[64]["stages_ms"],
+                 "whole_step_hbm_frac": res[64]["info"]["bytes64"] / (ms64 * 1e-3) / 1e9 / hbm},
+        "whole_step_hbm_frac": info["bytes32"] / (ms32 * 1e-3) / 1e9 / hbm,
         "mixed_rel_err_vs_fp64": mixed_err,
         "stages_ms": stg,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
@@ -377,6 +379,7 @@ def run_batch(args, dev, stream, flush):
     idx = list(range(0, 64, 64 // args.batch))[: args.batch]
     pars = [inputs.wl_gaussian_angles(i) for i in idx]
     ops = [sgf.Operator(p, device=dev.index, stream=stream.cuda_stream, precision=32) for p in pars]
+    infos = [op.info for op in ops]
     mus = [torch.from_numpy(inputs.random_density(p["N"], 30 + q)).to(dev) for q, p in enumerate(pars)]
     outs = [torch.empty_like(m) for m in mus]
     b = sgf.sgf_batch_create([op.ctx for op in ops], stream.cuda_stream)
@@ -424,9 +427,12 @@ def run_batch(args, dev, stream, flush):
     for op in ops:
         op.close()
     n = len(ops)
+    bytes_step = sum(op_info["bytes32"] for op_info in infos)
+    hbm, _ = peaks()
     return {
         "workload": f"gaussian_rms0.5_lc2_d10_n2048_{n}angles_of_64", "problems": n, "precision": "mixed",
-        "apply": {"value": n * 1000.0 / ms_b, "unit": "matvecs/s", "ms_per_step": ms_b},
+        "apply": {"value": n * 1000.0 / ms_b, "unit": "matvecs/s", "ms_per_step": ms_b,
+                  "hbm_frac": bytes_step / (ms_b * 1e-3) / 1e9 / hbm},
         "apply_sequential": {"value": n * 1000.0 / ms_s, "unit": "matvecs/s", "ms_per_step": ms_s},
         "batch_vs_sequential_rel_diff": diff,
         "solve": {"value": n / t_b, "unit": "solves/s", "s": t_b, "tol": BATCH_TOL, "status": st, "iters": its,
