@@ -383,6 +383,7 @@ def run_batch(args, dev, stream, flush):
     mus = [torch.from_numpy(inputs.random_density(p["N"], 30 + q)).to(dev) for q, p in enumerate(pars)]
     outs = [torch.empty_like(m) for m in mus]
     b = sgf.sgf_batch_create([op.ctx for op in ops], stream.cuda_stream)
+    shared = bool(sgf.sgf_batch_shared_near(b))
     mp, op_ = [m.data_ptr() for m in mus], [o.data_ptr() for o in outs]
     steps = max(3, min(args.steps, 50))
 
@@ -431,6 +432,7 @@ def run_batch(args, dev, stream, flush):
     hbm, _ = peaks()
     return {
         "workload": f"gaussian_rms0.5_lc2_d10_n2048_{n}angles_of_64", "problems": n, "precision": "mixed",
+        "shared_near": shared,
         "apply": {"value": n * 1000.0 / ms_b, "unit": "matvecs/s", "ms_per_step": ms_b,
                   "hbm_frac": bytes_step / (ms_b * 1e-3) / 1e9 / hbm},
         "apply_sequential": {"value": n * 1000.0 / ms_s, "unit": "matvecs/s", "ms_per_step": ms_s},

@@ -173,6 +173,16 @@ typedef struct sgf_batch sgf_batch;
  * grids are in use: do not apply or solve with those contexts on other streams at the same time.
  * On failure *out still receives a batch whose sgf_batch_last_error() explains it; destroy it. */
 sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* cuda_stream);
+
+/* 1 if the batch shares one near operator among its problems, 0 otherwise. sgf_batch_create turns
+ * this on when all problems have the same profile, wavenumber, boundary condition and parameters
+ * and differ only in the incidence angle: their near operators then differ only by the
+ * quasi-periodic phase e^{i alpha d w} of each block's period copy w, so one pass over the first
+ * problem's blocks (with the phase applied to the densities) serves every angle, and the rest of
+ * each forward map runs as before. The shared pass follows the problems' far-field work instead of
+ * overlapping it, so sgf_batch_create times both forms on the eligible batch and keeps the faster;
+ * the environment variable SGF_BATCH_SHARED=1 (or 0) forces the shared (or separate) form. */
+int sgf_batch_shared_near(const sgf_batch* batch);
 void sgf_batch_destroy(sgf_batch* batch);
 const char* sgf_batch_last_error(const sgf_batch* batch);
 

@@ -31,6 +31,8 @@ struct sgf_batch {
   zd** d_tb = nullptr;
   zd** h_tab = nullptr;   // pinned host staging of the per-call tables (2 n entries)
   cudaEvent_t ev_tab = nullptr;
+  bool shared_near = false;  // problems differ only in the incidence angle: one shared near pass
+  zd* d_ph = nullptr;        // [problem][period copy -1, 0, 1] phase relative to the first problem
   std::vector<void*> allocs;
   char err[1024] = {0};
 };
@@ -141,6 +143,101 @@ __global__ void k_bupdate(zd* const* __restrict__ wt, int wk, zd* const* __restr
   w[i] = acc;
 }
 
+static bool same_params(const sgf_params& a, const sgf_params& b) {
+  return a.N == b.N && a.j == b.j && a.h == b.h && a.n_per == b.n_per && a.c_win == b.c_win && a.Ma == b.Ma &&
+         a.eta == b.eta && a.nx == b.nx && a.ny == b.ny && a.hmin == b.hmin && a.p == b.p && a.e == b.e &&
+         a.n_coll == b.n_coll && a.n_fb == b.n_fb && a.delta_min == b.delta_min && a.spec_exp == b.spec_exp &&
+         a.precision == b.precision && a.ls_reg == b.ls_reg;
+}
+
+// ------------------------------------------------------------------ angle-shared near field
+// Problems that differ only in the incidence angle share every near-operator block up to the
+// quasi-periodic phase of the block's period copy: C(alpha) = e^{i alpha d w} C_base for a block
+// whose source cell is copy w in {-1, 0, 1}. One pass over the first problem's blocks therefore
+// serves all of them: out_a[i] += sum_c C_0[i][c] e^{i (alpha_a - alpha_0) d w(c)} mu_a[col c].
+// Block per work item of the shared layout; angles in groups of G whose phased densities are staged
+// in shared memory; each warp streams a row once per group and keeps G accumulators.
+template <bool FF>
+__global__ void k_near_multi(int n_ang, const zd* __restrict__ ph, const int* __restrict__ cell_start,
+                             const int* __restrict__ node_idx, const int* __restrict__ cols,
+                             const int* __restrict__ coloff, const signed char* __restrict__ colwrap,
+                             const long* __restrict__ cell_off, const int* __restrict__ cell_W,
+                             const zd* __restrict__ C, const float4* __restrict__ Cff, const int* __restrict__ item_cell,
+                             const int* __restrict__ item_lo, const int* __restrict__ item_hi, zd* const* __restrict__ mus,
+                             zd* const* __restrict__ outs) {
+  constexpr int G = 8;
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  const int W = cell_W[q];
+  const int* cq = cols + coloff[q];
+  const signed char* wq = colwrap + coloff[q];
+  zd* vd = reinterpret_cast<zd*>(smem_raw);          // [G][W]
+  float4* vf = reinterpret_cast<float4*>(smem_raw);  // [G][W]
+  for (int a0 = 0; a0 < n_ang; a0 += G) {
+    const int na = min(G, n_ang - a0);
+    for (int t = threadIdx.x; t < na * W; t += blockDim.x) {
+      const int a = t / W, cc = t - a * W;
+      const zd v = ph[(long)(a0 + a) * 3 + wq[cc] + 1] * mus[a0 + a][cq[cc]];
+      if (FF)
+        vf[t] = cff_from(v);
+      else
+        vd[t] = v;
+    }
+    __syncthreads();
+    for (int il = warp; il < nq; il += nw) {
+      const long row = cell_off[q] + (long)(rlo + il) * W;
+      if (FF) {
+        dot2c acc[G];
+#pragma unroll
+        for (int a = 0; a < G; ++a) acc[a] = {0.f, 0.f, 0.f, 0.f};
+        for (int cc = lane; cc < W; cc += 32) {
+          const float4 cv = Cff[row + cc];
+#pragma unroll
+          for (int a = 0; a < G; ++a)
+            if (a < na) dot2_mac(cv, vf[a * W + cc], acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+          if (a >= na) break;
+          for (int o = 16; o > 0; o >>= 1) {
+            dot2c t = {__shfl_down_sync(0xffffffffu, acc[a].sr, o), __shfl_down_sync(0xffffffffu, acc[a].si, o),
+                       __shfl_down_sync(0xffffffffu, acc[a].er, o), __shfl_down_sync(0xffffffffu, acc[a].ei, o)};
+            dot2_merge(acc[a], t);
+          }
+          if (lane == 0) {
+            ff vr = ff_add({acc[a].sr, 0.f}, {acc[a].er, 0.f}), vi = ff_add({acc[a].si, 0.f}, {acc[a].ei, 0.f});
+            zd* o = outs[a0 + a] + node_idx[s0 + il];
+            *o = *o + zd(ff_to_double(vr), ff_to_double(vi));
+          }
+        }
+      } else {
+        zd acc[G];
+#pragma unroll
+        for (int a = 0; a < G; ++a) acc[a] = zd(0, 0);
+        for (int cc = lane; cc < W; cc += 32) {
+          const zd cv = C[row + cc];
+#pragma unroll
+          for (int a = 0; a < G; ++a)
+            if (a < na) acc[a] = fma_c(cv, vd[a * W + cc], acc[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+          if (a >= na) break;
+          const zd v = warp_sum(acc[a]);
+          if (lane == 0) {
+            zd* o = outs[a0 + a] + node_idx[s0 + il];
+            *o = *o + v;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ batched forward map
 static dim3 bgrid(const sgf_batch* B) { return dim3(ceil_div(B->maxN, 256), B->n); }
 
@@ -175,6 +272,67 @@ static void free_batch(sgf_batch* B) {
   for (void* p : B->allocs) cudaFree(p);
   if (B->h_tab) cudaFreeHost(B->h_tab);
   if (B->ev_tab) cudaEventDestroy(B->ev_tab);
+}
+
+// One graph for graph slot s (0: each problem's own precision, 1: FP64): every problem's captured
+// forward map as an independent child graph; with `shared` the children leave out the near operator
+// and one angle-shared near-field node follows them.
+static sgf_status build_batch_graph(sgf_batch* B, int s, bool shared, cudaGraph_t* gout, cudaGraphExec_t* xout) {
+  const int n = B->n;
+  sgf_ctx* c0 = B->ctx[0];
+  cudaGraph_t graph = nullptr;
+  BCU(cudaGraphCreate(&graph, 0));
+  std::vector<cudaGraphNode_t> kids(n);
+  for (int p = 0; p < n; ++p) {
+    sgf_ctx* c = B->ctx[p];
+    int gi = (s == 0 && c->prm.precision == 32) ? 1 : 0;
+    cudaGraph_t child = c->gs[gi].g;
+    if (shared) {
+      if (!c->gs_nonear[gi].ok) BCU(build_apply_graph_mask(c, gi == 1 ? 32 : 64, 13, c->gs_nonear[gi]));
+      child = c->gs_nonear[gi].g;
+    }
+    BCU(cudaGraphAddChildGraphNode(&kids[p], graph, nullptr, 0, child));
+  }
+  if (shared) {
+    const bool ff = s == 0 && c0->prm.precision == 32;
+    const void* fn = ff ? (const void*)k_near_multi<true> : (const void*)k_near_multi<false>;
+    const size_t sm = (size_t)8 * c0->maxW * sizeof(zd);
+    BCU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int na = n;
+    void* args[] = {&na, &B->d_ph, &c0->d_cell_start, &c0->d_node_idx, &c0->d_cols, &c0->d_coloff, &c0->d_colwrap,
+                    &c0->d_cell_off, &c0->d_cell_W, &c0->d_C, &c0->d_Cff, &c0->d_item_cell, &c0->d_item_lo,
+                    &c0->d_item_hi, &B->d_in, &B->d_out};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)fn;
+    kp.gridDim = dim3(c0->n_items);
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = (unsigned)sm;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    cudaGraphNode_t nd;
+    BCU(cudaGraphAddKernelNode(&nd, graph, kids.data(), n, &kp));
+  }
+  BCU(cudaGraphInstantiate(xout, graph, cudaGraphInstantiateFlagUseNodePriority));
+  *gout = graph;
+  return SGF_OK;
+}
+
+// Mean time of one launch of x (3 warm-up, 10 timed launches on the batch stream).
+static sgf_status time_exec(sgf_batch* B, cudaGraphExec_t x, double* ms) {
+  cudaEvent_t e0, e1;
+  BCU(cudaEventCreate(&e0));
+  BCU(cudaEventCreate(&e1));
+  for (int r = 0; r < 3; ++r) BCU(cudaGraphLaunch(x, B->stream));
+  BCU(cudaEventRecord(e0, B->stream));
+  for (int r = 0; r < 10; ++r) BCU(cudaGraphLaunch(x, B->stream));
+  BCU(cudaEventRecord(e1, B->stream));
+  BCU(cudaEventSynchronize(e1));
+  float t = 0;
+  BCU(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / 10;
+  return SGF_OK;
 }
 
 extern "C" {
@@ -219,17 +377,51 @@ sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* 
   BCU(cudaMemcpy(B->d_N, B->N.data(), n * sizeof(long), cudaMemcpyHostToDevice));
   BCU(cudaMemcpy(B->d_in, in.data(), n * sizeof(zd*), cudaMemcpyHostToDevice));
   BCU(cudaMemcpy(B->d_out, outp.data(), n * sizeof(zd*), cudaMemcpyHostToDevice));
-  // one graph per slot: every problem's captured forward map as an independent child graph
+  // angle sharing: every problem on the same surface, wavenumber, boundary condition and
+  // parameters (only the incidence angle differs) shares the first problem's near operator
+  sgf_ctx* c0 = B->ctx[0];
+  B->shared_near = n > 1 && (size_t)8 * c0->maxW * sizeof(zd) <= 200 * 1024;
+  for (int p = 1; p < n && B->shared_near; ++p) {
+    const sgf_ctx* c = B->ctx[p];
+    B->shared_near = c->N == c0->N && c->d == c0->d && c->k == c0->k && c->bc == c0->bc && c->fa == c0->fa &&
+                     c->fb == c0->fb && same_params(c->prm, c0->prm) && c->nnz == c0->nnz &&
+                     c->n_items == c0->n_items && c->maxW == c0->maxW;
+  }
+  if (B->shared_near) {
+    std::vector<zd> ph((size_t)3 * n);
+    for (int p = 0; p < n; ++p) {
+      const double dl = (B->ctx[p]->alpha - c0->alpha) * c0->d;
+      for (int w = -1; w <= 1; ++w) ph[(size_t)p * 3 + w + 1] = zd(std::cos(dl * w), std::sin(dl * w));
+    }
+    BTRY(balloc(B, &B->d_ph, ph.size()));
+    BCU(cudaMemcpy(B->d_ph, ph.data(), ph.size() * sizeof(zd), cudaMemcpyHostToDevice));
+  }
+  // Angle sharing removes the repeated near operators but puts one near-field node after every
+  // problem's far-field work, so it pays only when the near operators dominate: the two forms are
+  // timed at creation and the faster is kept (SGF_BATCH_SHARED=0 / 1 forces one form).
+  if (B->shared_near) {
+    const char* env = getenv("SGF_BATCH_SHARED");
+    if (env && env[0] == '0') B->shared_near = false;
+    if (!(env && (env[0] == '0' || env[0] == '1'))) {
+      cudaGraph_t gsh = nullptr, gpl = nullptr;
+      cudaGraphExec_t xsh = nullptr, xpl = nullptr;
+      for (int p = 0; p < n; ++p)  // defined staging inputs for the timed launches
+        BCU(cudaMemsetAsync(B->ctx[p]->d_mu_tmp, 0, B->N[p] * sizeof(zd), B->stream));
+      BTRY(build_batch_graph(B, 0, true, &gsh, &xsh));
+      BTRY(build_batch_graph(B, 0, false, &gpl, &xpl));
+      double tsh = 0, tpl = 0;
+      BTRY(time_exec(B, xsh, &tsh));
+      BTRY(time_exec(B, xpl, &tpl));
+      B->shared_near = tsh < tpl;
+      cudaGraphExecDestroy(xsh);
+      cudaGraphExecDestroy(xpl);
+      cudaGraphDestroy(gsh);
+      cudaGraphDestroy(gpl);
+    }
+  }
   for (int s = 0; s < 2; ++s) {
     if (s == 1 && !B->any_mixed) break;
-    BCU(cudaGraphCreate(&B->graph[s], 0));
-    for (int p = 0; p < n; ++p) {
-      sgf_ctx* c = B->ctx[p];
-      int gi = (s == 0 && c->prm.precision == 32) ? 1 : 0;
-      cudaGraphNode_t nd;
-      BCU(cudaGraphAddChildGraphNode(&nd, B->graph[s], nullptr, 0, c->gs[gi].g));
-    }
-    BCU(cudaGraphInstantiate(&B->exec[s], B->graph[s], cudaGraphInstantiateFlagUseNodePriority));
+    BTRY(build_batch_graph(B, s, B->shared_near, &B->graph[s], &B->exec[s]));
   }
   if (!B->any_mixed) B->exec[1] = nullptr;
   return SGF_OK;
@@ -246,6 +438,8 @@ void sgf_batch_destroy(sgf_batch* B) {
 }
 
 const char* sgf_batch_last_error(const sgf_batch* B) { return B ? B->err : "null batch"; }
+
+int sgf_batch_shared_near(const sgf_batch* B) { return B && B->shared_near ? 1 : 0; }
 
 sgf_status sgf_batch_apply(sgf_batch* B, const void* const* mu_devs, void* const* out_devs) {
   if (!B) return SGF_EINVAL;

@@ -580,14 +580,20 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(cudaMemcpy(c->d_cell_W, cellW.data(), c->n_occ * sizeof(int), cudaMemcpyHostToDevice));
   {  // node index of every local column of every cell (cells in order, columns in block order)
     std::vector<int> cols, coloff(c->n_occ + 1, 0);
+    std::vector<signed char> colwrap;  // period copy (-1, 0, 1) of each column's source node
     for (int q = 0; q < c->n_occ; ++q) {
       coloff[q] = (int)cols.size();
       for (int b = blk_start[q]; b < blk_start[q + 1]; ++b) {
         int r = pr[b];
-        for (int l = c->cell_start[r]; l < c->cell_start[r + 1]; ++l) cols.push_back(c->node_idx[l]);
+        for (int l = c->cell_start[r]; l < c->cell_start[r + 1]; ++l) {
+          cols.push_back(c->node_idx[l]);
+          colwrap.push_back((signed char)pw[b]);
+        }
       }
     }
     coloff[c->n_occ] = (int)cols.size();
+    TRY(dalloc(ctx, &c->d_colwrap, colwrap.size()));
+    CU(cudaMemcpy(c->d_colwrap, colwrap.data(), colwrap.size(), cudaMemcpyHostToDevice));
     TRY(dalloc(ctx, &c->d_cols, cols.size()));
     TRY(dalloc(ctx, &c->d_coloff, c->n_occ + 1));
     CU(cudaMemcpy(c->d_cols, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice));

@@ -95,6 +95,7 @@ struct sgf_ctx {
   int* d_cell_W = nullptr;     // [n_occ] row length W_q
   int* d_cols = nullptr;       // node index of each local column, cells in order
   int* d_coloff = nullptr;     // [n_occ + 1] offsets into d_cols
+  signed char* d_colwrap = nullptr;  // period copy (-1, 0, 1) of each local column (its block's wrap)
   int maxW = 0;
   // adjoint near field: rows of each cell r hold conj(C) of the blocks (q, r), W^T_r columns
   zd* d_CT = nullptr;
@@ -129,6 +130,7 @@ struct sgf_ctx {
   // profiling
   bool profiling = false;
   GraphSlot gs[2];  // [0] FP64, [1] mixed
+  GraphSlot gs_nonear[2];  // the same without the near operator (angle-sharing batches), on demand
   bool use_graphs = true;
   int maxnq = 0;
   int debug_mask = 15;
@@ -190,6 +192,7 @@ cudaError_t launch_near_transpose(int nblk, const int* bq, const int* br, const 
                                   const long* dst_off, const int* dst_ld, const int* cell_start, const zd* C, zd* CT,
                                   cudaStream_t s);
 cudaError_t build_apply_graph(sgf_ctx* c, int prec);
+cudaError_t build_apply_graph_mask(sgf_ctx* c, int prec, int term_mask, GraphSlot& gs);
 cudaError_t launch_apply_graph(sgf_ctx* c, int prec, const zd* mu, zd* out);
 void destroy_graphs(sgf_ctx* c);
 cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const double* d_mp, zd* d_B);

@@ -1691,6 +1691,11 @@ static const int kNearArgs = 15, kNearMu = 13, kNearOut = 14;
 static const int kFarArgs = 19, kFarOut = 18;
 
 void destroy_graphs(sgf_ctx* c) {
+  for (auto& gs : c->gs_nonear) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    if (gs.g) cudaGraphDestroy(gs.g);
+    gs = GraphSlot();
+  }
   for (auto& gs : c->gs) {
     if (gs.exec) cudaGraphExecDestroy(gs.exec);
     if (gs.g) cudaGraphDestroy(gs.g);
@@ -1701,8 +1706,10 @@ void destroy_graphs(sgf_ctx* c) {
 // Captures one application (on an internal stream, from the context's staging buffers) and keeps
 // the instantiated graph; returns the capture or instantiation error, in which case the context
 // keeps launching the kernels directly.
-cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
-  GraphSlot& gs = c->gs[prec == 64 ? 0 : 1];
+cudaError_t build_apply_graph(sgf_ctx* c, int prec) { return build_apply_graph_mask(c, prec, 15, c->gs[prec == 64 ? 0 : 1]); }
+
+// The same capture with the terms of `mask` only (sgf_debug_mask bits) into the given slot.
+cudaError_t build_apply_graph_mask(sgf_ctx* c, int prec, int term_mask, GraphSlot& gs) {
   cudaStream_t orig = c->stream, cap = nullptr;
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
@@ -1713,7 +1720,7 @@ cudaError_t build_apply_graph(sgf_ctx* c, int prec) {
   const bool prof = c->profiling;
   const int mask = c->debug_mask;
   c->profiling = false;
-  c->debug_mask = 15;
+  c->debug_mask = term_mask;
   c->stream = cap;
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);

@@ -22,7 +22,8 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
             "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
-            "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve"]
+            "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve",
+            "sgf_batch_shared_near"]
 
 
 class SgfError(RuntimeError):
@@ -90,6 +91,8 @@ def load():
     lib.sgf_batch_destroy.restype = None
     lib.sgf_batch_last_error.argtypes = [vp]
     lib.sgf_batch_last_error.restype = ctypes.c_char_p
+    lib.sgf_batch_shared_near.argtypes = [vp]
+    lib.sgf_batch_shared_near.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -244,6 +247,10 @@ def sgf_batch_create(ctxs, stream=0):
 
 def sgf_batch_destroy(batch):
     load().sgf_batch_destroy(batch)
+
+
+def sgf_batch_shared_near(batch):
+    return bool(load().sgf_batch_shared_near(batch))
 
 
 def sgf_batch_apply(batch, mu_ptrs, out_ptrs):
