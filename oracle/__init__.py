@@ -9,7 +9,10 @@ uses it and it shares no code with the library; the two meet only through the se
 Modules
   green   free-space G, shifted G_j, windows, shifted spectral series, windowed lattice sums (Sec. 2-3)
   direct  the exact Nystrom system (1/2 I + D^dx) mu = -u^inc and Rayleigh extraction (Sec. 2, 4)
-  accel   the accelerated forward map, Algorithm 2 (initialisation) and Algorithm 3 (Sec. 5)
+  accel   the accelerated forward map, Algorithm 2 (initialisation) and Algorithm 3 (Sec. 5);
+          Accel.field: Algorithm 3 at targets off the surface
+  field   the scattered field off the surface by its definition (eq. int_eq_dirichlet discretised)
+          and by its Rayleigh form above every node; gradient: derivatives of e_n by definition
 
 Parity status: every function is pinned by tests/test_oracle_*.py (closed forms, identities,
 brute force, energy balance) except the exact values of B_n for curved surfaces, which the paper

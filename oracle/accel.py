@@ -253,17 +253,9 @@ class Accel:
             return (self.f1[nodes_idx][None, :] * gx - gy) * self.dx
         return gr.G0(k, X, Y) * (self.s[nodes_idx] * self.dx)[None, :]
 
-    # ------------------------------------------------------------------ Algorithm 3
-    def apply(self, mu, return_stages=False):
-        """Algorithm 3 on one density mu [N] or on a block of columns mu [N, R] (column by column;
-        every step is linear in mu)."""
-        par = self.par
-        k, d, j, h, al = self.k, self.d, self.j, self.h, self.alpha
-        N = self.N
-        mu = np.asarray(mu, complex)
-        st = {}
-
-        # EqSources (eq. eq_source_point): densities of every occupied reference cell
+    # ------------------------------------------------------------------ Algorithm 3 steps
+    def _eq_densities(self, mu):
+        """EqSources (eq. eq_source_point): densities of every occupied reference cell."""
         dens = {}
         for q in self.cells:
             idx = np.array(self.cell_nodes[q])
@@ -271,9 +263,11 @@ class Accel:
             psi = self.true_field(pts, idx) @ mu[idx]
             for lam in ("H", "V"):
                 dens[(q, lam)] = self.pinv_eq[lam] @ psi
-        st["dens"] = dens
+        return dens
 
-        # GlobalEqSMerge (eq. sum_eqsources): duplicates summed on Pi^per, quasi-periodic wrap
+    def _merge(self, dens, shape):
+        """GlobalEqSMerge (eq. sum_eqsources): duplicates summed on Pi^per, quasi-periodic wrap."""
+        al, d = self.alpha, self.d
         merged = {"H": {}, "V": {}}
         for q in self.cells:
             cxq, cyq = q
@@ -288,19 +282,22 @@ class Accel:
                     wrap = ixr // Px
                     ph = np.exp(-1j * al * d * wrap)
                     key = (ixr - wrap * Px, iy)
-                    a = merged[lam].setdefault(key, np.zeros((2,) + mu.shape[1:], complex))
+                    a = merged[lam].setdefault(key, np.zeros((2,) + shape, complex))
                     a[0] += v[t] * ph
                     a[1] += v[self.neq + t] * ph
+        return merged
 
-        # sample points of every occupied cell and their grid indices
-        def sample_grid(q, t):
-            cxq, cyq = q
-            o1, o2 = self.samp_idx[t]
-            if self.samp_ori[t] == "H":
-                return cxq * self.p + o1, cyq + o2
-            return cxq + o1, cyq * self.p + o2 + self.e
+    def _sample_grid(self, q, t):
+        """Grid indices (ix unwrapped, iy) of sample t of cell q."""
+        cxq, cyq = q
+        o1, o2 = self.samp_idx[t]
+        if self.samp_ori[t] == "H":
+            return cxq * self.p + o1, cyq + o2
+        return cxq + o1, cyq * self.p + o2 + self.e
 
-        # GlobalFFT (eq. large_convolution_per_grid), by its direct sum on the sample points
+    def _phi_all(self, merged, cells):
+        """GlobalFFT (eq. large_convolution_per_grid), by its direct sum on the sample points of the
+        given cells (any cells of the box, occupied or not)."""
         phi_all = {}
         for lam in ("H", "V"):
             keys = list(merged[lam].keys())
@@ -310,23 +307,25 @@ class Accel:
             gy_ = np.array([kk[1] for kk in keys])
             xi = np.array([merged[lam][kk][0] for kk in keys])
             ze = np.array([merged[lam][kk][1] for kk in keys])
-            for q in self.cells:
+            for q in cells:
                 ts = [t for t in range(len(self.samp_ori)) if self.samp_ori[t] == lam]
                 for t in ts:
-                    six, siy = sample_grid(q, t)
+                    six, siy = self._sample_grid(q, t)
                     km, kd = self.kernel(lam, six - gx_, siy - gy_)
                     phi_all[(q, t)] = km @ xi + kd @ ze
-        st["phi_all"] = phi_all
+        return phi_all
 
-        # LocalEqSMerge + LocalFFT (eqs. sum_eqsources_local, small_convolution_grid): phi^int
+    def _phi_int(self, dens, cells, shape):
+        """LocalEqSMerge + LocalFFT (eqs. sum_eqsources_local, small_convolution_grid): phi^int on the
+        sample points of the given cells from the equivalent sources of their local cells."""
+        k, d, j, h, al = self.k, self.d, self.j, self.h, self.alpha
         phi_int = {}
-        w = gr.binom_weights(j)
-        for q in self.cells:
+        for q in cells:
             loc = self.local_cells(q)
             for t in range(len(self.samp_ori)):
                 lam = self.samp_ori[t]
                 x_t = self.samp_rel[t] + self.corner(*q)
-                acc = np.zeros(mu.shape[1:], complex)
+                acc = np.zeros(shape, complex)
                 for (cxr, cyr) in loc:
                     ref = cxr % self.nx
                     wrap = (cxr - ref) // self.nx
@@ -347,6 +346,22 @@ class Accel:
                     dG = -(nu[0] * ax + nu[1] * ay)
                     acc = acc + Gv @ v[:self.neq] + dG @ v[self.neq:]
                 phi_int[(q, t)] = acc
+        return phi_int
+
+    # ------------------------------------------------------------------ Algorithm 3
+    def apply(self, mu, return_stages=False):
+        """Algorithm 3 on one density mu [N] or on a block of columns mu [N, R] (column by column;
+        every step is linear in mu)."""
+        par = self.par
+        k, d, j, h, al = self.k, self.d, self.j, self.h, self.alpha
+        mu = np.asarray(mu, complex)
+        st = {}
+        dens = self._eq_densities(mu)
+        st["dens"] = dens
+        merged = self._merge(dens, mu.shape[1:])
+        phi_all = self._phi_all(merged, self.cells)
+        st["phi_all"] = phi_all
+        phi_int = self._phi_int(dens, self.cells, mu.shape[1:])
         st["phi_int"] = phi_int
 
         out = np.zeros(mu.shape, complex)
@@ -399,6 +414,71 @@ class Accel:
             st["sing"], st["modes"] = sing, modes
             return y, st
         return y
+
+    # ------------------------------------------------------------------ field off the surface
+    def target_cell(self, xr, y):
+        """Cell (cx, cy) holding a target of the reference period inside the box (the last column and
+        row also take the box's right and top edges)."""
+        cx = min(int(math.floor(xr / self.L)), self.nx - 1)
+        cy = min(int(math.floor((y - self.hmin) / self.L)), self.ny - 1)
+        return cx, cy
+
+    def field(self, mu, pts, total=False):
+        """Scattered field at points of the cell box by Algorithm 3 with targets off the surface (the
+        remark after Algorithm 3: the steps of eqs. final_correction_0 and planewave evaluated at the
+        targets). Each target is reduced to the reference period, x = x_r + w d with x_r in [0, d);
+        in its cell the Fourier-Bessel fit of phi^ni = phi^all - phi^int gives the field of the
+        non-local sources, the nodes of the local cells add theirs exactly (plain trapezoid sum with
+        G_j; targets are off the surface), the completion modes add M^eta, and the quasi-periodic
+        phase e^{i alpha d w} restores the target's period."""
+        k, d, j, h, al = self.k, self.d, self.j, self.h, self.alpha
+        mu = np.asarray(mu, complex)
+        pts = np.asarray(pts, float).reshape(-1, 2)
+        w = np.floor(pts[:, 0] / d)
+        xr = pts[:, 0] - w * d
+        y = pts[:, 1]
+        top = self.hmin + self.ny * self.L
+        assert np.all((y >= self.hmin) & (y < top)), "targets outside the cell box"
+        tc = [self.target_cell(a, b) for a, b in zip(xr, y)]
+        cells = sorted(set(tc), key=lambda c: (c[1], c[0]))
+        dens = self._eq_densities(mu)
+        merged = self._merge(dens, ())
+        phi_all = self._phi_all(merged, cells)
+        phi_int = self._phi_int(dens, cells, ())
+        T, S = self.modes
+        msum = S @ mu
+        _, Ueta = dr.mode_sets(self.par)
+        ctr = np.array([self.L / 2, self.L / 2])
+        out = np.zeros(len(pts), complex)
+        for n_t, q in enumerate(tc):
+            phi_ni = np.array([phi_all[(q, t)] - phi_int[(q, t)] for t in range(len(self.samp_ori))])
+            wq = self.pinv_fb @ phi_ni
+            rel = np.array([[xr[n_t], y[n_t]]]) - (self.corner(*q) + ctr)
+            far = (self.fb_basis(rel) @ wq)[0]
+            near = 0j
+            for (cxr, cyr) in self.local_cells(q):
+                ref = cxr % self.nx
+                wrap = (cxr - ref) // self.nx
+                lidx = np.array(self.cell_nodes[(ref, cyr)])
+                mul = mu[lidx] * np.exp(1j * al * d * wrap)
+                X = xr[n_t] - (self.x[lidx] + wrap * d)
+                Y = y[n_t] - self.f[lidx]
+                if self.bc == 0:
+                    ax, ay = gr.gradGj(k, j, h, X, Y)
+                    kern = self.f1[lidx] * ax - ay
+                else:
+                    kern = gr.Gj(k, j, h, X, Y) * self.s[lidx]
+                near += self.dx * np.sum(kern * mul)
+            modes = 0j
+            for t, n in enumerate(Ueta):
+                an = al + 2 * math.pi * n / d
+                bn = complex(gr.beta_n(k, al, d, np.array([n]))[0])
+                modes += np.exp(1j * (an * xr[n_t] + bn * y[n_t])) * msum[t]
+            out[n_t] = (far + near + modes) * np.exp(1j * al * d * w[n_t])
+        if total:
+            al_, be_ = dr.wave(self.par)
+            out = out + np.exp(1j * (al_ * pts[:, 0] - be_ * pts[:, 1]))
+        return out
 
     def matrix(self):
         """The accelerated operator as a dense N x N matrix: Algorithm 3 applied to the identity."""
