@@ -91,13 +91,20 @@ def csinc(z):
 
 
 def Qj(beta, h, j):
-    """(1 - e^{i beta h})^j / beta, written as (-2i)^j e^{i j beta h/2} sin^{j-1}(beta h/2) (h/2) sinc(beta h/2)
-    so that the beta -> 0 limit (Wood anomaly) is evaluated exactly (Section 3.2, eq. betan_taylor)."""
+    """(1 - e^{i beta h})^j / beta. Where |beta h| < 1 it is written as
+    (-2i)^j e^{i j beta h/2} sin^{j-1}(beta h/2) (h/2) sinc(beta h/2), so that the beta -> 0 limit
+    (Wood anomaly) is evaluated exactly (Section 3.2, eq. betan_taylor); elsewhere the quotient itself
+    is well conditioned, while the factors of the rewrite overflow for strongly evanescent modes."""
     beta = np.asarray(beta, complex)
     if j == 0:
         return 1.0 / beta
-    half = beta * h / 2
-    return (-2j) ** j * np.exp(1j * j * half) * np.sin(half) ** (j - 1) * (h / 2) * csinc(half)
+    out = np.empty(beta.shape, complex)
+    small = np.abs(beta * h) < 1.0
+    half = beta[small] * h / 2
+    out[small] = (-2j) ** j * np.exp(1j * j * half) * np.sin(half) ** (j - 1) * (h / 2) * csinc(half)
+    b = beta[~small]
+    out[~small] = (1.0 - np.exp(1j * b * h)) ** j / b
+    return out
 
 
 # ------------------------------------------------------------------ shifted spectral series (Sec. 3.2)
