@@ -111,6 +111,25 @@ sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* ite
 sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int transpose_conj, double tol, int maxit, void* x_dev,
                          int* iters, double* relres);
 
+/* Scattered field off the surface (the remark after Algorithm 3; eq. int_eq_dirichlet discretised
+ * with the operator's trapezoid weights: the double layer of mu for Dirichlet, the single layer for
+ * Neumann, plus the completion modes M^eta) at n_targets points.
+ *   mu_dev    device complex128 [N], a density (normally the solution of sgf_solve)
+ *   xy        HOST double [2 n_targets], interleaved (x, y); any x (the field is alpha-quasi-
+ *             periodic), y >= h_min (the bottom of the cell box)
+ *   u_dev     device complex128 [n_targets], the field in the targets' order
+ *   total     0: u^scat; 1: u^scat + u^inc
+ * Targets inside the cell box (y < h_min + n_y L) take Algorithm 3 in FP64 with the target in
+ * place of a node: the convolved equivalent-source grids, the Fourier-Bessel fit of phi^ni on the
+ * target's cell, and the exact sum over the nodes of its local cells. Targets above the box take the
+ * Rayleigh form of the same sum (every node lies below them). The trapezoid sum loses accuracy
+ * within a few node spacings of the surface (near-singular integrand); the value below the surface
+ * is that of the representation, not a physical field.
+ * Errors: SGF_EINVAL for a non-finite target, a target below the box, a target on a node, or
+ * targets above the box too close to the highest node for the Rayleigh form (fewer than ~2e5
+ * modes); SGF_ESTATE before build. Synchronises. */
+sgf_status sgf_field(sgf_ctx* ctx, const void* mu_dev, long n_targets, const double* xy, void* u_dev, int total);
+
 /* Rayleigh coefficients B_n for n = n_lo..n_hi (eq. rayexp) from the solution mu (device), into
  * host B[2*(n_hi-n_lo+1)] (interleaved complex); host eff[n_hi-n_lo+1] gets e_n = beta_n/beta |B_n|^2
  * for propagating n (0 otherwise) and *energy_err = 1 - sum over propagating n in the range

@@ -193,7 +193,7 @@ static void layouts(sgf_ctx* c, std::vector<double>& src_rel, std::vector<double
 }
 
 // Rows c of cells meeting S^r - m h e_2 for some 0 <= m <= j (half-open cells, Section 5.3).
-static std::set<int> rows_of_Sj(int cy_r, int j, double h, double L) {
+std::set<int> rows_of_Sj(int cy_r, int j, double h, double L) {
   std::set<int> rows;
   for (int m = 0; m <= j; ++m) {
     double sh = m * h / L;
@@ -204,8 +204,16 @@ static std::set<int> rows_of_Sj(int cy_r, int j, double h, double L) {
   return rows;
 }
 
+// (1 - e^{i beta h})^j / beta; for |beta h| < 1 in the form (-2i)^j e^{i j beta h/2}
+// sin^{j-1}(beta h/2) (h/2) sinc(beta h/2) that is exact at beta = 0 (eq. betan_taylor). Beyond, the
+// quotient is well conditioned and the rewrite's factors would overflow for evanescent modes.
 static cd Qj_host(cd beta, double h, int j) {
   if (j == 0) return 1.0 / beta;
+  if (std::abs(beta * h) >= 1.0) {
+    cd q = 1.0 - std::exp(cd(0, 1) * (beta * h)), acc = 1.0;
+    for (int m = 0; m < j; ++m) acc *= q;
+    return acc / beta;
+  }
   cd half = 0.5 * h * beta;
   cd sn = std::sin(half);
   cd sinc = std::abs(half) < 1e-3 ? 1.0 - half * half / 6.0 + std::pow(half, 4) / 120.0 : std::sin(half) / half;
@@ -229,6 +237,19 @@ static std::vector<int> ueta_set(sgf_ctx* c) {
     if (std::abs(Qj_host(bn, c->prm.h, c->prm.j)) < c->prm.eta && std::abs(bn) <= k) out.push_back(n);
   }
   return out;
+}
+
+void rayleigh_mode_params(sgf_ctx* c, int n_lo, int nmod, double* mp) {
+  std::vector<int> ue = ueta_set(c);
+  for (int t = 0; t < nmod; ++t) {
+    int n = n_lo + t;
+    double an = c->alpha + 2 * SGF_PI * n / c->d;
+    cd bn = beta_host(c->k, an);
+    cd Q = Qj_host(bn, c->prm.h, c->prm.j);
+    bool in = std::find(ue.begin(), ue.end(), n) != ue.end();
+    mp[6 * t] = an; mp[6 * t + 1] = bn.real(); mp[6 * t + 2] = bn.imag();
+    mp[6 * t + 3] = Q.real(); mp[6 * t + 4] = Q.imag(); mp[6 * t + 5] = in ? 1.0 : 0.0;
+  }
 }
 
 static sgf_status validate(sgf_ctx* ctx) {
@@ -606,6 +627,7 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(launch_near(c, d_phi, dcy_min, n_dcy, d_Iplain, pp, d_kress));
   c->keep.coll_rel = d_coll_rel;
   c->keep.samp_rel = d_samp_rel;
+  c->keep.src_rel = d_src_rel;
   c->keep.kress = d_kress;
   c->keep.pinv_eq = d_pinv_eq;
   c->keep.pinv_fb = d_pinv_fb;
@@ -1051,19 +1073,10 @@ extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, i
   if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (n_hi < n_lo || n_hi - n_lo > 100000) return set_err(ctx, SGF_EINVAL, "bad mode range");
   int nmod = n_hi - n_lo + 1;
-  std::vector<int> ue = ueta_set(ctx);
   std::vector<double> mp(6 * nmod);
+  rayleigh_mode_params(ctx, n_lo, nmod, mp.data());
   std::vector<cd> bns(nmod);
-  for (int t = 0; t < nmod; ++t) {
-    int n = n_lo + t;
-    double an = ctx->alpha + 2 * SGF_PI * n / ctx->d;
-    cd bn = beta_host(ctx->k, an);
-    cd Q = Qj_host(bn, ctx->prm.h, ctx->prm.j);
-    bool in = std::find(ue.begin(), ue.end(), n) != ue.end();
-    mp[6 * t] = an; mp[6 * t + 1] = bn.real(); mp[6 * t + 2] = bn.imag();
-    mp[6 * t + 3] = Q.real(); mp[6 * t + 4] = Q.imag(); mp[6 * t + 5] = in ? 1.0 : 0.0;
-    bns[t] = bn;
-  }
+  for (int t = 0; t < nmod; ++t) bns[t] = cd(mp[6 * t + 1], mp[6 * t + 2]);
   double* d_mp;
   zd* d_B;
   CU(cudaMalloc(&d_mp, mp.size() * sizeof(double)));

@@ -104,6 +104,25 @@ __device__ inline zd csinc(zd z) {
   return cdiv(csin(z), z);
 }
 
+__device__ inline int orient_of_sample(int t, int p) { return t < 2 * (p + 1) ? 0 : 1; }
+
+// J_n(x) e^{i n th} for any integer n (J_{-n} = (-1)^n J_n): the Fourier-Bessel functions of the
+// cell reconstruction, normalised by fb_norm(n, k rho_0) = (k rho_0 / 2)^|n| / |n|!
+__device__ inline zd fb_Z(int n, double kr, double th) {
+  int an = n < 0 ? -n : n;
+  // J_n(0) = delta_{n0}; evaluated explicitly (a node can sit exactly at a cell centre)
+  double J = kr > 0 ? jn(an, kr) : (an == 0 ? 1.0 : 0.0);
+  if (n < 0 && (an & 1)) J = -J;
+  zd e = expi(n * th);
+  return J * e;
+}
+__device__ inline double fb_norm(int n, double krho0) {
+  int an = n < 0 ? -n : n;
+  double v = 1.0;
+  for (int i = 1; i <= an; ++i) v *= (krho0 / 2.0) / i;
+  return v;
+}
+
 // H0^(1)(x), H1^(1)(x) for real x > 0 from the CUDA Bessel functions of the first and second kind.
 __device__ inline zd hankel0(double x) { return zd(j0(x), y0(x)); }
 __device__ inline zd hankel1(double x) { return zd(j1(x), y1(x)); }

@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <string>
+#include <set>
 #include <vector>
 #include <algorithm>
 
@@ -48,7 +49,7 @@ struct NearPairs {  // device arrays of the (q, r) block list
 // Build-time operands kept after sgf_build_operator so that the node-dependent factors (P, I, the
 // near operator, mode factors) can be rebuilt at moved node positions by sgf_gradient.
 struct BuildKeep {
-  double *coll_rel = nullptr, *samp_rel = nullptr, *kress = nullptr, *modes_n = nullptr;
+  double *coll_rel = nullptr, *samp_rel = nullptr, *src_rel = nullptr, *kress = nullptr, *modes_n = nullptr;
   zd *pinv_eq = nullptr, *pinv_fb = nullptr, *phi = nullptr, *Iplain = nullptr;
   long* tr_off = nullptr;  // adjoint near layout: destination offset and leading dimension per block
   int* tr_ld = nullptr;
@@ -145,6 +146,11 @@ struct sgf_ctx {
 };
 
 sgf_status set_err(sgf_ctx* ctx, sgf_status st, const char* fmt, ...);
+// host helpers shared by the entry points (sgf_capi.cu)
+// cell rows cy_q whose cells lie within the local reach S_j of source row cy_r (the local sets L(q))
+std::set<int> rows_of_Sj(int cy_r, int j, double h, double L);
+// per mode n_lo .. n_lo + nmod - 1: [alpha_n, Re beta_n, Im beta_n, Re Q_j, Im Q_j, n in U^eta]
+void rayleigh_mode_params(sgf_ctx* c, int n_lo, int nmod, double* mp);
 
 // ---------------------------------------------------------------- launchers (sgf_kernels.cu)
 struct BuildArgs;
@@ -185,6 +191,7 @@ cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s);
 cudaError_t launch_grad_acc(zd* g, double s, const zd* a, const zd* u, const zd* v, long n, cudaStream_t st);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
+cudaError_t launch_far_grids64(sgf_ctx* c, const zd* mu);  // phi^all on the grids only (field evaluation)
 cudaError_t launch_apply_adj64(sgf_ctx* c, const zd* v, zd* out);
 cudaError_t launch_apply_adj32(sgf_ctx* c, const zd* v, zd* out);
 cudaError_t launch_conj_transpose(const zd* src, long R, long Cc, zd* dst, cudaStream_t s);

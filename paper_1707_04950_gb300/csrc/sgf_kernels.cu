@@ -25,26 +25,6 @@
 #include "sgf_internal.h"
 #include "sgf_fft.cuh"
 
-// ============================================================== small device helpers
-__device__ inline int orient_of_sample(int t, int p) { return t < 2 * (p + 1) ? 0 : 1; }
-
-
-// J_n(x) e^{i n th} for any integer n (J_{-n} = (-1)^n J_n)
-__device__ inline zd fb_Z(int n, double kr, double th) {
-  int an = n < 0 ? -n : n;
-  // J_n(0) = delta_{n0}; evaluated explicitly (a node can sit exactly at a cell centre)
-  double J = kr > 0 ? jn(an, kr) : (an == 0 ? 1.0 : 0.0);
-  if (n < 0 && (an & 1)) J = -J;
-  zd e = expi(n * th);
-  return J * e;
-}
-__device__ inline double fb_norm(int n, double krho0) {
-  int an = n < 0 ? -n : n;
-  double v = 1.0;
-  for (int i = 1; i <= an; ++i) v *= (krho0 / 2.0) / i;
-  return v;
-}
-
 // ============================================================== profile
 __global__ void k_profile(const double* __restrict__ coef, int M, double d, int N, double* x, double* f,
                           double* f1, double* f2) {
@@ -1412,6 +1392,34 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
 
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<double>(c, c->o64, mu, out); }
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<float>(c, c->o32, mu, out); }
+
+// EqSources + GlobalEqSMerge + GlobalFFT alone, in FP64 on the context's stream: leaves the
+// twisted phi^all of every grid point in o64.grid[lambda] (first array of each orientation) for
+// evaluations at points other than the nodes.
+cudaError_t launch_far_grids64(sgf_ctx* c, const zd* mu) {
+  cudaStream_t s = c->stream;
+  OpData<double>& od = c->o64;
+  const Orient& oH = c->og[0];
+  const Orient& oV = c->og[1];
+  long szH = (long)oH.Px * oH.nrow, szV = (long)oV.Px * oV.nrow;
+  cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(zd), s);
+  cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(zd), s);
+  k_project<double><<<c->n_items + c->nm * c->mode_chunks, 128, (size_t)32 * sizeof(zd), s>>>(
+      c->n_occ, c->neq, c->nm, c->N, c->d_cell_start, c->d_node_idx, mu, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
+      szH, od.grid[1], szV, c->d_MS, c->d_MSff, c->d_mpart, c->d_mpart_ff, nullptr, c->mode_chunks, c->n_items,
+      c->d_item_cell, c->d_item_lo, c->d_item_hi);
+  cudaError_t e;
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    long sz = (long)o.Px * o.nrow;
+    if ((e = run_fft_x<double>(od.grid[lam], o, o.nrow, 2, od.tw, c->twlog, -1, s)) != cudaSuccess) return e;
+    e = conv_y<double>(od.grid[lam], od.grid[lam] + sz, od.Khat[lam][0], od.Khat[lam][1], o, od.twy[lam],
+                       od.accg[lam], s);
+    if (e != cudaSuccess) return e;
+    if ((e = run_fft_x<double>(od.grid[lam], o, o.nrow, 1, od.tw, c->twlog, +1, s)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
 
 // ============================================================== adjoint map
 // The forward map is  out = hs mu + MT (MS mu) + C mu + Ip G(K (S P mu))  with P the per-cell
