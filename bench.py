@@ -219,6 +219,7 @@ def run_ours(args):
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
     tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
+    field = run_field(dev, stream) if args.field and rank == 0 else None
     st32 = res[32]["stages_ms"]
     cufft = run_cufft_reference(res[32]["info"], st32["fft_x"] + st32["conv_y"] + st32["ifft_x"], dev, stream, flush,
                                 max(3, min(args.steps, 50))) if rank == 0 else None
@@ -272,6 +273,8 @@ def run_ours(args):
         line["gradient"] = grad
     if tune is not None:
         line["autotune"] = tune
+    if field is not None:
+        line["field"] = field
     if cufft is not None:
         line["cufft_reference"] = cufft
     if not args.no_cpu_baseline and ws >= 1:
@@ -345,6 +348,41 @@ def run_gradient(dev, stream):
             "forward_solve_s": t_solve, "forward_iters": its, "gradient_s": t_grad, "adjoint_iters": adj_its,
             "grad_norm": float(np.sqrt(np.sum(ga**2) + np.sum(gb**2))),
             "difference_quotient_equivalent_s": 2 * (2 * M) * t_solve}
+
+
+def run_field(dev, stream, n_side=256):
+    """Scattered field image of the deep corrugation (N = 16384, mixed operator; the field itself is
+    FP64): an n_side x n_side grid over one period, from the bottom of the cell box to one period
+    above its top, keeping the targets at least three node spacings above the surface. One
+    sgf_field call = host binning + copies of the targets + kernels + synchronisation."""
+    import torch
+
+    from paper_1707_04950_gb300 import sgf
+
+    par = inputs.wl_deep_corrugation_neumann()
+    op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=32)
+    mu = torch.from_numpy(inputs.random_density(par["N"], 21)).to(dev)
+    top = par["hmin"] + par["ny"] * par["L"]
+    xs = np.arange(n_side) * par["d"] / n_side
+    ys = par["hmin"] + np.arange(n_side) * (top + par["d"] - par["hmin"]) / n_side
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    fx = inputs.profile_eval_host({"d": par["d"], "a": par["a"], "b": par["b"]}, X.ravel())
+    keep = Y.ravel() > fx + 3 * par["d"] / par["N"]
+    xy = np.stack([X.ravel()[keep], Y.ravel()[keep]], 1)
+    u = torch.empty(len(xy), dtype=torch.complex128, device=dev)
+    sgf.sgf_field(op.ctx, mu.data_ptr(), xy, u.data_ptr())  # warm-up
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sgf.sgf_field(op.ctx, mu.data_ptr(), xy, u.data_ptr())
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / reps
+    n_box = int(np.sum(xy[:, 1] < top))
+    op.close()
+    return {"workload": f"deep corrugation N=16384, {n_side}x{n_side} image over one period",
+            "targets": len(xy), "targets_in_box": n_box, "targets_above_box": len(xy) - n_box,
+            "s_per_call": t, "value": len(xy) / t, "unit": "targets/s", "precision": "fp64"}
 
 
 def run_autotune(dev, stream):
@@ -500,6 +538,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
+    ap.add_argument("--field", type=int, default=1, help="1: time the scattered-field image block")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
