@@ -111,6 +111,26 @@ sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* ite
 sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int transpose_conj, double tol, int maxit, void* x_dev,
                          int* iters, double* relres);
 
+/* The unaccelerated Nystrom operator (Section 4: eq. discrete_eq with D^dx = D~_sing + D~_reg + D_M,
+ * eqs. local_mat, D_ns, G_jq_s, D_M_deltax; G~ by the hybrid spectral/spatial evaluation of
+ * Sections 3.2 and 4.2.3) assembled as a dense row-major N x N complex128 matrix in device memory
+ * owned by the context (16 N^2 bytes; 8 <= N <= 32768, 2 <= Ma < N/2). It needs the profile, the
+ * wave and the parameters (N, j, h, n_per, c_win, Ma, eta, delta_min, spec_exp; the accelerator's
+ * cell parameters are not used) and works with or without sgf_build_operator; a later
+ * sgf_build_operator discards it. Errors: SGF_ESTATE before the setters, SGF_EINVAL for sizes out
+ * of range, SGF_EWINDOW (j > 0 and h <= a max|f'|). Synchronises. */
+sgf_status sgf_build_exact(sgf_ctx* ctx);
+
+/* Which operator sgf_apply, sgf_apply_host, sgf_solve and sgf_solve_rhs use: 0 the accelerated
+ * operator of sgf_build_operator (the default), 1 the dense operator of sgf_build_exact (FP64 GEMV,
+ * forward and adjoint; solves skip the mixed-precision refinement). sgf_gradient, sgf_field and
+ * batches always use the accelerated operator (sgf_gradient refuses while 1 is selected).
+ * SGF_ESTATE when 1 is asked before sgf_build_exact. */
+sgf_status sgf_select_operator(sgf_ctx* ctx, int exact);
+
+/* Copy of the dense operator into A_dev (device complex128, N*N, row-major). Synchronises. */
+sgf_status sgf_exact_matrix(const sgf_ctx* ctx, void* A_dev);
+
 /* Scattered field off the surface (the remark after Algorithm 3; eq. int_eq_dirichlet discretised
  * with the operator's trapezoid weights: the double layer of mu for Dirichlet, the single layer for
  * Neumann, plus the completion modes M^eta) at n_targets points.

@@ -349,6 +349,7 @@ sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* 
   for (int p = 0; p < n; ++p) {
     sgf_ctx* c = ctxs[p];
     if (!c || !c->built) return berr(B, SGF_ESTATE, "context %d is not built", p);
+    if (c->op_exact) return berr(B, SGF_EINVAL, "context %d has the dense operator selected", p);
     if (c->device != B->device) return berr(B, SGF_EINVAL, "context %d is on another device", p);
     bool mixed = c->prm.precision == 32;
     if (!c->use_graphs || !c->gs[0].ok || (mixed && !c->gs[1].ok))

@@ -55,6 +55,8 @@ static void free_all(sgf_ctx* ctx) {
   ctx->keep = BuildKeep();
   ctx->o32 = OpData<float>();
   ctx->built = false;
+  ctx->d_Aex = nullptr;
+  ctx->geom = ctx->exact_ready = ctx->op_exact = false;
 }
 
 static int ilog2_exact(long n) {
@@ -118,7 +120,7 @@ sgf_status sgf_set_profile_fourier(sgf_ctx* ctx, double d, int M, const double* 
   ctx->fb.assign(b, b + M + 1);
   ctx->fb[0] = 0;
   ctx->have_profile = true;
-  ctx->built = false;
+  ctx->built = ctx->geom = ctx->exact_ready = ctx->op_exact = false;
   return SGF_OK;
 }
 
@@ -132,7 +134,7 @@ sgf_status sgf_set_wave(sgf_ctx* ctx, double k, double theta, int bc) {
   ctx->beta = k * cos(theta);
   ctx->bc = bc;
   ctx->have_wave = true;
-  ctx->built = false;
+  ctx->built = ctx->geom = ctx->exact_ready = ctx->op_exact = false;
   return SGF_OK;
 }
 
@@ -140,7 +142,7 @@ sgf_status sgf_set_params(sgf_ctx* ctx, const sgf_params* p) {
   if (!ctx || !p) return SGF_EINVAL;
   ctx->prm = *p;
   ctx->have_params = true;
-  ctx->built = false;
+  ctx->built = ctx->geom = ctx->exact_ready = ctx->op_exact = false;
   return SGF_OK;
 }
 
@@ -784,6 +786,11 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
 static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec);
 
 static sgf_status apply_adj_prec(sgf_ctx* ctx, const zd* v, zd* out, int prec) {
+  if (ctx->op_exact) {
+    cudaError_t e = launch_exact_gemv(ctx, v, out, true);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "exact adjoint apply: %s", cudaGetErrorString(e));
+    return SGF_OK;
+  }
   if (!ctx->adj_ok)
     return set_err(ctx, SGF_EINVAL, "adjoint near rows of %d columns exceed the shared-memory limit", ctx->maxWT);
   cudaError_t e = prec == 64 ? launch_apply_adj64(ctx, v, out) : launch_apply_adj32(ctx, v, out);
@@ -791,9 +798,11 @@ static sgf_status apply_adj_prec(sgf_ctx* ctx, const zd* v, zd* out, int prec) {
   return SGF_OK;
 }
 
+static bool op_ready(const sgf_ctx* ctx) { return ctx->op_exact ? ctx->exact_ready : ctx->built; }
+
 extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev, int nrhs, int transpose_conj) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!op_ready(ctx)) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (transpose_conj != 0 && transpose_conj != 1) return set_err(ctx, SGF_EINVAL, "transpose_conj must be 0 or 1");
   if (nrhs < 1 || !mu_dev || !out_dev) return set_err(ctx, SGF_EINVAL, "bad apply arguments");
   for (int r = 0; r < nrhs; ++r) {
@@ -803,7 +812,7 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
                                    : apply_prec(ctx, mu, out, ctx->prm.precision);
     if (st != SGF_OK) return st;
   }
-  if (transpose_conj) return SGF_OK;
+  if (transpose_conj || ctx->op_exact) return SGF_OK;
   if (ctx->profiling) {
     cudaEventSynchronize(ctx->ev[5]);
     float ms;
@@ -820,6 +829,11 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
 static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec) {
   const GraphSlot& gs = ctx->gs[prec == 64 ? 0 : 1];
   cudaError_t e;
+  if (ctx->op_exact) {
+    e = launch_exact_gemv(ctx, mu, out, false);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "exact apply: %s", cudaGetErrorString(e));
+    return SGF_OK;
+  }
   if (ctx->use_graphs && gs.ok && !ctx->profiling && ctx->debug_mask == 15)
     e = launch_apply_graph(ctx, prec, mu, out);
   else
@@ -830,7 +844,7 @@ static sgf_status apply_prec(sgf_ctx* ctx, const zd* mu, zd* out, int prec) {
 
 extern "C" sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* out_host, int nrhs) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!op_ready(ctx)) return set_err(ctx, SGF_ESTATE, "operator not built");
   size_t nb = (size_t)ctx->N * sizeof(zd);
   for (int r = 0; r < nrhs; ++r) {
     CU(cudaMemcpyAsync(ctx->d_mu_tmp, (const char*)mu_host + r * nb, nb, cudaMemcpyHostToDevice, ctx->stream));
@@ -843,7 +857,7 @@ extern "C" sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* ou
 
 extern "C" sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!ctx->built && !ctx->geom) return set_err(ctx, SGF_ESTATE, "operator not built");
   CU(launch_rhs(ctx, (zd*)out_dev));
   return SGF_OK;
 }
@@ -972,9 +986,9 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
 static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol, int maxit, void* x_dev, int* iters,
                              double* relres) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!op_ready(ctx)) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (!(tol > 0) || maxit < 1 || !x_dev) return set_err(ctx, SGF_EINVAL, "bad solve arguments");
-  if (adj && !ctx->adj_ok) return apply_adj_prec(ctx, nullptr, nullptr, 64);
+  if (adj && !ctx->op_exact && !ctx->adj_ok) return apply_adj_prec(ctx, nullptr, nullptr, 64);
   const long N = ctx->N;
   Krylov K;
   // restart length: up to 1000 Krylov vectors (unrestarted below that), within 2 GiB of basis
@@ -1000,7 +1014,7 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
     cudaMemcpyAsync(b, b_in, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
   else
     launch_rhs(ctx, b);
-  if (ctx->prm.precision == 64) {
+  if (ctx->prm.precision == 64 || ctx->op_exact) {
     st = gmres(ctx, K, 64, adj, b, x, tol, maxit, &its, &rr);
   } else {
     // FP64 residual refinement around inner mixed-precision GMRES solves
@@ -1070,7 +1084,7 @@ extern "C" sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int trans
 extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                                    double* energy_err) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!ctx->built && !ctx->geom) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (n_hi < n_lo || n_hi - n_lo > 100000) return set_err(ctx, SGF_EINVAL, "bad mode range");
   int nmod = n_hi - n_lo + 1;
   std::vector<double> mp(6 * nmod);
@@ -1164,6 +1178,8 @@ static sgf_status gradient_impl(sgf_ctx* ctx, const void* mu_dev, int n_mode, do
                                 double* e_n, double* grad_a, double* grad_b, int* adj_iters, bool analytic) {
   if (!ctx) return SGF_EINVAL;
   if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (ctx->op_exact)
+    return set_err(ctx, SGF_ESTATE, "the gradient differentiates the accelerated operator: select it first");
   if (!mu_dev || !grad_a || !grad_b || !(tol > 0) || maxit < 1) return set_err(ctx, SGF_EINVAL, "bad gradient arguments");
   if (!ctx->adj_ok || !ctx->keep.tr_off) return apply_adj_prec(ctx, nullptr, nullptr, 64);
   sgf_ctx* c = ctx;
@@ -1453,4 +1469,101 @@ extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode,
 extern "C" sgf_status sgf_gradient_fd(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,
                                       double* e_n, double* grad_a, double* grad_b, int* adj_iters) {
   return gradient_impl(ctx, mu_dev, n_mode, tol, maxit, B, e_n, grad_a, grad_b, adj_iters, false);
+}
+
+// ------------------------------------------------------------------------------------------
+// The unaccelerated operator as a dense matrix (Section 4). Without an accelerated build it sets up
+// the nodes, the log-quadrature weights and the completion modes itself (no cells are needed).
+extern "C" sgf_status sgf_build_exact(sgf_ctx* ctx) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->have_profile || !ctx->have_wave || !ctx->have_params)
+    return set_err(ctx, SGF_ESTATE, "profile, wave and params must be set before build");
+  const sgf_params& P = ctx->prm;
+  if (P.N < 8 || P.N > 32768 || P.j < 0 || P.j > 24 || !(P.h > 0) || P.n_per < 1 || P.Ma < 2 || 2 * P.Ma >= P.N ||
+      !(P.c_win > 0 && P.c_win < 1) || !(P.delta_min > 0) || !(P.spec_exp > 0))
+    return set_err(ctx, SGF_EINVAL, "parameter out of range for the dense operator (8 <= N <= 32768, 2 <= Ma < N/2)");
+  CU(cudaSetDevice(ctx->device));
+  sgf_ctx* c = ctx;
+  if (!c->built && !c->geom) {
+    free_all(ctx);
+    c->N = P.N;
+    c->dx = c->d / P.N;
+    c->a_s = P.Ma * c->dx;
+    c->gam = 0.5 * c->a_s;
+    int M = (int)c->fa.size() - 1;
+    TRY(dalloc(ctx, &c->d_coef, 2 * (M + 1)));
+    CU(cudaMemcpyAsync(c->d_coef, c->fa.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_coef + M + 1, c->fb.data(), (M + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    TRY(dalloc(ctx, &c->d_x, c->N));
+    TRY(dalloc(ctx, &c->d_f, c->N));
+    TRY(dalloc(ctx, &c->d_f1, c->N));
+    TRY(dalloc(ctx, &c->d_f2, c->N));
+    CU(launch_profile(c));
+    c->hx.resize(c->N); c->hf.resize(c->N); c->hf1.resize(c->N); c->hf2.resize(c->N);
+    CU(cudaMemcpyAsync(c->hx.data(), c->d_x, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->hf.data(), c->d_f, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->hf1.data(), c->d_f1, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    double maxslope = 0;
+    for (int i = 0; i < c->N; ++i) maxslope = std::max(maxslope, fabs(c->hf1[i]));
+    if (P.j > 0 && !(P.h > c->a_s * maxslope))
+      return set_err(ctx, SGF_EWINDOW, "shift h = %g must exceed a max|f'| = %g", P.h, c->a_s * maxslope);
+    std::vector<double> binw(P.j + 1);
+    for (int m = 0; m <= P.j; ++m) {
+      double cb = 1;
+      for (int i = 0; i < m; ++i) cb = cb * (P.j - i) / (i + 1);
+      binw[m] = (m % 2 ? -1.0 : 1.0) * cb;
+    }
+    TRY(dalloc(ctx, &c->d_binw, binw.size()));
+    CU(cudaMemcpy(c->d_binw, binw.data(), binw.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<double> kress(2 * P.Ma - 1);
+    for (int s = -(P.Ma - 1); s <= P.Ma - 1; ++s) {
+      double acc = 0;
+      for (int m = 1; m < P.Ma; ++m) acc += cos(SGF_PI * m * s / P.Ma) / m;
+      kress[s + P.Ma - 1] = -2 * c->dx * acc - c->dx / P.Ma * ((s & 1) ? -1.0 : 1.0);
+    }
+    TRY(dalloc(ctx, &c->keep.kress, kress.size()));
+    CU(cudaMemcpy(c->keep.kress, kress.data(), kress.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<int> ue = ueta_set(c);
+    c->nm = (int)ue.size();
+    std::vector<double> mn(3 * std::max(1, c->nm));
+    for (int t = 0; t < c->nm; ++t) {
+      double an = c->alpha + 2 * SGF_PI * ue[t] / c->d;
+      cd bn = beta_host(c->k, an);
+      mn[3 * t] = an; mn[3 * t + 1] = bn.real(); mn[3 * t + 2] = bn.imag();
+    }
+    TRY(dalloc(ctx, &c->keep.modes_n, mn.size()));
+    CU(cudaMemcpy(c->keep.modes_n, mn.data(), mn.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TRY(dalloc(ctx, &c->d_MT, (size_t)c->N * std::max(1, c->nm)));
+    TRY(dalloc(ctx, &c->d_MS, (size_t)c->N * std::max(1, c->nm)));
+    CU(launch_modes(c, c->keep.modes_n));
+    TRY(dalloc(ctx, &c->d_msum, 64));
+    TRY(dalloc(ctx, &c->d_mu_tmp, (size_t)c->N * 2));
+    TRY(dalloc(ctx, &c->d_out_tmp, (size_t)c->N * 2));
+    c->geom = true;
+  }
+  if (!c->d_Aex) TRY(dalloc(ctx, &c->d_Aex, (size_t)c->N * c->N));
+  zd hk(0, 0);
+  CU(near_hk(c, &hk));
+  CU(launch_exact_entries(c, hk));
+  CU(cudaStreamSynchronize(c->stream));
+  c->exact_ready = true;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_select_operator(sgf_ctx* ctx, int exact) {
+  if (!ctx) return SGF_EINVAL;
+  if (exact != 0 && exact != 1) return set_err(ctx, SGF_EINVAL, "operator selector must be 0 or 1");
+  if (exact && !ctx->exact_ready) return set_err(ctx, SGF_ESTATE, "dense operator not built");
+  ctx->op_exact = exact == 1;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_exact_matrix(const sgf_ctx* ctx_, void* A_dev) {
+  sgf_ctx* ctx = const_cast<sgf_ctx*>(ctx_);
+  if (!ctx || !A_dev) return SGF_EINVAL;
+  if (!ctx->exact_ready) return set_err(ctx, SGF_ESTATE, "dense operator not built");
+  CU(cudaMemcpyAsync(A_dev, ctx->d_Aex, (size_t)ctx->N * ctx->N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return SGF_OK;
 }

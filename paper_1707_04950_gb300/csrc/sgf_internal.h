@@ -143,6 +143,10 @@ struct sgf_ctx {
   int launches_per_apply = 0;
   double bytes64 = 0, bytes32 = 0;
   BuildKeep keep;
+  // the unaccelerated operator as a dense row-major N x N matrix (sgf_build_exact); geom: the nodes,
+  // weights and mode factors exist without the accelerated build
+  zd* d_Aex = nullptr;
+  bool geom = false, exact_ready = false, op_exact = false;
 };
 
 sgf_status set_err(sgf_ctx* ctx, sgf_status st, const char* fmt, ...);
@@ -191,7 +195,12 @@ cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s);
 cudaError_t launch_grad_acc(zd* g, double s, const zd* a, const zd* u, const zd* v, long n, cudaStream_t st);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
-cudaError_t launch_far_grids64(sgf_ctx* c, const zd* mu);  // phi^all on the grids only (field evaluation)
+cudaError_t launch_far_grids64(sgf_ctx* c, const zd* mu);
+// the dense unaccelerated operator (sgf_exact.cu): entries of d_Aex; y = A x or A^H x
+cudaError_t launch_exact_entries(sgf_ctx* c, zd hk);
+cudaError_t launch_exact_gemv(sgf_ctx* c, const zd* x, zd* y, bool adjoint);
+// sum_{m=1..j} (-1)^m C(j,m) (ik/4) H1(k m h): the shifted images' part of the K_r diagonal
+cudaError_t near_hk(sgf_ctx* c, zd* hk);  // phi^all on the grids only (field evaluation)
 cudaError_t launch_apply_adj64(sgf_ctx* c, const zd* v, zd* out);
 cudaError_t launch_apply_adj32(sgf_ctx* c, const zd* v, zd* out);
 cudaError_t launch_conj_transpose(const zd* src, long R, long Cc, zd* dst, cudaStream_t s);

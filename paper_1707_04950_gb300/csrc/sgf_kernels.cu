@@ -339,54 +339,6 @@ struct TabArgs {
   int j, Px, logPx, Py, nrow, lam;
 };
 
-__device__ inline double row_delta(double Y, int j, double h) {
-  double dl = fabs(Y);
-  for (int m = 1; m <= j; ++m) dl = fmin(dl, fabs(Y + m * h));
-  return dl;
-}
-
-// (1 - e^{i beta h})^j / beta = (-2i)^j e^{i j beta h/2} sin^{j-1}(beta h/2) (h/2) sinc(beta h/2)
-__device__ inline zd Qj_dev(zd beta, double h, int j) {
-  if (j == 0) return cdiv(zd(1, 0), beta);
-  zd half = (0.5 * h) * beta;
-  zd sn = csin(half);
-  zd acc = (0.5 * h) * csinc(half);
-  for (int m = 1; m < j; ++m) acc = acc * sn;
-  zd mi2(1, 0);
-  for (int m = 0; m < j; ++m) mi2 = mi2 * zd(0, -2);
-  zd ij = cexpz(zd(0, (double)j) * half);
-  return mi2 * ij * acc;
-}
-
-// c_n(Y) and cy_n(Y) of the shifted spectral series (eq. shifted_quasi_per_rayleigh), with the
-// exact beta -> 0 rewrite of eq. betan_taylor where |beta| (|Y| + j h) < 1.
-__device__ inline void spec_coef(double k, double alpha, double d, int j, double h, double Y, int n,
-                                 const double* binw, zd& c, zd& cy, double& an) {
-  an = alpha + 2.0 * SGF_PI * n / d;
-  double q = k * k - an * an;
-  bool real_b = q >= 0;
-  double bm = sqrt(fabs(q));
-  zd beta = real_b ? zd(bm, 0) : zd(0, bm);
-  zd S0(0, 0), S1(0, 0);
-  for (int m = 0; m <= j; ++m) {
-    double t = Y + m * h, at = fabs(t);
-    zd em = real_b ? expi(bm * at) : zd(exp(-bm * at), 0);
-    S0 += binw[m] * em;
-    S1 += (t > 0 ? binw[m] : (t < 0 ? -binw[m] : 0.0)) * em;
-  }
-  cy = (-0.5 / d) * S1;
-  if (j >= 1 && bm * (fabs(Y) + j * h) < 1.0) {
-    zd acc = cexpz(zd(0, 1) * (Y * beta)) * Qj_dev(beta, h, j);
-    for (int m = 0; m <= j; ++m) {
-      double t = Y + m * h;
-      if (t < 0) acc -= zd(0, 2.0 * binw[m] * t) * csinc(t * beta);
-    }
-    c = zd(0, 0.5 / d) * acc;
-  } else {
-    c = zd(0, 0.5 / d) * cdiv(S0, beta);
-  }
-}
-
 // Block per lag row iy_lag in [-(nrow-1), nrow-1] whose delta >= delta_min: writes
 // Tx[kx][iy_cyc] = Px * sum_{n = kx mod Px} coefficient (the X transform of the twisted row).
 __global__ void k_table_spec(TabArgs a, const double* __restrict__ binw, zd* Txm, zd* Txd) {

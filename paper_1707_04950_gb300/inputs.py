@@ -85,8 +85,9 @@ def harmonic_surface(d, n_harm, scale, seed):
 
 def make_params(prof, k, theta_deg, bc, N, *, j=8, h0=0.5, n_per=40, nx, ny=None, hmin=None,
                 p=8, e=1, n_coll=200, n_fb=12, eta=1e-3, delta_min=None, spec_exp=40.0,
-                c_win=0.5, precision=64, ls_reg=1e-6):
-    """Assemble the full parameter record of one scattering problem."""
+                c_win=0.5, precision=64, ls_reg=1e-6, h=None):
+    """Assemble the full parameter record of one scattering problem. The shift h is h0 moved off the
+    accelerator's grid lags unless given exactly (the dense operator has no grid)."""
     d = prof["d"]
     dx = d / N
     L = d / nx
@@ -101,7 +102,8 @@ def make_params(prof, k, theta_deg, bc, N, *, j=8, h0=0.5, n_per=40, nx, ny=None
     Ma = int(math.floor(0.75 * L / dx + 1e-9))
     a_s = Ma * dx
     dg = L / p
-    h = (round(h0 / dg) + 1.0 / (j + 1)) * dg
+    if h is None:
+        h = (round(h0 / dg) + 1.0 / (j + 1)) * dg
     if delta_min is None:
         delta_min = d / 64.0
     theta = math.radians(theta_deg)
@@ -173,6 +175,22 @@ def wl_harmonic_gradient_small(N=256, d=2.0, n_harm=3, scale=0.05, nx=8, seed=4,
     """The same kind of surface at period 2 with 3 harmonics: the small gradient parity case."""
     prof = harmonic_surface(d, n_harm, scale, seed)
     return make_params(prof, 2 * math.pi, 20.0, bc, N, nx=nx, **kw)
+
+
+def wl_composite(N, n_per, wood=False, nx=32, **kw):
+    """Composite surface f = -(sin x + sin 2x / 2 + sin 3x / 3 + sin 4x / 4) / 4, d = 2 pi, theta =
+    45 deg, Dirichlet (the convergence study of Section 6.1): k = 20 with the unshifted Green function
+    (j = 0), or the Wood wavenumber k = 6 / (1 - sin 45 deg) with j = 8 and h = 0.16. 32 cell columns
+    keep the singular window a = 0.75 L below h / max|f'| (max|f'| = 1)."""
+    prof = {"d": 2 * math.pi, "a": np.zeros(5), "b": -0.25 * np.array([0.0, 1.0, 1 / 2, 1 / 3, 1 / 4])}
+    if wood:
+        k = 6.0 / (1.0 - math.sin(math.radians(45.0)))
+        kw.setdefault("j", 8)
+        kw.setdefault("h", 0.16)
+    else:
+        k = 20.0
+        kw.setdefault("j", 0)
+    return make_params(prof, k, 45.0, DIRICHLET, N, n_per=n_per, nx=nx, **kw)
 
 
 def flat(N=64, d=1.0, k=2 * math.pi, theta_deg=20.0, bc=DIRICHLET, nx=8, **kw):

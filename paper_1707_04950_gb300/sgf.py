@@ -21,7 +21,8 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
-            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_field", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_field", "sgf_build_exact", "sgf_select_operator",
+            "sgf_exact_matrix", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve",
             "sgf_batch_shared_near"]
 
@@ -66,6 +67,9 @@ def load():
         "sgf_solve_rhs": [vp, vp, i, d, i, vp, ctypes.POINTER(i), dp],
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
         "sgf_field": [vp, vp, ctypes.c_long, dp, vp, i],
+        "sgf_build_exact": [vp],
+        "sgf_select_operator": [vp, i],
+        "sgf_exact_matrix": [vp, vp],
         "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
         "sgf_gradient": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
         "sgf_gradient_fd": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
@@ -190,6 +194,18 @@ def sgf_field(ctx, mu_ptr, xy, u_ptr, total=False):
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
     _check(ctx, load().sgf_field(ctx, ctypes.c_void_p(mu_ptr), len(xy), _dptr(xy), ctypes.c_void_p(u_ptr),
                                  1 if total else 0))
+
+
+def sgf_build_exact(ctx):
+    _check(ctx, load().sgf_build_exact(ctx))
+
+
+def sgf_select_operator(ctx, exact):
+    _check(ctx, load().sgf_select_operator(ctx, 1 if exact else 0))
+
+
+def sgf_exact_matrix(ctx, A_ptr):
+    _check(ctx, load().sgf_exact_matrix(ctx, ctypes.c_void_p(A_ptr)))
 
 
 def sgf_gradient(ctx, mu_ptr, n, M, tol=1e-12, maxit=2000, fd=False):
