@@ -220,6 +220,7 @@ def run_ours(args):
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
     tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
     field = run_field(dev, stream) if args.field and rank == 0 else None
+    exact = run_exact(dev, stream, flush, max(3, min(args.steps, 50))) if args.field and rank == 0 else None
     st32 = res[32]["stages_ms"]
     cufft = run_cufft_reference(res[32]["info"], st32["fft_x"] + st32["conv_y"] + st32["ifft_x"], dev, stream, flush,
                                 max(3, min(args.steps, 50))) if rank == 0 else None
@@ -275,6 +276,8 @@ def run_ours(args):
         line["autotune"] = tune
     if field is not None:
         line["field"] = field
+    if exact is not None:
+        line["exact_dense"] = exact
     if cufft is not None:
         line["cufft_reference"] = cufft
     if not args.no_cpu_baseline and ws >= 1:
@@ -383,6 +386,61 @@ def run_field(dev, stream, n_side=256):
     return {"workload": f"deep corrugation N=16384, {n_side}x{n_side} image over one period",
             "targets": len(xy), "targets_in_box": n_box, "targets_above_box": len(xy) - n_box,
             "s_per_call": t, "value": len(xy) / t, "unit": "targets/s", "precision": "fp64"}
+
+
+FP64_TFLOPS = 1.25  # GB300 FP64 (vector) rate, nominal
+
+
+def run_exact(dev, stream, flush, steps):
+    """The unaccelerated operator as a dense matrix on the 128-coefficient gradient workload
+    (N = 4096): assembly time, and one application (a bandwidth-bound GEMV over the 16 N^2-byte
+    matrix, larger than L2) against one FP64 application of the accelerated operator."""
+    import torch
+
+    from paper_1707_04950_gb300 import sgf
+
+    par = inputs.wl_harmonic_gradient()
+    N = par["N"]
+    op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sgf.sgf_build_exact(op.ctx)
+    t_build = time.perf_counter() - t0
+    x = torch.from_numpy(inputs.random_density(N, 5)).to(dev)
+    y = torch.empty_like(x)
+
+    def timed(exact):
+        sgf.sgf_select_operator(op.ctx, exact)
+        for _ in range(3):
+            sgf.sgf_apply(op.ctx, x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sgf.sgf_apply(op.ctx, x.data_ptr(), y.data_ptr())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    ms_dense = timed(True)
+    y_dense = y.clone()
+    ms_acc = timed(False)
+    rel = float(torch.linalg.norm(y - y_dense) / torch.linalg.norm(y_dense))
+    op.close()
+    hbm, kind = peaks()
+    gbs = (16.0 * N * N + 32.0 * N) / (ms_dense * 1e-3) / 1e9
+    # 8 flops (four FP64 FMAs) per 16-byte entry: above the FP64 ridge (1.25 TFLOP/s nominal for
+    # GB300, against the measured HBM bandwidth), so the FP64 pipes bound the GEMV
+    tflops = 8.0 * N * N / (ms_dense * 1e-3) / 1e12
+    return {"workload": "harmonic64_d20_n4096_theta20_dirichlet", "N": N, "assembly_s": t_build,
+            "dense_apply_ms": ms_dense, "accelerated_fp64_apply_ms": ms_acc,
+            "dense_gemv": {"bound": "alu", "achieved": tflops, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                           "frac": tflops / FP64_TFLOPS, "peak_kind": "nominal FP64 of GB300",
+                           "hbm_gbs": gbs, "hbm_frac": gbs / hbm, "hbm_peak_kind": kind,
+                           "algorithmic_flops_per_launch": 8.0 * N * N,
+                           "algorithmic_bytes_per_launch": 16.0 * N * N + 32.0 * N},
+            "accelerated_vs_dense_rel_diff": rel}
 
 
 def run_autotune(dev, stream):
@@ -538,7 +596,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
-    ap.add_argument("--field", type=int, default=1, help="1: time the scattered-field image block")
+    ap.add_argument("--field", type=int, default=1,
+                    help="1: time the scattered-field image and the dense unaccelerated operator blocks")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -15,7 +15,9 @@
 //   k_exact_entries  warp per entry: lanes share the spectral terms or the lattice periods of G~,
 //                    lanes 0-2 the windowed p = -1, 0, 1 subtraction, lane 3 the singular band,
 //                    lane 4 the modes and the identity
-//   k_exact_gemv     y = A x, warp per row (each row one contiguous 16 N-byte stream)
+//   k_exact_gemv     y = A x, warp per row (each row one contiguous 16 N-byte stream); four FP64 FMAs
+//                    per 16-byte entry put it above GB300's FP64 ridge (1.25 TFLOP/s against
+//                    ~6.7 TB/s): it is bound by the FP64 pipes, not by HBM
 //   k_exact_gemv_adj y = A^H x, a thread per column over a chunk of rows (coalesced across the
 //                    warp), chunks combined with atomics
 #include "sgf_internal.h"
@@ -146,7 +148,7 @@ __global__ void k_exact_gemv(long N, const zd* __restrict__ A, const zd* __restr
       }
     }
 #pragma unroll
-    for (int u = 0; u < GEMV_U; ++u) acc[u] += av[u] * xv[u];
+    for (int u = 0; u < GEMV_U; ++u) acc[u] = fma_c(av[u], xv[u], acc[u]);
   }
   zd s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   s = warp_sum(s);
@@ -159,7 +161,11 @@ __global__ void k_exact_gemv_adj(long N, long rows_per, const zd* __restrict__ A
   if (col >= N) return;
   const long r0 = (long)blockIdx.y * rows_per, r1 = min(N, r0 + rows_per);
   zd acc(0, 0);
-  for (long r = r0; r < r1; ++r) acc += mulc(x[r], A[r * N + col]);  // conj(A[r][col]) x[r]
+  for (long r = r0; r < r1; ++r) {  // acc += conj(A[r][col]) x[r]
+    const zd av = A[r * N + col], xv = x[r];
+    acc.re = fma(av.re, xv.re, fma(av.im, xv.im, acc.re));
+    acc.im = fma(av.re, xv.im, fma(-av.im, xv.re, acc.im));
+  }
   atomicAdd(&y[col].re, acc.re);
   atomicAdd(&y[col].im, acc.im);
 }
