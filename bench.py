@@ -221,6 +221,7 @@ def run_ours(args):
     tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
     field = run_field(dev, stream) if args.field and rank == 0 else None
     exact = run_exact(dev, stream, flush, max(3, min(args.steps, 50))) if args.field and rank == 0 else None
+    tables = run_tables(dev, stream) if args.tables and rank == 0 else None
     st32 = res[32]["stages_ms"]
     cufft = run_cufft_reference(res[32]["info"], st32["fft_x"] + st32["conv_y"] + st32["ifft_x"], dev, stream, flush,
                                 max(3, min(args.steps, 50))) if rank == 0 else None
@@ -278,6 +279,8 @@ def run_ours(args):
         line["field"] = field
     if exact is not None:
         line["exact_dense"] = exact
+    if tables is not None:
+        line["sinusoid_tables"] = tables
     if cufft is not None:
         line["cufft_reference"] = cufft
     if not args.no_cpu_baseline and ws >= 1:
@@ -386,6 +389,45 @@ def run_field(dev, stream, n_side=256):
     return {"workload": f"deep corrugation N=16384, {n_side}x{n_side} image over one period",
             "targets": len(xy), "targets_in_box": n_box, "targets_above_box": len(xy) - n_box,
             "s_per_call": t, "value": len(xy) / t, "unit": "targets/s", "precision": "fp64"}
+
+
+def run_tables(dev, stream):
+    """The sinusoid tables of Section 6.2 (Littrow mount, H = d/4, d/2, d; non-Wood j = 0 and Wood
+    j = 8 rows) with the dense unaccelerated operator at the paper's N and twice its n_per: energy
+    error, GMRES iterations and time per application beside the paper's single-core values (read
+    from the golden fixture the tests use)."""
+    import torch
+
+    from paper_1707_04950_gb300 import sgf
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "sinusoid_littrow_energy_error.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    out = []
+    for r in rows:
+        Hd, dl, N, hl, n_per = float(r[0]), float(r[2]), int(r[3]), float(r[4]), int(r[5])
+        par = inputs.wl_littrow(Hd, dl, N, hl, 2 * n_per)
+        ctx = sgf.sgf_create(dev.index, stream.cuda_stream)
+        sgf.sgf_set_profile_fourier(ctx, par["d"], par["a"], par["b"])
+        sgf.sgf_set_wave(ctx, par["k"], par["theta"], par["bc"])
+        sgf.sgf_set_params(ctx, sgf.params_from(par, 64))
+        t0 = time.perf_counter()
+        sgf.sgf_build_exact(ctx)
+        t_init = time.perf_counter() - t0
+        sgf.sgf_select_operator(ctx, 1)
+        mu = torch.zeros(N, dtype=torch.complex128, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, its, rr = sgf.sgf_solve(ctx, 1e-12, 2000, mu.data_ptr())
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        _, _, eps = sgf.sgf_rayleigh(ctx, mu.data_ptr(), -60, 60)
+        sgf.sgf_destroy(ctx)
+        out.append({"H_over_d": Hd, "d_over_lambda": dl, "N": N, "j": 8 if hl > 0 else 0, "n_per": 2 * n_per,
+                    "eps": abs(eps), "paper_eps": float(r[8]), "iters": its, "paper_iters": int(r[7]),
+                    "relres": rr, "status": st, "init_s": t_init, "s_per_iter": t_solve / max(1, its),
+                    "paper_s_per_iter": float(r[6])})
+    return out
 
 
 FP64_TFLOPS = 1.25  # GB300 FP64 (vector) rate, nominal
@@ -596,6 +638,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
+    ap.add_argument("--tables", type=int, default=0,
+                    help="1: the sinusoid tables of Section 6.2 with the dense operator (about a minute)")
     ap.add_argument("--field", type=int, default=1,
                     help="1: time the scattered-field image and the dense unaccelerated operator blocks")
     args = ap.parse_args()

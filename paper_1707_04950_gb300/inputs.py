@@ -193,6 +193,29 @@ def wl_composite(N, n_per, wood=False, nx=32, **kw):
     return make_params(prof, k, 45.0, DIRICHLET, N, n_per=n_per, nx=nx, **kw)
 
 
+def wl_littrow(H_over_d, d_over_lambda, N, h_over_lambda, n_per, **kw):
+    """Sinusoid f = (H/2) sin(2 pi x / d) in the Littrow mount of order -1 (sin theta = 1/3),
+    Dirichlet, d = 2 pi so that k = d / lambda (the sinusoid tables of Section 6.2): j = 0 when
+    h_over_lambda is 0 (non-Wood rows), else j = 8 with h = h_over_lambda lambda. For the dense
+    operator: singular window a = min(lambda/2, 0.4 d), below 0.9 h / max|f'| when shifted."""
+    d = 2 * math.pi
+    k = float(d_over_lambda)
+    lam = d / k
+    H = H_over_d * d
+    prof = {"d": d, "a": np.zeros(2), "b": np.array([0.0, H / 2])}
+    shifted = h_over_lambda > 0
+    a = min(0.5 * lam, 0.4 * d)
+    if shifted:
+        a = min(a, 0.9 * h_over_lambda * lam / (math.pi * H / d))
+    par = make_params(prof, k, math.degrees(math.asin(1.0 / 3.0)), DIRICHLET, N, j=8 if shifted else 0,
+                      h=h_over_lambda * lam if shifted else 0.5, n_per=n_per, nx=4, hmin=-H, ny=8, **kw)
+    dx = d / N
+    par["Ma"] = max(2, int(a / dx))
+    par["a_s"] = par["Ma"] * dx
+    par["gamma"] = 0.5 * par["a_s"]
+    return par
+
+
 def flat(N=64, d=1.0, k=2 * math.pi, theta_deg=20.0, bc=DIRICHLET, nx=8, **kw):
     prof = {"d": float(d), "a": np.zeros(1), "b": np.zeros(1)}
     kw.setdefault("hmin", -0.5 * d / nx)
