@@ -183,8 +183,10 @@ __global__ void k_field_ray_coef(FieldArgs a, long N, const double* __restrict__
   }
 }
 
-__global__ void k_field_ray_eval(FieldArgs a, long n_r, int nmod, const double* __restrict__ mp, double yR,
-                                 const zd* __restrict__ Bp, const double* __restrict__ t_xr,
+// Each target sums only the modes its own height needs: |n - n_0| <= n_t with the same e^{-37}
+// criterion as the call's range (n_c, set by the lowest target), applied to this target's gap.
+__global__ void k_field_ray_eval(FieldArgs a, long n_r, int nmod, int n_c, double fmax, const double* __restrict__ mp,
+                                 double yR, const zd* __restrict__ Bp, const double* __restrict__ t_xr,
                                  const double* __restrict__ t_y, const double* __restrict__ t_w,
                                  const double* __restrict__ t_x0, const long* __restrict__ t_out, int total,
                                  zd* __restrict__ out) {
@@ -192,8 +194,10 @@ __global__ void k_field_ray_eval(FieldArgs a, long n_r, int nmod, const double* 
   const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (wid >= n_r) return;  // uniform across the warp
   const double xr = t_xr[wid], y = t_y[wid];
+  const double nt = ceil((37.0 / (y - fmax) + a.k + SGF_PI / a.d) * a.d / (2 * SGF_PI)) + 1;
+  const int n_t = nt < (double)n_c ? (int)nt : n_c;
   zd acc(0, 0);
-  for (int n = lane; n < nmod; n += 32) {
+  for (int n = n_c - n_t + lane; n <= n_c + n_t && n < nmod; n += 32) {
     const zd bn(mp[6 * n + 1], mp[6 * n + 2]);
     acc += Bp[n] * cexpz(zd(0, mp[6 * n] * xr) + zd(0, 1) * ((y - yR) * bn));
   }
@@ -421,8 +425,8 @@ extern "C" sgf_status sgf_field(sgf_ctx* ctx, const void* mu_dev, long n_t, cons
     FCU(S.alloc(&d_Bp, nmod));
     k_field_ray_coef<<<nmod, 256, 0, c->stream>>>(a, c->N, d_mp, yR, c->d_x, c->d_f, c->d_f1, mu, d_Bp);
     FCU(cudaGetLastError());
-    k_field_ray_eval<<<(unsigned)((n_r + 7) / 8), 256, 0, c->stream>>>(a, n_r, nmod, d_mp, yR, d_Bp, d_r_xr, d_r_y,
-                                                                       d_r_w, d_r_x0, d_r_out, total, u);
+    k_field_ray_eval<<<(unsigned)((n_r + 7) / 8), 256, 0, c->stream>>>(a, n_r, nmod, n_c, fmax, d_mp, yR, d_Bp, d_r_xr,
+                                                                       d_r_y, d_r_w, d_r_x0, d_r_out, total, u);
     FCU(cudaGetLastError());
   }
   int herr = 0;
