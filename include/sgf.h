@@ -117,7 +117,8 @@ sgf_status sgf_solve_rhs(sgf_ctx* ctx, const void* rhs_dev, int transpose_conj, 
  * owned by the context (16 N^2 bytes; 8 <= N <= 32768, 2 <= Ma < N/2). It needs the profile, the
  * wave and the parameters (N, j, h, n_per, c_win, Ma, eta, delta_min, spec_exp; the accelerator's
  * cell parameters are not used) and works with or without sgf_build_operator; a later
- * sgf_build_operator discards it. Errors: SGF_ESTATE before the setters, SGF_EINVAL for sizes out
+ * sgf_build_operator discards it. Assembly evaluates G~ once per entry (a warp per entry, FP64):
+ * about 5 s at N = 4096 on one GB300, growing as N^2. Errors: SGF_ESTATE before the setters, SGF_EINVAL for sizes out
  * of range, SGF_EWINDOW (j > 0 and h <= a max|f'|). Synchronises. */
 sgf_status sgf_build_exact(sgf_ctx* ctx);
 
