@@ -322,8 +322,11 @@ extern "C" sgf_status sgf_field(sgf_ctx* ctx, const void* mu_dev, long n_t, cons
     // local cells of every target cell (the same reach as the nodes' local sets) and their nodes
     std::vector<int> occ_id((size_t)ncell, -1);
     for (int q = 0; q < c->n_occ; ++q) occ_id[(size_t)c->occ_cy[q] * nx + c->occ_cx[q]] = q;
-    std::vector<std::set<int>> rowsS(ny);
-    for (int cy = 0; cy < ny; ++cy) rowsS[cy] = rows_of_Sj(cy, P.j, P.h, L);
+    // for each target row, the source rows whose local reach contains it (ascending)
+    std::vector<std::vector<int>> src_rows(ny);
+    for (int cyr = 0; cyr < ny; ++cyr)
+      for (int cy : rows_of_Sj(cyr, P.j, P.h, L))
+        if (cy >= 0 && cy < ny) src_rows[cy].push_back(cyr);
     std::vector<int> tc_bstart(n_tc + 1, 0), tc_cstart(n_tc + 1, 0), b_r, b_wrap, b_dcx, b_dcy, col_node;
     std::vector<signed char> col_wrap;
     int dmin = 1 << 30, dmax = -(1 << 30);
@@ -334,16 +337,15 @@ extern "C" sgf_status sgf_field(sgf_ctx* ctx, const void* mu_dev, long n_t, cons
         const int cxr = tc_cx[q] + dcx;
         const int ref = ((cxr % nx) + nx) % nx;
         const int wrap = (cxr - ref) / nx;
-        for (int cyr = 0; cyr < ny; ++cyr) {
+        for (int cyr : src_rows[tc_cy[q]]) {
           const int r = occ_id[(size_t)cyr * nx + ref];
-          if (r < 0 || !rowsS[cyr].count(tc_cy[q])) continue;
+          if (r < 0) continue;
           b_r.push_back(r); b_wrap.push_back(wrap); b_dcx.push_back(dcx); b_dcy.push_back(cyr - tc_cy[q]);
           dmin = std::min(dmin, cyr - tc_cy[q]);
           dmax = std::max(dmax, cyr - tc_cy[q]);
-          for (int l = c->cell_start[r]; l < c->cell_start[r + 1]; ++l) {
-            col_node.push_back(c->node_idx[l]);
-            col_wrap.push_back((signed char)wrap);
-          }
+          const int l0 = c->cell_start[r], l1 = c->cell_start[r + 1];
+          col_node.insert(col_node.end(), c->node_idx.begin() + l0, c->node_idx.begin() + l1);
+          col_wrap.insert(col_wrap.end(), (size_t)(l1 - l0), (signed char)wrap);
         }
       }
     }
