@@ -15,6 +15,7 @@ Modules
           and by its Rayleigh form above every node; gradient: derivatives of e_n by definition
 
 Parity status: every function is pinned by tests/test_oracle_*.py (closed forms, identities,
-brute force, energy balance) except the exact values of B_n for curved surfaces, which the paper
+brute force, energy balance, and the energy-balance errors the paper prints for its composite and
+sinusoid tables, tests/golden/) except the exact values of B_n for curved surfaces, which the paper
 does not print ("parity unpinned" for those values; only energy balance and invariances fix them).
 """
