@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libsgf.so")
-SOURCES = ["sgf_kernels.cu", "sgf_capi.cu", "sgf_noalloc.cu", "sgf_batch.cu", "sgf_field.cu", "sgf_exact.cu"]
+SOURCES = ["sgf_kernels.cu", "sgf_capi.cu", "sgf_noalloc.cu", "sgf_batch.cu", "sgf_field.cu", "sgf_exact.cu", "sgf_suggest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

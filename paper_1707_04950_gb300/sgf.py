@@ -22,7 +22,7 @@ STATUS = {0: "SGF_OK", 1: "SGF_EINVAL", 2: "SGF_ERESONANT_CELL", 3: "SGF_EPOLE_O
 EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_fourier", "sgf_set_wave",
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
             "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_field", "sgf_build_exact", "sgf_select_operator",
-            "sgf_exact_matrix", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_exact_matrix", "sgf_suggest_params", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve",
             "sgf_batch_shared_near"]
 
@@ -68,6 +68,7 @@ def load():
         "sgf_rayleigh": [vp, vp, i, i, dp, dp, dp],
         "sgf_field": [vp, vp, ctypes.c_long, dp, vp, i],
         "sgf_build_exact": [vp],
+        "sgf_suggest_params": [d, i, dp, dp, d, d, i, d, i, ctypes.POINTER(sgf_params)],
         "sgf_select_operator": [vp, i],
         "sgf_exact_matrix": [vp, vp],
         "sgf_rayleigh_noalloc": [vp, vp, i, i, dp, dp, dp],
@@ -194,6 +195,19 @@ def sgf_field(ctx, mu_ptr, xy, u_ptr, total=False):
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
     _check(ctx, load().sgf_field(ctx, ctypes.c_void_p(mu_ptr), len(xy), _dptr(xy), ctypes.c_void_p(u_ptr),
                                  1 if total else 0))
+
+
+def sgf_suggest_params(d, a, b, k, theta, bc, tol, precision=64):
+    """Suggested sgf_params for a profile (cosine/sine coefficients a, b), a wave and a target
+    accuracy (host only). Returns the ctypes record."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    p = sgf_params()
+    st = load().sgf_suggest_params(float(d), len(a) - 1, _dptr(a), _dptr(b), float(k), float(theta), int(bc),
+                                   float(tol), int(precision), ctypes.byref(p))
+    if st != 0:
+        raise SgfError(st, "sgf_suggest_params: argument out of range")
+    return p
 
 
 def sgf_build_exact(ctx):
