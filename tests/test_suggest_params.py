@@ -18,6 +18,7 @@ from paper_1707_04950_gb300 import sgf
 def _library():
     _build.build()  # host-only entry point: the library loads without a GPU
 
+
 THETA_LITTROW = math.degrees(math.asin(1 / 3))
 COMPOSITE = {"d": 2 * math.pi, "a": np.zeros(5), "b": -0.25 * np.array([0.0, 1.0, 1 / 2, 1 / 3, 1 / 4])}
 
