@@ -62,8 +62,9 @@ typedef struct {
  * sgf_set_wave) and a target accuracy tol in [1e-14, 1e-2], following the parameter guidance of
  * Section 6.1 ("Computing costs"): cells of side L <= 0.45 lambda (n_x a power of two, the cell not
  * resonant); N from 6 log10(1/tol) points per wavelength of arc length (at least 16), a multiple
- * of n_x; the singular window a = 0.95 L; the cell box around the profile; j = 8 shifts near a Wood anomaly (some |beta_n| < k/10),
- * none otherwise; h/lambda from 1/3 (shallow) to 1 (deep: 1/3 + 0.06 H/lambda), clear of the
+ * of n_x; the singular window a = 0.95 L; the cell box around the profile; j = 8 shifts near a
+ * Wood anomaly (some |beta_n| < k/10), none otherwise; h/lambda from 1/3 (shallow) to 1 (deep:
+ * 1/3 + 0.06 H/lambda), clear of the
  * singular window (h > 1.2 a max|f'|) and off the grid lags; n_per doubled from 8 until the
  * windowed lattice sum of G_j next to the shifted images changes by less than tol/10 (at most
  * 20000); the remaining fields at the library's defaults. Host only (no GPU, no context).
