@@ -64,8 +64,8 @@ typedef struct {
  * resonant); N from 6 log10(1/tol) points per wavelength of arc length (at least 16), a multiple
  * of n_x; the singular window a = 0.95 L; the cell box around the profile; j = 8 shifts near a
  * Wood anomaly (some |beta_n| < k/10), none otherwise; h/lambda from 1/3 (shallow) to 1 (deep:
- * 1/3 + 0.06 H/lambda), clear of the
- * singular window (h > 1.2 a max|f'|) and off the grid lags; n_per doubled from 8 until the
+ * 1/3 + 0.06 H/lambda), clear of the singular window (h > 1.2 a max|f'|) and off the grid lags;
+ * n_per doubled from 8 until the
  * windowed lattice sum of G_j next to the shifted images changes by less than tol/10 (at most
  * 20000); the remaining fields at the library's defaults. Host only (no GPU, no context).
  * SGF_EINVAL for arguments out of range. */
