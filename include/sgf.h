@@ -67,8 +67,10 @@ typedef struct {
  * 1/3 + 0.06 H/lambda), clear of the singular window (h > 1.2 a max|f'|) and off the grid lags;
  * n_per doubled from 8 until the
  * windowed lattice sum of G_j next to the shifted images changes by less than tol/10 (at most
- * 20000); the remaining fields at the library's defaults. Host only (no GPU, no context).
- * SGF_EINVAL for arguments out of range. */
+ * 16384); the remaining fields at the library's defaults. Host only (no GPU, no context).
+ * SGF_EINVAL for arguments out of range. SGF_ENOCONV when the lattice-sum check did not reach
+ * tol/10 by n_per = 16384: *out is still filled (with n_per = 16384), but that accuracy is not
+ * reached by the windowed sums. */
 sgf_status sgf_suggest_params(double d, int M, const double* a, const double* b, double k, double theta_rad, int bc,
                               double tol, int precision, sgf_params* out);
 
@@ -172,19 +174,21 @@ sgf_status sgf_field(sgf_ctx* ctx, const void* mu_dev, long n_targets, const dou
 sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                         double* energy_err);
 
-/* Same result as sgf_rayleigh, for callers that cannot allocate memory during the call: code running
- * while a stream is being captured into a CUDA graph (cudaMalloc cannot be captured), processes
- * working inside a device-memory budget fixed up front, real-time loops that must stay out of the
- * allocator. (The paper has no counterpart; this is a property of the library, not of the method.)
- * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch (per-mode data and the
- * B_n before they are copied back) lives in a static device array of 1024 modes x 64 bytes that
- * every GPU loading the library holds until the process exits. At most 1024 modes
- * (n_hi - n_lo + 1) per call; larger ranges return SGF_EINVAL with a message. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with that device current), so
- * make that first call before any stream capture starts. All calls share the one array, which keeps
- * the last call's contents; every entry a call reads is written by that call first. Calls whose GPU
- * work overlaps (other streams, other host threads on the same device) race on the array: serialise
- * them. Synchronises the context stream. */
+/* Same result as sgf_rayleigh, for callers that cannot allocate memory during the call: processes
+ * working inside a device-memory budget fixed up front, and real-time loops that must stay out of
+ * the allocator (cudaMalloc and cudaFree can synchronise the device and take unbounded time). (The
+ * paper has no counterpart; this is a property of the library, not of the method.)
+ * It calls no cudaMalloc, cudaFree or other allocating routine, on the device or the host: its
+ * scratch (per-mode data and the B_n before they are copied back) lives in a static device array of
+ * 1024 modes x 64 bytes that every GPU loading the library holds until the process exits. At most
+ * 1024 modes (n_hi - n_lo + 1) per call; larger ranges return SGF_EINVAL with a message. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current). All calls share the one array, which keeps the last call's contents; every entry a call
+ * reads is written by that call first. Calls whose GPU work overlaps (other streams, other host
+ * threads on the same device) race on the array: serialise them. The call copies through fixed host
+ * stack buffers and synchronises the context stream after each copy, so it must not be made on a
+ * stream that is being captured into a graph. Accepts the same context states as sgf_rayleigh (a
+ * built operator, or the geometry set by sgf_build_exact); SGF_ESTATE otherwise. */
 sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B, double* eff,
                                 double* energy_err);
 

@@ -206,27 +206,6 @@ std::set<int> rows_of_Sj(int cy_r, int j, double h, double L) {
   return rows;
 }
 
-// (1 - e^{i beta h})^j / beta; for |beta h| < 1 in the form (-2i)^j e^{i j beta h/2}
-// sin^{j-1}(beta h/2) (h/2) sinc(beta h/2) that is exact at beta = 0 (eq. betan_taylor). Beyond, the
-// quotient is well conditioned and the rewrite's factors would overflow for evanescent modes.
-static cd Qj_host(cd beta, double h, int j) {
-  if (j == 0) return 1.0 / beta;
-  if (std::abs(beta * h) >= 1.0) {
-    cd q = 1.0 - std::exp(cd(0, 1) * (beta * h)), acc = 1.0;
-    for (int m = 0; m < j; ++m) acc *= q;
-    return acc / beta;
-  }
-  cd half = 0.5 * h * beta;
-  cd sn = std::sin(half);
-  cd sinc = std::abs(half) < 1e-3 ? 1.0 - half * half / 6.0 + std::pow(half, 4) / 120.0 : std::sin(half) / half;
-  cd acc = 0.5 * h * sinc;
-  for (int m = 1; m < j; ++m) acc *= sn;
-  return std::pow(cd(0, -2), j) * std::exp(cd(0, 1) * (double)j * half) * acc;
-}
-static cd beta_host(double k, double an) {
-  double q = k * k - an * an;
-  return q >= 0 ? cd(std::sqrt(q), 0) : cd(0, std::sqrt(-q));
-}
 // U^eta (eq. M_eta) restricted to |beta_n| <= k.
 static std::vector<int> ueta_set(sgf_ctx* c) {
   std::vector<int> out;
@@ -347,7 +326,8 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(cudaStreamSynchronize(c->stream));
   double maxslope = 0;
   for (int i = 0; i < c->N; ++i) maxslope = std::max(maxslope, fabs(c->hf1[i]));
-  if (!(P.h > c->a_s * maxslope))
+  // shifted poles (j > 0) must stay outside the singular window
+  if (P.j > 0 && !(P.h > c->a_s * maxslope))
     return set_err(ctx, SGF_EWINDOW, "shift h = %g must exceed a max|f'| = %g", P.h, c->a_s * maxslope);
 
   // ---------------- binning (Remark cell_def: half-open cells)

@@ -4,6 +4,8 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <string>
+#include <complex>
+#include <cmath>
 #include <set>
 #include <vector>
 #include <algorithm>
@@ -221,3 +223,30 @@ cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* p
                         cudaStream_t s);
 cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s);
 cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s);  // y = a x + b y
+
+// Host mode helpers shared by the Rayleigh entry points, the mode completion and the gradient.
+// beta_n = sqrt(k^2 - alpha_n^2) with the branch i sqrt(alpha_n^2 - k^2) for evanescent modes
+// (Section 2, eq. alpha_beta_def).
+inline std::complex<double> beta_host(double k, double an) {
+  double q = k * k - an * an;
+  return q >= 0 ? std::complex<double>(std::sqrt(q), 0) : std::complex<double>(0, std::sqrt(-q));
+}
+// Q_j = (1 - e^{i beta h})^j / beta; for |beta h| < 1 in the form (-2i)^j e^{i j beta h/2}
+// sin^{j-1}(beta h/2) (h/2) sinc(beta h/2) that is exact at beta = 0 (eq. betan_taylor). Beyond, the
+// quotient is well conditioned, while the rewrite's factors (growing like sinh(|beta| h/2) for
+// evanescent modes) would overflow before the decaying e^{i j beta h/2} cancels them.
+inline std::complex<double> Qj_host(std::complex<double> beta, double h, int j) {
+  typedef std::complex<double> c;
+  if (j == 0) return 1.0 / beta;
+  if (std::abs(beta * h) >= 1.0) {
+    c q = 1.0 - std::exp(c(0, 1) * (beta * h)), acc = 1.0;
+    for (int m = 0; m < j; ++m) acc *= q;
+    return acc / beta;
+  }
+  c half = 0.5 * h * beta;
+  c sn = std::sin(half);
+  c sinc = std::abs(half) < 1e-3 ? 1.0 - half * half / 6.0 + std::pow(half, 4) / 120.0 : std::sin(half) / half;
+  c acc = 0.5 * h * sinc;
+  for (int m = 1; m < j; ++m) acc *= sn;
+  return std::pow(c(0, -2), j) * std::exp(c(0, 1) * (double)j * half) * acc;
+}

@@ -1,11 +1,13 @@
 // Rayleigh extraction without any device or host heap allocation.
 //
 // sgf_rayleigh allocates a small per-call table and output buffer with cudaMalloc. Some callers
-// cannot allocate while they run: code executing while a CUDA stream is being captured into a
-// graph (cudaMalloc is not a capturable operation), processes that run under a fixed device-memory
-// budget reserved up front, and real-time loops that must not enter the allocator. This file gives
-// them sgf_rayleigh_noalloc: the same reduction, with its scratch in a file-scope __device__ array
-// of fixed size that every GPU loading the library keeps until the process exits.
+// cannot allocate while they run: processes that run under a fixed device-memory budget reserved up
+// front, and real-time loops that must not enter the allocator (cudaMalloc and cudaFree may
+// synchronise the device and take unbounded time). This file gives them sgf_rayleigh_noalloc: the
+// same reduction, with its scratch in a file-scope __device__ array of fixed size that every GPU
+// loading the library keeps until the process exits. The call synchronises its stream (it copies
+// the mode data in and B_n out through fixed stack buffers), so it is not for a stream that is
+// being captured into a graph.
 #include <mutex>
 
 #include "sgf_internal.h"
@@ -41,49 +43,12 @@ sgf_status scratch_address(sgf_ctx* ctx, double** out) {
   return SGF_OK;
 }
 
-// (1 - e^{i beta h})^j / beta in the product form that stays finite at beta = 0.
-void qj(double br, double bi, double h, int j, double* qr, double* qi) {
-  // complex helpers on plain doubles (no allocation)
-  auto mul = [](double ar, double ai, double cr, double ci, double* rr, double* ri) {
-    *rr = ar * cr - ai * ci;
-    *ri = ar * ci + ai * cr;
-  };
-  if (j == 0) {
-    double s = br * br + bi * bi;
-    *qr = br / s;
-    *qi = -bi / s;
-    return;
-  }
-  double hr = 0.5 * h * br, hi = 0.5 * h * bi;  // half = beta h / 2
-  double snr = sin(hr) * cosh(hi), sni = cos(hr) * sinh(hi);  // sin(half)
-  double sincr, scinci;
-  if (hr * hr + hi * hi < 1e-6) {  // 1 - z^2/6 + z^4/120
-    double z2r = hr * hr - hi * hi, z2i = 2 * hr * hi;
-    double z4r, z4i;
-    mul(z2r, z2i, z2r, z2i, &z4r, &z4i);
-    sincr = 1 - z2r / 6 + z4r / 120;
-    scinci = -z2i / 6 + z4i / 120;
-  } else {
-    double s = hr * hr + hi * hi;
-    sincr = (snr * hr + sni * hi) / s;
-    scinci = (sni * hr - snr * hi) / s;
-  }
-  double ar = 0.5 * h * sincr, ai = 0.5 * h * scinci;
-  for (int m = 1; m < j; ++m) mul(ar, ai, snr, sni, &ar, &ai);
-  double pr = 1, pi = 0;  // (-2i)^j
-  for (int m = 0; m < j; ++m) mul(pr, pi, 0, -2, &pr, &pi);
-  // e^{i j half} = e^{-j hi} (cos(j hr) + i sin(j hr))
-  double em = exp(-j * hi);
-  double er = em * cos(j * hr), ei = em * sin(j * hr);
-  mul(pr, pi, er, ei, &pr, &pi);
-  mul(pr, pi, ar, ai, qr, qi);
-}
 }  // namespace
 
 extern "C" sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int n_lo, int n_hi, double* B,
                                            double* eff, double* energy_err) {
   if (!ctx) return SGF_EINVAL;
-  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (!ctx->built && !ctx->geom) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (!mu_dev || n_hi < n_lo) return set_err(ctx, SGF_EINVAL, "bad Rayleigh arguments");
   const int nmod = n_hi - n_lo + 1;
   if (nmod > SGF_NOALLOC_MAX_MODES)
@@ -106,14 +71,12 @@ extern "C" sgf_status sgf_rayleigh_noalloc(sgf_ctx* ctx, const void* mu_dev, int
     for (int u = 0; u < cnt; ++u) {
       int n = n_lo + t0 + u;
       double an = ctx->alpha + 2 * SGF_PI * n / d;
-      double q = k * k - an * an;
-      double br = q >= 0 ? sqrt(q) : 0.0, bi = q >= 0 ? 0.0 : sqrt(-q);
-      double qr, qi;
-      qj(br, bi, h, j, &qr, &qi);
-      double babs = sqrt(br * br + bi * bi);
-      bool in_ueta = sqrt(qr * qr + qi * qi) < ctx->prm.eta && babs <= k;
+      // the same host helpers as sgf_rayleigh, so both entry points take identical mode data
+      std::complex<double> bn = beta_host(k, an);
+      std::complex<double> Q = Qj_host(bn, h, j);
+      bool in_ueta = std::abs(Q) < ctx->prm.eta && std::abs(bn) <= k;
       double* r = chunk + 6 * u;
-      r[0] = an; r[1] = br; r[2] = bi; r[3] = qr; r[4] = qi; r[5] = in_ueta ? 1.0 : 0.0;
+      r[0] = an; r[1] = bn.real(); r[2] = bn.imag(); r[3] = Q.real(); r[4] = Q.imag(); r[5] = in_ueta ? 1.0 : 0.0;
     }
     e = cudaMemcpyAsync(d_mp + 6 * t0, chunk, sizeof(double) * 6 * cnt, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "copy of mode data: %s", cudaGetErrorString(e));

@@ -127,8 +127,10 @@ extern "C" sgf_status sgf_suggest_params(double d, int M, const double* a, const
   const int jl = P.j;
   const double Ys[2] = {jl > 0 ? -P.h + 0.5 * P.delta_min : 0.5 * P.delta_min, 0.25 * P.delta_min};
   const double Xs[2] = {0.23 * d, 0.41 * d};
+  // the largest n_per tried is 16384 (its check sums 32768 periods)
+  bool converged = false;
   int n_per = 8;
-  for (; n_per < 20000; n_per *= 2) {
+  for (; n_per <= 16384; n_per *= 2) {
     double worst = 0;
     for (double Y : Ys)
       for (double X : Xs) {
@@ -136,9 +138,13 @@ extern "C" sgf_status sgf_suggest_params(double d, int M, const double* a, const
         const cdh s2 = lattice_sum(k, alpha, d, jl, P.h, X, Y, 2.0 * n_per * d, P.c_win);
         worst = std::max(worst, std::abs(s2 - s1) / std::max(1e-300, std::abs(s2)));
       }
-    if (worst < 0.1 * tol) break;
+    if (worst < 0.1 * tol) {
+      converged = true;
+      break;
+    }
   }
-  P.n_per = std::min(n_per, 20000);
+  P.n_per = std::min(n_per, 16384);
   *out = P;
-  return SGF_OK;
+  // the record is filled either way; SGF_ENOCONV says the lattice-sum check did not reach tol / 10
+  return converged ? SGF_OK : SGF_ENOCONV;
 }

@@ -205,6 +205,10 @@ def sgf_suggest_params(d, a, b, k, theta, bc, tol, precision=64):
     p = sgf_params()
     st = load().sgf_suggest_params(float(d), len(a) - 1, _dptr(a), _dptr(b), float(k), float(theta), int(bc),
                                    float(tol), int(precision), ctypes.byref(p))
+    if st == 5:  # SGF_ENOCONV: the record is filled; the error carries it
+        e = SgfError(st, f"sgf_suggest_params: the windowed lattice sums do not reach {tol:g} by n_per = 16384")
+        e.params = p
+        raise e
     if st != 0:
         raise SgfError(st, "sgf_suggest_params: argument out of range")
     return p
