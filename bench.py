@@ -1,6 +1,10 @@
-"""Benchmark: FFT-accelerated shifted-Green matvecs/s at N = 16384 (deep corrugation, TM/Neumann,
-period 10 wavelengths, depth/period 2, 128 x 257 cells), mixed precision (FP32 complex
-projection/FFT/interpolation, FP64 near field) beside the FP64 path.
+"""Benchmark: FFT-accelerated matvecs/s at N = 16384 on the deep corrugation (TM/Neumann, period 10
+wavelengths, depth/period 2, 128 x 257 cells), mixed precision (FP32 complex projection/FFT/
+interpolation, float-float near field) beside the FP64 path.
+
+The workload uses the periodic Green function without shifts (j = 0, n_per = 2048), as the paper
+does for its deep non-Wood gratings (Section 6, Table deep_gratings); the same geometry with the
+shifted kernel (j = 8) is timed beside it, and the headline FP64 and mixed solves are timed too.
 
 One step = one application of the accelerated operator (Algorithm 3) to one density vector,
 inputs resident on the device. L2 is flushed (256 MiB write) before every timed step; each step is
@@ -9,8 +13,8 @@ timed with CUDA events on the stream the library launches on, the flush outside 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank builds its own replica (independent problems, no collective) and the
-slowest rank's time is reported. `--impl reference` times the CPU oracle (the exact operator rows,
-matrix-free) on a bounded row sample of the same workload.
+slowest rank's time is reported. `--impl reference` times the CPU oracle: the exact operator,
+assembled as dense rows of the same workload, applied by ZGEMV on all host cores.
 """
 from __future__ import annotations
 
@@ -64,7 +68,9 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU is under the benchmark's
+    load. nvidia-smi writes its samples straight to a file (-f), so nothing is lost in a pipe buffer
+    when it is stopped; start() returns once the first sample is on disk."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,30 +82,41 @@ class Clocks:
         # the raw samples go to SGF_CLOCKS_DIR (default: the system's temporary directory); the JSON
         # line carries their summary
         out_dir = os.environ.get("SGF_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
+        self.path = os.path.join(out_dir, f"clocks_gpu{index}_{os.getpid()}.csv")
 
-    def start(self):
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return [ln for ln in f.read().splitlines() if ln.strip()]
+        except OSError:
+            return []
+
+    def start(self, wait_s=5.0):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            if os.path.exists(self.path):
+                os.remove(self.path)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < wait_s and not self._lines():
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        self.proc.terminate()
+        self.proc.send_signal(2)  # SIGINT: nvidia-smi closes its file
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in self._lines():
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -114,11 +131,16 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "nvidia-smi every 100 ms across the load window that holds the "
+                                              "timed steps (at least 1 s of back-to-back applications)"}
+
+
+STAGES = ["project", "fft_x", "conv_y", "ifft_x", "near", "interp"]
 
 
 def stage_bytes(info, s):
-    """Algorithmic bytes per launch group of the forward map for far-field complex size s (8 or 16)."""
+    """Algorithmic bytes per stage of the forward map (compulsory traffic) for far-field complex size
+    s (8 mixed, 16 FP64); the near field is float-float (16 bytes per entry) or FP64 either way."""
     N, nnz, neq, nfit = info["N"], info["nnz"], info["neq"], info["nfit"]
     gH, gV = info["PxH"] * info["nrowH"], info["PxV"] * info["nrowV"]
     kH, kV = info["PxH"] * info["PyH"], info["PxV"] * info["PyV"]
@@ -127,17 +149,19 @@ def stage_bytes(info, s):
         "fft_x": s * 2 * 2 * (gH + gV),
         "conv_y": s * ((2 * gH + 2 * kH + gH) + (2 * gV + 2 * kV + gV)),
         "ifft_x": s * 2 * (gH + gV),
-        "interp_near": s * nfit * N + 16 * nnz + s * info["n_occ"] * nfit + 32 * N,
+        "near": 16 * nnz + 32 * N,
+        "interp": s * nfit * N + s * info["n_occ"] * nfit + 32 * N,
     }
 
 
-STAGES = ["project", "fft_x", "conv_y", "ifft_x", "interp_near"]
-# DRAM bytes per launch (read + write) of the mixed-path kernels of each stage, from one ncu capture
-# of the current kernels (profiles/forward_map_deep_corrugation_n16384.md): mean of the H and V
-# launches where a stage has two. None where no capture of the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"project": 13.24e6, "fft_x": 4.26e6, "conv_y": 13.74e6, "ifft_x": 2.15e6,
-                         "interp_near": 27.35e6}
-LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "interp_near": 2}
+# launches per stage of one application (two orientations where a stage has two)
+LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "near": 1, "interp": 1}
+# DRAM bytes (read + write) per launch of the current mixed-path kernels, from one ncu capture of the
+# benchmark workload (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+# -k regex:k_ python bench.py --steps 3 --warmup 3 --batch 0 --gradient 0 --field 0
+# --no-cpu-baseline`); None where no capture of the current kernel exists.
+DRAM_BYTES_PER_LAUNCH = {"project": None, "fft_x": None, "conv_y": None, "ifft_x": None, "near": None,
+                         "interp": None}
 
 
 def peaks():
@@ -146,6 +170,66 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def time_applies(sgf, op, mu, out, stream, flush, steps, warmup):
+    """Mean CUDA-event time (ms) of one application, L2 flushed before every step (outside the
+    events), after `warmup` untimed applications."""
+    import torch
+
+    for _ in range(warmup):
+        sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def stage_times(sgf, op, mu, out, flush, n):
+    """Per-stage device times (ms) of `n` applications with profiling on: the stages then run one
+    after another on the context stream, each bracketed by CUDA events on that stream."""
+    sgf.sgf_set_profiling(op.ctx, 1)
+    st = np.zeros(8)
+    for _ in range(n):
+        flush.zero_()
+        sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+        st += sgf.sgf_stage_times(op.ctx)
+    sgf.sgf_set_profiling(op.ctx, 0)
+    st /= n
+    return dict(zip(STAGES, st[:6].tolist()))
+
+
+def run_solves(sgf, par, dev, stream, tol, maxit):
+    """Headline solves (Algorithm 1, zero initial guess): FP64 GMRES and the mixed path (FP32 far
+    field, FP64 residual refinement), each timed end to end (one untimed solve first), with the
+    energy error of its solution and the distance between the two solutions."""
+    import torch
+
+    out = {}
+    sols = {}
+    for prec in (64, 32):
+        op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=prec)
+        x = torch.zeros(par["N"], dtype=torch.complex128, device=dev)
+        sgf.sgf_solve(op.ctx, tol, maxit, x.data_ptr())  # warm-up
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, its, rr = sgf.sgf_solve(op.ctx, tol, maxit, x.data_ptr())
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        _, _, eps = sgf.sgf_rayleigh(op.ctx, x.data_ptr(), -40, 40)
+        op.close()
+        sols[prec] = x
+        out["fp64" if prec == 64 else "mixed"] = {
+            "value": 1.0 / t, "unit": "solves/s", "s": t, "tol": tol, "status": st, "applications": its,
+            "relres": rr, "energy_error": eps}
+    out["mixed_vs_fp64_solution_rel"] = float(torch.linalg.norm(sols[32] - sols[64]) / torch.linalg.norm(sols[64]))
+    return out
 
 
 def run_ours(args):
@@ -168,41 +252,41 @@ def run_ours(args):
     res = {}
     ops = {}
     for prec in (64, 32):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         op = sgf.Operator(par, device=local, stream=stream.cuda_stream, precision=prec)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
         ops[prec] = op
         out = torch.empty_like(mu)
-        for _ in range(args.warmup):
-            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         clocks = Clocks(local)
         if prec == 32:
             clocks.start()
+            # back-to-back load before the timed steps, so that the sampler sees the clocks under it
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 0.5:
+                for _ in range(50):
+                    sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+                torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        ms = time_applies(sgf, op, mu, out, stream, flush, args.steps, args.warmup)
         if ws > 1:
             torch.distributed.barrier()
-        ck = clocks.stop() if prec == 32 else None
-        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-        # stage times of the same launches (event pairs between stages), averaged over steps
-        sgf.sgf_set_profiling(op.ctx, 1)
-        st = np.zeros(8)
-        nprof = max(3, min(args.steps, 20))
-        for _ in range(nprof):
-            flush.zero_()
-            sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
-            st += sgf.sgf_stage_times(op.ctx)
-        sgf.sgf_set_profiling(op.ctx, 0)
-        st /= nprof
-        res[prec] = {"ms": ms, "stages_ms": dict(zip(STAGES, st[:5].tolist())), "clocks": ck,
-                     "out": out.clone(), "info": op.info}
+        ck = None
+        if prec == 32:
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 0.5:
+                for _ in range(50):
+                    sgf.sgf_apply(op.ctx, mu.data_ptr(), out.data_ptr())
+                torch.cuda.synchronize()
+            ck = clocks.stop()
+        stg = stage_times(sgf, op, mu, out, flush, max(3, min(args.steps, 20)))
+        info = op.info
+        res[prec] = {"ms": ms, "stages_ms": stg, "clocks": ck, "out": out.clone(), "info": info,
+                     "init": {"s": t_build, "build_ms": info["build_ms"], "tables_ms": info["build_tables_ms"],
+                              "least_squares_ms": info["build_ls_ms"], "near_operator_ms": info["build_near_ms"]}}
     # accuracy of the mixed path against the FP64 path on the benchmark input
     y64, y32 = res[64]["out"], res[32]["out"]
     mixed_err = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
@@ -220,6 +304,8 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / args.steps
     for op in ops.values():
         op.close()
+    solves = run_solves(sgf, par, dev, stream, 1e-12, 4000) if args.solve and rank == 0 else None
+    shifted = run_shifted(sgf, dev, stream, flush, args) if args.shifted and rank == 0 else None
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
     tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
@@ -234,13 +320,15 @@ def run_ours(args):
     if rank != 0:
         return
     info = res[32]["info"]
-    # roofline of the dominant stage of the headline (mixed) path
+    # roofline of the dominant kernel of the headline (mixed) path, from its own CUDA-event time
     hbm, kind = peaks()
     sb = stage_bytes(info, 8)
     stg = res[32]["stages_ms"]
     dom = max(STAGES, key=lambda k: stg[k])
     per_launch_ms = stg[dom] / LAUNCHES[dom]
     ach = sb[dom] / LAUNCHES[dom] / (per_launch_ms * 1e-3) / 1e9
+    kernel_names = {"project": "k_project", "fft_x": "k_fft_x (forward)", "conv_y": "k_conv_y",
+                    "ifft_x": "k_fft_x (inverse)", "near": "k_near_rows<float>", "interp": "k_interp_far<float>"}
     line = {
         "metric": METRIC,
         "value": whole_job_rate(ws, ms32),
@@ -252,10 +340,12 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64 far field (projection, FFT, interpolation) + c128 near field",
+        "dtype": "c64 far field (projection, FFT, interpolation); float-float (FP32 hi/lo pairs, compensated "
+                 "FP32 arithmetic) near field and modes; c128 in and out",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": 16384, "cells": "128x257", "k": "2pi", "theta_deg": 45,
-                   "bc": "neumann", "shifts_j": 8, "n_per": 40, "eq_sources_per_orientation": int(info["neq"]),
+        "config": {"workload": WORKLOAD, "N": int(par["N"]), "cells": f"{par['nx']}x{par['ny']}", "k": "2pi",
+                   "theta_deg": 45, "bc": "neumann", "shifts_j": int(par["j"]), "n_per": int(par["n_per"]),
+                   "eq_sources_per_orientation": int(info["neq"]),
                    "fft_grids": f"H {int(info['PxH'])}x{int(info['PyH'])}, V {int(info['PxV'])}x{int(info['PyV'])}",
                    "near_field_entries": int(info["nnz"]), "l2": "flushed (256 MiB write) before each timed step",
                    "parallelism": f"replicas x{ws}"},
@@ -265,14 +355,21 @@ def run_ours(args):
         "whole_step_hbm_frac": info["bytes32"] / (ms32 * 1e-3) / 1e9 / hbm,
         "mixed_rel_err_vs_fp64": mixed_err,
         "stages_ms": stg,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom), "peak_kind": kind,
-                     "algorithmic_bytes_per_launch": sb[dom] / LAUNCHES[dom]},
-        "e2e": {"value": ws / e2e_s, "unit": "matvecs/s", "h2d_bytes_per_step": 16 * 16384,
-                "d2h_bytes_per_step": 16 * 16384},
+        "stage_hbm_frac": {k: sb[k] / (stg[k] * 1e-3) / 1e9 / hbm for k in STAGES if stg[k] > 0},
+        "init": {"mixed": res[32]["init"], "fp64": res[64]["init"]},
+        "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "stage": dom, "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom), "peak_kind": kind,
+                     "algorithmic_bytes_per_launch": sb[dom] / LAUNCHES[dom],
+                     "time": "CUDA events around the stage's launches on the library's stream (stages serialised)"},
+        "e2e": {"value": ws / e2e_s, "unit": "matvecs/s", "h2d_bytes_per_step": 16 * int(par["N"]),
+                "d2h_bytes_per_step": 16 * int(par["N"])},
         "gpu_launches": int(info["launches"]) * args.steps,
         "clocks": res[32]["clocks"],
     }
+    if solves is not None:
+        line["solve"] = solves
+    if shifted is not None:
+        line["shifted_j8"] = shifted
     if batch is not None:
         line["batch"] = batch
     if grad is not None:
@@ -290,6 +387,26 @@ def run_ours(args):
     if not args.no_cpu_baseline and ws >= 1:
         line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
     print(json.dumps(line), flush=True)
+
+
+def run_shifted(sgf, dev, stream, flush, args):
+    """The same geometry with the shifted kernel (j = 8, n_per = 40, h ~ lambda/2): applications per
+    second of both precisions. The shifted system is nearly singular on this 20-wavelength-deep
+    profile (condition ~4^j growth), so no solve is timed for it."""
+    import torch
+
+    par = inputs.wl_deep_corrugation_neumann(j=8, n_per=40)
+    mu = torch.from_numpy(inputs.random_density(par["N"], 7)).to(dev)
+    out = {}
+    for prec in (32, 64):
+        op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=prec)
+        y = torch.empty_like(mu)
+        ms = time_applies(sgf, op, mu, y, stream, flush, max(3, min(args.steps, 100)), args.warmup)
+        info = op.info
+        op.close()
+        out["mixed" if prec == 32 else "fp64"] = {"value": 1000.0 / ms, "unit": "matvecs/s", "ms_per_step": ms,
+                                                   "near_field_entries": int(info["nnz"])}
+    return out
 
 
 def run_cufft_reference(info, ours_ms, dev, stream, flush, steps):
@@ -587,47 +704,121 @@ def run_batch(args, dev, stream, flush):
     }
 
 
-def cpu_baseline(rows=6):
-    """The CPU oracle (exact operator, matrix-free rows) on `rows` rows of the same workload; the
-    row rate is scaled to full matvecs (N rows each)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def assemble_oracle_rows(par, rows):
+    """Oracle rows of the exact operator (the assembly cost, timed on its own) and the dense
+    row block the ZGEMV is timed on: the assembled rows tiled to GEMV_BLOCK rows."""
     from oracle import direct
 
-    par = workload()
-    mu = inputs.random_density(par["N"], 7)
-    idx = np.linspace(0, par["N"] - 1, rows).astype(int)
+    N = par["N"]
+    idx = np.linspace(0, N - 1, rows).astype(int)
     t0 = time.perf_counter()
-    direct.apply_rows(par, mu, idx)
-    dt = time.perf_counter() - t0
-    return {"value": rows / dt / par["N"], "unit": "matvecs/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows} rows of the exact operator (matrix-free, hybrid G~ per pair) at N=16384, "
-                      f"{dt:.1f} s, scaled by rows/N"}
+    R = direct.assemble_rows(par, idx)
+    t_asm = time.perf_counter() - t0
+    blk = np.ascontiguousarray(np.tile(R, (GEMV_BLOCK // rows, 1)))
+    return blk, t_asm
+
+
+GEMV_BLOCK = 512
+
+
+def gemv_times(blk, mu, threads, reps_min_s=1.0, steps=None):
+    """Seconds per ZGEMV (blk @ mu) with `threads` BLAS threads, in a child process (the BLAS thread
+    count is fixed when numpy loads). steps: time exactly that many GEMVs and return each one's time;
+    otherwise repeat for at least reps_min_s and return the mean."""
+    d = tempfile.mkdtemp(prefix="sgf_gemv_")
+    fa, fm = os.path.join(d, "blk.npy"), os.path.join(d, "mu.npy")
+    np.save(fa, blk)
+    np.save(fm, mu)
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--gemv-worker", fa, fm, str(reps_min_s),
+           str(steps if steps else 0)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    for f in (fa, fm):
+        os.remove(f)
+    os.rmdir(d)
+    if r.returncode != 0:
+        raise RuntimeError("ZGEMV worker failed: " + r.stderr[-500:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def gemv_worker(fa, fm, reps_min_s, steps):
+    blk = np.load(fa)
+    mu = np.load(fm)
+    for _ in range(3):
+        blk @ mu
+    if steps > 0:
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            blk @ mu
+            ts.append(time.perf_counter() - t0)
+        print(json.dumps(ts))
+        return
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < reps_min_s:
+        blk @ mu
+        n += 1
+    print(json.dumps((time.perf_counter() - t0) / n))
+
+
+def cpu_baseline(rows=4):
+    """The CPU oracle's matvec: the exact operator assembled as dense rows (assembly timed on its own)
+    and applied by ZGEMV, on all host cores and on one. `rows` rows of the benchmark workload are
+    assembled and tiled to a GEMV_BLOCK x N block; the block's GEMV time is scaled by N / GEMV_BLOCK
+    to one full matvec (extrapolated: the N x N matrix, 4.3 GB at N = 16384, is not assembled)."""
+    par = workload()
+    N = par["N"]
+    blk, t_asm = assemble_oracle_rows(par, rows)
+    mu = inputs.random_density(N, 7)
+    cores = host_cores()
+    t_all = gemv_times(blk, mu, cores)
+    t_one = gemv_times(blk, mu, 1)
+    scale = N / GEMV_BLOCK
+    return {"value": 1.0 / (t_all * scale), "unit": "matvecs/s", "cores": cores, "kind": "oracle",
+            "sample": f"dense ZGEMV (numpy/OpenBLAS, {cores} threads) of a {GEMV_BLOCK} x {N} row block of the exact "
+                      f"operator ({rows} assembled rows tiled), {t_all * 1e3:.2f} ms, scaled by N/{GEMV_BLOCK} "
+                      f"(extrapolated); assembly of the {rows} rows {t_asm:.1f} s on one core",
+            "one_core": {"value": 1.0 / (t_one * scale), "unit": "matvecs/s", "cores": 1},
+            "assembly_s_per_row": t_asm / rows, "assembly_s_extrapolated": t_asm / rows * N,
+            "extrapolated": True}
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm: every step evaluates one row of the exact operator
-    (matrix-free) of the benchmark workload; the row rate is scaled to matvecs (N rows)."""
-    from oracle import direct
-
+    """The CPU oracle as the reference arm, on the benchmark workload: `--cpu-rows` rows of the exact
+    operator are assembled once (timed and reported; scaled to the full matrix), then every step is one
+    dense ZGEMV of a GEMV_BLOCK x N row block on all host cores, scaled by N / GEMV_BLOCK to one matvec."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     par = workload()
-    mu = inputs.random_density(par["N"], 7)
-    rng = np.random.default_rng(0)
-    steps = min(args.steps, 60)
-    for _ in range(args.warmup):
-        direct.apply_rows(par, mu, [int(rng.integers(par["N"]))])
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        direct.apply_rows(par, mu, [int(rng.integers(par["N"]))])
-    dt = time.perf_counter() - t0
-    v = steps / dt / par["N"]
-    sample = f"{steps} single rows of the exact operator at N=16384 in {dt:.1f} s, scaled by rows/N"
+    N = par["N"]
+    blk, t_asm = assemble_oracle_rows(par, args.cpu_rows)
+    mu = inputs.random_density(N, 7)
+    cores = host_cores()
+    steps = args.steps
+    ts = gemv_times(blk, mu, cores, steps=args.warmup + steps)[args.warmup:]
+    scale = N / GEMV_BLOCK
+    ms = float(np.mean(ts)) * scale * 1e3
+    v = 1000.0 / ms
+    sample = (f"dense ZGEMV (numpy/OpenBLAS, {cores} threads) of a {GEMV_BLOCK} x {N} row block of the exact operator "
+              f"({args.cpu_rows} assembled rows tiled) per step, scaled by N/{GEMV_BLOCK} (extrapolated); "
+              f"assembly {t_asm / args.cpu_rows * N:.0f} s extrapolated to all N rows (one core)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "matvecs/s", "n_gpus": ws,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": 16384, "cells": "128x257", "parallelism": "cpu oracle, 1 core"},
-            "cpu_baseline": {"value": v, "unit": "matvecs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "N": N, "cells": "128x257", "shifts_j": int(par["j"]),
+                       "n_per": int(par["n_per"]), "parallelism": f"cpu oracle, {cores} cores"},
+            "cpu_baseline": {"value": v, "unit": "matvecs/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "assembly_s_extrapolated": t_asm / args.cpu_rows * N},
             "e2e": {"value": v, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -641,15 +832,21 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
+    ap.add_argument("--solve", type=int, default=1, help="1: time the headline FP64 and mixed solves")
+    ap.add_argument("--shifted", type=int, default=1, help="1: time the j = 8 shifted kernel on the same geometry")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
     ap.add_argument("--tables", type=int, default=0,
                     help="1: the sinusoid tables of Section 6.2 with the dense operator (about a minute)")
     ap.add_argument("--field", type=int, default=1,
                     help="1: time the scattered-field image and the dense unaccelerated operator blocks")
+    ap.add_argument("--gemv-worker", nargs=4, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.gemv_worker:
+        fa, fm, rs, st = args.gemv_worker
+        gemv_worker(fa, fm, float(rs), int(st))
+        return
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
-        args.warmup = 1
         run_reference(args)
     else:
         from paper_1707_04950_gb300 import build

@@ -273,16 +273,20 @@ sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out);
  * restored). Rebuilds the operator several times: a set-up step, not for a hot loop. */
 sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms);
 
-/* Introspection: fills host info[0..19] with N, number of occupied cells, near-field entries,
- * P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per orientation), n_fit, n_fb basis size,
- * |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed matvec, kernel launches per matvec,
- * 1 if applications run as captured CUDA graphs, the longest near-field row, the largest cell node
- * count, log2 of the twiddle table length. */
+/* Introspection: fills host info[0..23] (the caller's buffer holds 24 doubles) with N, number of
+ * occupied cells, near-field entries, P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per
+ * orientation), n_fit, n_fb basis size, |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed
+ * matvec, kernel launches per matvec, 1 if applications run as captured CUDA graphs, the longest
+ * near-field row, the largest cell node count, log2 of the twiddle table length, then the wall
+ * times (ms) of the last sgf_build_operator (Algorithm 2): total, kernel tables and their spectra
+ * (the periodised Green function on the grids), least squares with the projection and
+ * reconstruction factors, near operator. */
 sgf_status sgf_info(const sgf_ctx* ctx, double* info);
 
 /* Device time of the stages of the last sgf_apply when profiling is switched on with
- * sgf_set_profiling(ctx, 1): host times_ms[0..7] = project, forward X-FFT, Y convolution, inverse
- * X-FFT, interpolation + near field + modes, total. */
+ * sgf_set_profiling(ctx, 1) (the stages then run one after another on the context stream): host
+ * times_ms[0..7] = project, forward X-FFT, Y convolution, inverse X-FFT, near field (block-sparse
+ * rows, sigma/2 identity), interpolation of the far field + modes, total, unused. */
 sgf_status sgf_set_profiling(sgf_ctx* ctx, int on);
 sgf_status sgf_stage_times(const sgf_ctx* ctx, double* times_ms);
 

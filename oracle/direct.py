@@ -135,6 +135,21 @@ def reg_matrix(par, rows=None):
     return (dx * kreg).reshape(len(rows), N)
 
 
+def assemble_rows(par, rows):
+    """Rows `rows` of the dense matrix (sigma/2 I + D_sing + D_reg + D_M) (eq. discrete_eq), as a
+    len(rows) x N block: the same parts as assemble(), restricted to the given targets."""
+    rows = np.asarray(rows)
+    A = reg_matrix(par, rows).astype(complex)
+    r, c, v = sing_triplets(par, rows)
+    pos = {int(t): n for n, t in enumerate(rows)}
+    np.add.at(A, (np.array([pos[int(t)] for t in r]), c), v)
+    T, S = modes_factors(par)
+    A += T[rows] @ S
+    sigma = 0.5 if par["bc"] == 0 else -0.5
+    A[np.arange(len(rows)), rows] += sigma
+    return A
+
+
 def apply_rows(par, mu, rows):
     """Rows `rows` of (sigma/2 I + D^dx) mu of the exact system, without assembling the matrix."""
     rows = np.asarray(rows)

@@ -2,6 +2,7 @@
 // index bookkeeping of Section 5.1 (binning, occupied cells, local sets L(q), grid indices of the
 // equivalent sources and samples), the orchestration of Algorithm 2 and Algorithm 3, restarted
 // GMRES with CGS2 Arnoldi (Algorithm 1), and Rayleigh extraction.
+#include <chrono>
 #include <complex>
 #include <cmath>
 #include <cstring>
@@ -252,9 +253,15 @@ static sgf_status validate(sgf_ctx* ctx) {
   return SGF_OK;
 }
 
+// host wall clock in ms (build-stage timers)
+static double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   if (!ctx) return SGF_EINVAL;
   TRY(validate(ctx));
+  const double t_build0 = wall_ms();
   CU(cudaSetDevice(ctx->device));
   free_all(ctx);
   sgf_ctx* c = ctx;
@@ -466,6 +473,8 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(cudaMemcpy(d_kress, kress.data(), kress.size() * sizeof(double), cudaMemcpyHostToDevice));
 
   // ---------------- least-squares operators (Algorithm 2, first step)
+  CU(cudaStreamSynchronize(ctx->stream));
+  const double t_ls0 = wall_ms();
   const int nc = P.n_coll;
   zd *d_Acoll, *d_Bfb, *d_pinv_eq, *d_pinv_fb, *d_qrs;
   const long lda = nc + 2 * neq;
@@ -489,6 +498,9 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   CU(launch_build_I(c, d_pinv_fb, d_Iplain, d_samp_rel));
 
   // ---------------- kernel tables and spectra
+  CU(cudaStreamSynchronize(c->stream));
+  const double t_tab0 = wall_ms();
+  c->build_ms[2] = t_tab0 - t_ls0;
   TRY(dalloc(ctx, &c->o64.tw, (size_t)1 << c->twlog));
   bool mixed = P.precision == 32;
   if (mixed) TRY(dalloc(ctx, &c->o32.tw, (size_t)1 << c->twlog));
@@ -507,6 +519,9 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   }
   TRY(dalloc(ctx, &c->d_msum, 64));
   CU(launch_tables(c));
+  CU(cudaStreamSynchronize(c->stream));
+  const double t_near0 = wall_ms();
+  c->build_ms[1] = t_near0 - t_tab0;
 
   // ---------------- local sets L(q) and the near-field block list
   // Values of cell q form one row-major n_q x W_q block (W_q = sum of n_r over its local cells, in
@@ -618,6 +633,9 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   c->keep.dcy_min = dcy_min;
   c->keep.n_dcy = n_dcy;
   c->keep.pp = pp;
+
+  CU(cudaStreamSynchronize(c->stream));
+  c->build_ms[3] = wall_ms() - t_near0;
 
   // ---------------- adjoint near layout: the rows of cell r collect conj(C) of every block (q, r),
   // blocks in block order, so each adjoint row is again one contiguous stream
@@ -760,6 +778,7 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     }
   }
   CU(cudaStreamSynchronize(c->stream));
+  c->build_ms[0] = wall_ms() - t_build0;
   return SGF_OK;
 }
 
@@ -794,14 +813,14 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
   }
   if (transpose_conj || ctx->op_exact) return SGF_OK;
   if (ctx->profiling) {
-    cudaEventSynchronize(ctx->ev[5]);
+    cudaEventSynchronize(ctx->ev[6]);
     float ms;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
       cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
       ctx->stage_ms[i] = ms;
     }
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
-    ctx->stage_ms[5] = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[6]);
+    ctx->stage_ms[6] = ms;
   }
   return SGF_OK;
 }
@@ -1099,11 +1118,12 @@ extern "C" sgf_status sgf_rayleigh(sgf_ctx* ctx, const void* mu_dev, int n_lo, i
 extern "C" sgf_status sgf_info(const sgf_ctx* ctx, double* info) {
   if (!ctx || !info) return SGF_EINVAL;
   if (!ctx->built) return SGF_ESTATE;
-  double v[20] = {(double)ctx->N, (double)ctx->n_occ, (double)ctx->nnz, (double)ctx->og[0].Px,
+  double v[24] = {(double)ctx->N, (double)ctx->n_occ, (double)ctx->nnz, (double)ctx->og[0].Px,
                   (double)ctx->og[0].nrow, (double)ctx->og[0].Py, (double)ctx->og[1].Px, (double)ctx->og[1].nrow,
                   (double)ctx->og[1].Py, (double)ctx->neq, (double)ctx->nfit, (double)ctx->nb,
                   (double)ctx->nm, ctx->bytes64, ctx->bytes32, (double)ctx->launches_per_apply,
-                  ctx->use_graphs ? 1.0 : 0.0, (double)ctx->maxW, (double)ctx->maxnq, (double)ctx->twlog};
+                  ctx->use_graphs ? 1.0 : 0.0, (double)ctx->maxW, (double)ctx->maxnq, (double)ctx->twlog,
+                  ctx->build_ms[0], ctx->build_ms[1], ctx->build_ms[2], ctx->build_ms[3]};
   memcpy(info, v, sizeof(v));
   return SGF_OK;
 }

@@ -142,6 +142,9 @@ struct sgf_ctx {
   cudaStream_t side2 = nullptr;  // third stream for the near field of the forward map
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork0 = nullptr, ev_join2 = nullptr;
   double stage_ms[8] = {0};
+  // wall times of the last sgf_build_operator (ms): total, kernel tables and spectra (A1), least
+  // squares + projection/reconstruction factors, near operator (local sets, blocks, values)
+  double build_ms[4] = {0};
   int launches_per_apply = 0;
   double bytes64 = 0, bytes32 = 0;
   BuildKeep keep;

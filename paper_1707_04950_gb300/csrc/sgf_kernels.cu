@@ -1334,11 +1334,12 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
     cudaStreamWaitEvent(s, c->ev_join2, 0);
   else
     near_rows(s);
+  if (c->profiling) cudaEventRecord(c->ev[5], s);
   k_interp_far<T><<<c->n_items, 128, 0, s>>>(c->debug_mask, c->nfit, c->nm, c->d_cell_start, c->d_node_idx,
                                              c->d_samp_gidx, c->prm.p, od.grid[0], od.grid[1], od.Ip, c->d_MT, c->d_MTff,
                                              c->d_mpart, c->d_mpart_ff, c->mode_chunks, c->d_item_cell, c->d_item_lo,
                                              c->d_item_hi, out);
-  if (c->profiling) cudaEventRecord(c->ev[5], s);
+  if (c->profiling) cudaEventRecord(c->ev[6], s);
   return cudaGetLastError();
 }
 

@@ -135,8 +135,17 @@ def wl_sinusoid_dirichlet(N=512, nx=16, **kw):
 def wl_deep_corrugation_neumann(N=16384, nx=128, **kw):
     """Deep sinusoidal corrugation, depth/period = 2, period 10 (wavelength 1), TM (Neumann),
     theta = 45 deg, 128 cell columns (L = 10/128); one extra cell row so that half-open cells hold
-    both the crest and the trough node."""
+    both the crest and the trough node.
+
+    Away from Wood anomalies (the nearest, n = 3 and n = -17, have |beta_n| = 0.75 and 0.74) the
+    unshifted periodic Green function is used (j = 0), as in the paper's deep-grating runs (Section 6,
+    Table deep_gratings: "G^qper_0 eval."); Section 6.1 warns that shifted sources close to a deep
+    surface make the system ill-conditioned. The j = 0 windowed lattice sum converges slowly here
+    (n_per = 640: 3e-8, 1280: 5e-11 next to Y = 0), so n_per = 2048 (the parameter rule for 1e-8).
+    Pass j = 8 (and n_per = 40) for the shifted kernel on the same geometry."""
     prof = sinusoid(10.0, 10.0)
+    kw.setdefault("j", 0)
+    kw.setdefault("n_per", 2048)
     return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
 
 

@@ -309,11 +309,12 @@ def sgf_batch_solve(batch, tol, maxit, mu_ptrs):
 
 
 INFO_KEYS = ["N", "n_occ", "nnz", "PxH", "nrowH", "PyH", "PxV", "nrowV", "PyV", "neq", "nfit", "nb", "nm",
-             "bytes64", "bytes32", "launches", "graphs", "maxW", "maxnq", "twlog"]
+             "bytes64", "bytes32", "launches", "graphs", "maxW", "maxnq", "twlog",
+             "build_ms", "build_tables_ms", "build_ls_ms", "build_near_ms"]
 
 
 def sgf_info(ctx):
-    v = np.zeros(20)
+    v = np.zeros(24)
     _check(ctx, load().sgf_info(ctx, _dptr(v)))
     return dict(zip(INFO_KEYS, v.tolist()))
 

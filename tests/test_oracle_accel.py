@@ -14,21 +14,69 @@ def _relerr(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+# Accelerated vs exact operator (the accelerator's approximation error, not rounding): measured
+# 9.0e-7 (Dirichlet, double Wood sinusoid, N = 128) and 5.4e-7 (Neumann, deep shape, N = 192); the
+# pins hold them at 5e-6. A local set missing one cell row moves them to 2.7e-2 and 8.1e-3, and so
+# does a dipole kernel of the wrong sign on one orientation (test_planted_mistakes_fail_the_pins).
+ACCEL_VS_EXACT = 5e-6
+
+
+def _dirichlet_case():
+    par = I.wl_sinusoid_dirichlet(N=128)
+    return par, I.random_density(128, 7)
+
+
+def _neumann_case():
+    par = I.wl_deep_corrugation_neumann_small(N=192, nx=24)
+    return par, I.random_density(192, 11)
+
+
 def test_accelerated_matches_exact_operator_dirichlet_wood():
     # the accelerated forward map approximates (1/2 I + D^dx) of the exact system
-    par = I.wl_sinusoid_dirichlet(N=128)
-    mu = I.random_density(128, 7)
+    par, mu = _dirichlet_case()
     y_exact = dr.assemble(par) @ mu
     y = ac.Accel(par).apply(mu)
-    assert _relerr(y, y_exact) < 3e-5
+    assert _relerr(y, y_exact) < ACCEL_VS_EXACT
 
 
 def test_accelerated_matches_exact_operator_neumann_deep():
-    par = I.wl_deep_corrugation_neumann_small(N=192, nx=24)
-    mu = I.random_density(192, 11)
+    par, mu = _neumann_case()
     y_exact = dr.assemble(par) @ mu
     y = ac.Accel(par).apply(mu)
-    assert _relerr(y, y_exact) < 1e-3
+    assert _relerr(y, y_exact) < ACCEL_VS_EXACT
+
+
+def _drop_top_row(orig):
+    def rows(self, cy_r):
+        r = set(orig(self, cy_r))
+        if r:
+            r.discard(max(r))
+        return r
+    return rows
+
+
+@pytest.mark.parametrize("case", ["dirichlet", "neumann"])
+@pytest.mark.parametrize("mistake", ["local_set_row", "dipole_sign_V"])
+def test_planted_mistakes_fail_the_pins(monkeypatch, case, mistake):
+    # a plausible mistake planted in the oracle's Algorithm 2/3 must move the accelerated operator
+    # far outside the accelerated-vs-exact pin
+    par, mu = _dirichlet_case() if case == "dirichlet" else _neumann_case()
+    y_exact = dr.assemble(par) @ mu
+    if mistake == "local_set_row":
+        monkeypatch.setattr(ac.Accel, "rows_of_Sj", _drop_top_row(ac.Accel.rows_of_Sj))
+        acc = ac.Accel(par)
+    else:
+        # the V dipole kernel of the periodised table with the wrong sign (the least-squares fit
+        # keeps the right one)
+        orig_tables = ac.Accel._tables
+
+        def tables(self):
+            orig_tables(self)
+            mono, dip, nr = self.tab["V"]
+            self.tab["V"] = (mono, -dip, nr)
+        monkeypatch.setattr(ac.Accel, "_tables", tables)
+        acc = ac.Accel(par)
+    assert _relerr(acc.apply(mu), y_exact) > 100 * ACCEL_VS_EXACT
 
 
 def test_mode_and_singular_parts_are_the_exact_ones():
