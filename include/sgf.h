@@ -32,7 +32,8 @@ typedef enum {
   SGF_ENOCONV = 5,         /* GMRES did not reach the tolerance within maxit                  */
   SGF_EBREAKDOWN = 6,      /* Krylov breakdown                                                 */
   SGF_ENONFINITE = 7,      /* a non-finite value was produced                                   */
-  SGF_ETIMEOUT = 8,        /* a bounded device wait gave up                                     */
+  SGF_ETIMEOUT = 8,        /* reserved: no kernel of this library waits on a device flag, so no
+                              call returns it                                                   */
   SGF_ECUDA = 9,           /* a CUDA runtime call failed                                        */
   SGF_ESTATE = 10          /* call order violated (e.g. apply before build)                    */
 } sgf_status;
@@ -294,6 +295,16 @@ sgf_status sgf_stage_times(const sgf_ctx* ctx, double* times_ms);
  * (interpolated phi^all), bit 1 the block-sparse near operator, bit 2 the mode completion D_M,
  * bit 3 the sigma/2 identity. Default 15 (all). */
 sgf_status sgf_debug_mask(sgf_ctx* ctx, int mask);
+
+/* Testing hook: force the launch variants of the grid convolution for the following applications
+ * (forward and adjoint, every orientation) instead of the per-launch choice: conv_variant 1 = the Y
+ * convolution with 16 values per thread in registers, 2 = the same with its partial product in a
+ * global scratch array (allocated here if the build did not need it), 3 = 8 values per thread, 0 =
+ * chosen per launch; fftx_vpt 8 or 16 values per thread in the X passes, 0 = chosen per launch. The
+ * captured forward maps are captured again. SGF_EINVAL if a forced variant does not fit the launch
+ * limits (threads, shared memory, registers) of an orientation; SGF_ESTATE before build. A rebuild
+ * clears the forcing. Synchronises. */
+sgf_status sgf_debug_force_variants(sgf_ctx* ctx, int conv_variant, int fftx_vpt);
 
 /* Copy of internal tables for testing: which = 0 twisted kernel table of orientation lam
  * (0 = H, 1 = V) before the Y transform, [P_x][P_y] complex128 with kind 0 monopole, 1 dipole.

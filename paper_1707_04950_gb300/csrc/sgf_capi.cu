@@ -275,6 +275,7 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   c->nfit = 4 * (P.p + 1);
   c->nb = 2 * P.n_fb + 1;
   if (!(c->a_s < c->L)) return set_err(ctx, SGF_EWINDOW, "singular window a = %g must be below the cell side %g", c->a_s, c->L);
+  for (int l = 0; l < 2; ++l) c->og[l].force_conv = c->og[l].force_vpt = 0;
   // grids
   Orient& H = c->og[0];
   Orient& V = c->og[1];
@@ -893,6 +894,7 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   TRY(dot_host(ctx, K, b, 1, b, tmp));
   double bn = std::sqrt(tmp[0].real());
   CU(cudaMemsetAsync(x, 0, N * sizeof(zd), ctx->stream));
+  if (!std::isfinite(bn)) return set_err(ctx, SGF_ENONFINITE, "non-finite right-hand side");
   if (bn == 0) { *relres = 0; return SGF_OK; }
   int total = 0;
   double res = bn;
@@ -1022,6 +1024,7 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
     cudaMemcpyAsync(K.r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
     st = dot_host(ctx, K, b, 1, b, tmp);
     double bn = std::sqrt(tmp[0].real());
+    if (st == SGF_OK && !std::isfinite(bn)) st = set_err(ctx, SGF_ENONFINITE, "non-finite right-hand side");
     zd* r = nullptr;
     if (st == SGF_OK) st = al(&r, N);
     if (st == SGF_OK) cudaMemcpyAsync(r, b, N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1137,6 +1140,48 @@ extern "C" sgf_status sgf_set_profiling(sgf_ctx* ctx, int on) {
 extern "C" sgf_status sgf_debug_mask(sgf_ctx* ctx, int mask) {
   if (!ctx || mask < 0 || mask > 15) return SGF_EINVAL;
   ctx->debug_mask = mask;
+  return SGF_OK;
+}
+
+extern "C" sgf_status sgf_debug_force_variants(sgf_ctx* ctx, int conv_variant, int fftx_vpt) {
+  if (!ctx) return SGF_EINVAL;
+  if (!ctx->built) return set_err(ctx, SGF_ESTATE, "operator not built");
+  if (conv_variant < 0 || conv_variant > 3 || (fftx_vpt != 0 && fftx_vpt != 8 && fftx_vpt != 16))
+    return set_err(ctx, SGF_EINVAL, "conv_variant must be 0..3 and fftx_vpt 0, 8 or 16");
+  sgf_ctx* c = ctx;
+  const bool mixed = c->prm.precision == 32;
+  for (int lam = 0; lam < 2; ++lam)
+    for (int prec : {64, 32}) {
+      if (prec == 32 && !mixed) continue;
+      if (!debug_variants_fit(c->og[lam], prec, conv_variant, fftx_vpt))
+        return set_err(ctx, SGF_EINVAL, "variant %d / %d values per thread does not fit orientation %d (FP%d)",
+                       conv_variant, fftx_vpt, lam, prec);
+    }
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  if (conv_variant == 2)  // the global-scratch variant's partial products
+    for (int lam = 0; lam < 2; ++lam) {
+      size_t n = (size_t)c->og[lam].Px * c->og[lam].Py;
+      if (!c->o64.accg[lam]) TRY(dalloc(ctx, &c->o64.accg[lam], n));
+      if (mixed && !c->o32.accg[lam]) TRY(dalloc(ctx, &c->o32.accg[lam], n));
+    }
+  for (int lam = 0; lam < 2; ++lam) {
+    c->og[lam].force_conv = conv_variant;
+    c->og[lam].force_vpt = fftx_vpt;
+  }
+  // the captured forward maps hold the launch shapes: capture them again
+  destroy_graphs(c);
+  if (c->use_graphs)
+    for (int prec : {64, 32}) {
+      if (prec == 32 && !mixed) continue;
+      cudaError_t ge = build_apply_graph(c, prec);
+      if (ge != cudaSuccess) {
+        c->use_graphs = false;
+        destroy_graphs(c);
+        break;
+      }
+    }
+  CU(cudaStreamSynchronize(c->stream));
   return SGF_OK;
 }
 

@@ -18,6 +18,9 @@
 struct Orient {
   int Px, logPx, nrow, Py, la, lb;  // Py = 2^la 3^lb >= 2 nrow - 1
   double dxg, dyg;
+  // testing hook (sgf_debug_force_variants): 0 = chosen per launch, else the forced Y-convolution
+  // variant (1 registers/16 values, 2 global scratch, 3 8 values) and X-pass values per thread
+  int force_conv = 0, force_vpt = 0;
 };
 
 // Device operator data of one precision (T = double or float).
@@ -220,6 +223,9 @@ cudaError_t launch_rayleigh_mp(sgf_ctx* c, const zd* mu, int nmodes, const doubl
 cudaError_t launch_twiddles(sgf_ctx* c);
 // which Y-convolution kernel serves this orientation: 1 registers, 2 global scratch, 0 none fits
 int conv_y_variant_of(const Orient& o, int precision, bool adjoint = false);
+// whether the forced variants fit the launch limits (threads, shared memory, registers) of this
+// orientation in this precision, forward and adjoint (0 = not forced)
+bool debug_variants_fit(const Orient& o, int precision, int conv_variant, int fftx_vpt);
 cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);
 // Krylov helpers
 cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,

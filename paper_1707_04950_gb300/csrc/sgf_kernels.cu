@@ -488,7 +488,8 @@ static cudaError_t run_fft_x(cplx<T>* g, const Orient& o, int nrow, int narr, co
   size_t sm = fftx_smem(o.Px, ty, sizeof(cplx<T>));
   dim3 grid(ceil_div(nrow, ty), narr);
   int t8 = fftx_threads(o.Px, ty, 8);
-  if (t8 <= 1024 && (long)fftx_regs<T, 8>() * t8 <= 65536) {
+  const bool fits8 = t8 <= 1024 && (long)fftx_regs<T, 8>() * t8 <= 65536;
+  if (o.force_vpt ? o.force_vpt == 8 : fits8) {
     cudaFuncSetAttribute(k_fft_x<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_fft_x<T, 8><<<grid, t8, sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
   } else {
@@ -1209,6 +1210,38 @@ static int conv_y_variant(const Orient& o) {
   return 0;
 }
 
+template <typename T, bool ADJ>
+static bool conv_variant_fits(const Orient& o, int v) {
+  const size_t col = (size_t)splen(o.Py) * sizeof(cplx<T>), twb = (size_t)o.Py * sizeof(cplx<T>);
+  const int t8 = conv_threads(o.Py, 8, o.lb), t16 = conv_threads(o.Py, 16, o.lb);
+  const size_t sm8 = col + twb + (ADJ ? 0 : col);
+  switch (v) {
+    case 3: return t8 <= 1024 && sm8 <= 200 * 1024 && (long)conv_regs<T, ADJ, 8, false>() * t8 <= 65536;
+    case 1: return t16 <= 1024 && col + twb <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, false>() * t16 <= 65536;
+    case 2: return t16 <= 1024 && col <= 200 * 1024 && (long)conv_regs<T, ADJ, 16, true>() * t16 <= 65536;
+    default: return false;
+  }
+}
+template <typename T>
+static bool variants_fit(const Orient& o, int conv_variant, int vpt) {
+  if (conv_variant && !(conv_variant_fits<T, false>(o, conv_variant) && conv_variant_fits<T, true>(o, conv_variant)))
+    return false;
+  const int ty = fftx_ty(o.Px, o.nrow, sizeof(cplx<T>));
+  if (vpt == 8) {
+    const int t8 = fftx_threads(o.Px, ty, 8);
+    if (t8 > 1024 || (long)fftx_regs<T, 8>() * t8 > 65536) return false;
+  } else if (vpt == 16) {
+    const int t16 = fftx_threads(o.Px, ty, 16);
+    if (t16 > 1024 || (long)fftx_regs<T, 16>() * t16 > 65536) return false;
+  } else if (vpt != 0) {
+    return false;
+  }
+  return true;
+}
+bool debug_variants_fit(const Orient& o, int precision, int conv_variant, int fftx_vpt) {
+  return precision == 64 ? variants_fit<double>(o, conv_variant, fftx_vpt) : variants_fit<float>(o, conv_variant, fftx_vpt);
+}
+
 int conv_y_variant_of(const Orient& o, int precision, bool adjoint) {
   if (adjoint) return precision == 64 ? conv_y_variant<double, true>(o) : conv_y_variant<float, true>(o);
   return precision == 64 ? conv_y_variant<double, false>(o) : conv_y_variant<float, false>(o);
@@ -1233,7 +1266,7 @@ static void conv_launch(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cpl
 template <typename T, bool ADJ>
 static cudaError_t conv_y_any(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
                               const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
-  switch (conv_y_variant<T, ADJ>(o)) {
+  switch (o.force_conv ? o.force_conv : conv_y_variant<T, ADJ>(o)) {
     case 3:
       conv_launch<T, ADJ, 8, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 8, o.lb), s);
       break;

@@ -132,6 +132,32 @@ def wl_sinusoid_dirichlet(N=512, nx=16, **kw):
     return make_params(prof, 2 * math.pi, 30.0, DIRICHLET, N, nx=nx, ny=ny, hmin=hmin, **kw)
 
 
+def wl_sinusoid_dirichlet_energy(N=512, **kw):
+    """The double-Wood sinusoid (wl_sinusoid_dirichlet) at the settings of its energy-balance run:
+    n_per = 640 (the windowed sums converge like A^-3.5 at the anomaly, Lemma lemma_app_1: energy
+    error of the exact system 2.1e-6 at n_per = 40, 1.3e-8 at 160, 8e-11 at 640) and the
+    equivalent-source fit with e = 2 extra points per side end, n_coll = 196 collocation points
+    and Tikhonov weight 1e-10: measured accelerated energy error -2.9e-9. The neighbouring settings
+    (e in {1, 2, 3}, ls_reg in 3e-11..3e-10, n_coll in {160, 196, 200}) give 3e-9..8e-8, and
+    e = 1 with ls_reg = 1e-6 4.4e-6: at 16 x 16 cells (k L = 0.79) the equivalent-source fit
+    limits the accelerated operator to ~1e-8."""
+    kw.setdefault("n_per", 640)
+    kw.setdefault("ls_reg", 1e-10)
+    kw.setdefault("e", 2)
+    kw.setdefault("n_coll", 196)
+    return wl_sinusoid_dirichlet(N=N, **kw)
+
+
+def wl_gaussian_wood_energy(N=8192, **kw):
+    """The Gaussian Wood surface (wl_gaussian_wood) at the settings of its energy-balance run:
+    n_per = 1024 (the paper's scaling d n_per ~ 4e4 for its grazing rough surfaces), Tikhonov weight
+    1e-10 and n_fb = 14 (measured accelerated energy error 3.9e-6; exact system 4.7e-10)."""
+    kw.setdefault("n_per", 1024)
+    kw.setdefault("ls_reg", 1e-10)
+    kw.setdefault("n_fb", 14)
+    return wl_gaussian_wood(N=N, **kw)
+
+
 def wl_deep_corrugation_neumann(N=16384, nx=128, **kw):
     """Deep sinusoidal corrugation, depth/period = 2, period 10 (wavelength 1), TM (Neumann),
     theta = 45 deg, 128 cell columns (L = 10/128); one extra cell row so that half-open cells hold
@@ -146,6 +172,9 @@ def wl_deep_corrugation_neumann(N=16384, nx=128, **kw):
     prof = sinusoid(10.0, 10.0)
     kw.setdefault("j", 0)
     kw.setdefault("n_per", 2048)
+    # Tikhonov weight of the equivalent-source fit: measured energy error of the solution 7.2e-7
+    # (1e-6), 9.9e-9 (1e-7), 4.4e-9 (1e-8), 4.9e-9 (1e-9), 7.4e-9 (1e-10)
+    kw.setdefault("ls_reg", 1e-8)
     return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
 
 

@@ -23,6 +23,7 @@ EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_four
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
             "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_field", "sgf_build_exact", "sgf_select_operator",
             "sgf_exact_matrix", "sgf_suggest_params", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
+            "sgf_debug_force_variants",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve",
             "sgf_batch_shared_near"]
 
@@ -81,6 +82,7 @@ def load():
         "sgf_stage_times": [vp, dp],
         "sgf_debug_mask": [vp, i],
         "sgf_debug_table": [vp, i, i, vp],
+        "sgf_debug_force_variants": [vp, i, i],
         "sgf_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), vp],
         "sgf_batch_apply": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "sgf_batch_solve": [vp, d, i, ctypes.POINTER(vp), ctypes.POINTER(i), dp],
@@ -331,6 +333,10 @@ def sgf_stage_times(ctx):
 
 def sgf_debug_mask(ctx, mask):
     _check(ctx, load().sgf_debug_mask(ctx, int(mask)))
+
+
+def sgf_debug_force_variants(ctx, conv_variant, fftx_vpt):
+    _check(ctx, load().sgf_debug_force_variants(ctx, int(conv_variant), int(fftx_vpt)))
 
 
 def sgf_debug_table(ctx, lam, kind, shape):

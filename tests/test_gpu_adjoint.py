@@ -6,7 +6,8 @@ against the FP64 one.
 Tolerances follow the forward map: the FP64 adjoint evaluates the same operator as the oracle in
 another order. The least-squares factors built on each side (condition ~1e6 after the Tikhonov
 term) differ at rounding times condition, which leaves the two operators ~1e-10 apart at the Wood
-configuration in some directions (the forward map measures 7e-11 there); we require 3e-10. The
+configuration in some directions (the forward map measures 7e-11 there); compared element by
+element (largest difference over the largest reference element) we require 1e-9. The
 mixed adjoint carries the FP32 far-field error (1e-5); an
 identity between the GPU's own forward and adjoint maps holds to rounding (1e-12 FP64; the two
 mixed maps round differently, 1e-6).
@@ -42,6 +43,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def _maxrel(a, b):
+    """Largest element-wise difference over the largest reference element."""
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
 def _apply(op, x, adj, mask=None):
     xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
     yt = torch.empty_like(xt)
@@ -64,7 +70,24 @@ def test_adjoint_fp64_matches_oracle(name):
     op = sgf.Operator(par, precision=64)
     got = _apply(op, v, 1)
     op.close()
-    assert _rel(got, A.conj().T @ v) < 3e-10
+    assert _maxrel(got, A.conj().T @ v) < 1e-9  # element-wise; the forward map's tolerance
+
+
+@pytest.mark.parametrize("name", ["sinusoid_dirichlet_wood_n512", "deep_neumann_n1024"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_adjoint_every_convolution_variant_matches_oracle(name, prec):
+    # the adjoint Y convolution and X passes in every launch variant (forced; see the forward test)
+    par = CASES[name]()
+    ref = _matrix(name).conj().T @ I.random_density(par["N"], 9)
+    v = I.random_density(par["N"], 9)
+    op = sgf.Operator(par, precision=prec)
+    errs = {}
+    for c in (1, 2, 3):
+        for vpt in (8, 16):
+            sgf.sgf_debug_force_variants(op.ctx, c, vpt)
+            errs[(c, vpt)] = _maxrel(_apply(op, v, 1), ref)
+    op.close()
+    assert max(errs.values()) < (1e-9 if prec == 64 else 5e-5), errs
 
 
 @pytest.mark.parametrize("name", ["sinusoid_dirichlet_wood_n512", "deep_neumann_n1024"])
