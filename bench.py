@@ -306,6 +306,8 @@ def run_ours(args):
         op.close()
     solves = run_solves(sgf, par, dev, stream, 1e-12, 4000) if args.solve and rank == 0 else None
     shifted = run_shifted(sgf, dev, stream, flush, args) if args.shifted and rank == 0 else None
+    multi = run_multi_rhs(sgf, dev, stream, flush, args) if args.multi and rank == 0 else None
+    sweep = run_sweep(sgf, dev, stream, flush, args) if args.sweep and rank == 0 else None
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
     tune = run_autotune(dev, stream) if args.gradient and rank == 0 else None
@@ -370,6 +372,10 @@ def run_ours(args):
         line["solve"] = solves
     if shifted is not None:
         line["shifted_j8"] = shifted
+    if multi is not None:
+        line["multi_rhs"] = multi
+    if sweep is not None:
+        line["sweep_batch"] = sweep
     if batch is not None:
         line["batch"] = batch
     if grad is not None:
@@ -387,6 +393,121 @@ def run_ours(args):
     if not args.no_cpu_baseline and ws >= 1:
         line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
     print(json.dumps(line), flush=True)
+
+
+def run_sweep(sgf, dev, stream, flush, args):
+    """The batched sweep, bounded to one surface per period: Gaussian rough surfaces of periods 10,
+    25, 50, 100 (N = 2048 ... 16384), each at 16 of the 64 incidence angles (every 4th) and at 4 of
+    the 16 Wood wavenumbers (w = 1, 5, 9, 13), mixed precision: 80 problems. Timed two ways: one
+    batch over all 80 (one graph launch per application of every problem) and one batch per surface
+    and wavenumber (where the angles of a surface may take the multi-column form). Solves: lockstep
+    GMRES of every batch to 1e-8."""
+    import torch
+
+    t0 = time.perf_counter()
+    groups = []
+    for pi in range(len(inputs.SWEEP_SURFACES)):
+        ang = [sgf.Operator(inputs.wl_sweep_angle(pi, 0, i), device=dev.index, stream=stream.cuda_stream,
+                            precision=32) for i in range(0, 64, 4)]
+        wood = [sgf.Operator(inputs.wl_sweep_wood(pi, 0, w), device=dev.index, stream=stream.cuda_stream,
+                             precision=32) for w in (1, 5, 9, 13)]
+        groups.append((ang, wood))
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    ops = [op for a, w in groups for op in a + w]
+    xs = [torch.from_numpy(inputs.random_density(op.par["N"], 90 + p)).to(dev) for p, op in enumerate(ops)]
+    ys = [torch.empty_like(x) for x in xs]
+    steps = max(3, min(args.steps, 20))
+
+    def timed(batches):
+        def once():
+            for b, idx in batches:
+                sgf.sgf_batch_apply(b, [xs[i].data_ptr() for i in idx], [ys[i].data_ptr() for i in idx])
+        for _ in range(3):
+            once()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            once()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    b_all = sgf.sgf_batch_create([op.ctx for op in ops], stream.cuda_stream)
+    ms_all = timed([(b_all, list(range(len(ops))))])
+    sgf.sgf_batch_destroy(b_all)
+    per = []
+    forms = []
+    p0 = 0
+    for ang, wood in groups:
+        for grp in (ang, wood):
+            idx = list(range(p0, p0 + len(grp)))
+            b = sgf.sgf_batch_create([op.ctx for op in grp], stream.cuda_stream)
+            per.append((b, idx))
+            forms.append(int(sgf.sgf_batch_shared_near(b)))
+            p0 += len(grp)
+    ms_per = timed(per)
+    mus = [torch.zeros_like(x) for x in xs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its_all, rr_max, st_all = [], 0.0, 0
+    for b, idx in per:
+        st, its, rr = sgf.sgf_batch_solve(b, 1e-8, 2000, [mus[i].data_ptr() for i in idx])
+        st_all = st_all or st
+        its_all += list(its)
+        rr_max = max(rr_max, float(np.max(rr)))
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    for b, _ in per:
+        sgf.sgf_batch_destroy(b)
+    for op in ops:
+        op.close()
+    n = len(ops)
+    return {"workload": "gaussian rms 0.5 lc 2, periods 10/25/50/100 with N 2048/4096/8192/16384, one surface each, "
+                        "16 angles (every 4th of 64) + 4 Wood wavenumbers (w = 1, 5, 9, 13) per surface",
+            "problems": n, "precision": "mixed", "init_s": t_init,
+            "apply_one_batch": {"value": n * 1000.0 / ms_all, "unit": "matvecs/s", "ms_per_step": ms_all},
+            "apply_per_surface": {"value": n * 1000.0 / ms_per, "unit": "matvecs/s", "ms_per_step": ms_per,
+                                  "forms": forms, "form_legend": "0 child graphs, 1 shared near pass, 2 multi-column"},
+            "solve": {"value": n / t_solve, "unit": "solves/s", "s": t_solve, "tol": 1e-8, "status": st_all,
+                      "applications": its_all, "max_relres": rr_max},
+            "l2": "flushed (256 MiB write) before each timed step"}
+
+
+def run_multi_rhs(sgf, dev, stream, flush, args):
+    """Several densities through the headline operator per call (sgf_apply with nrhs columns): the
+    operator data (P, the near rows, the reconstruction rows) is read once per pass of up to 8
+    columns. Applications per second for nrhs = 1, 8, 64, both precisions."""
+    import torch
+
+    par = workload()
+    out = {}
+    for prec in (32, 64):
+        op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=prec)
+        res = {}
+        for nrhs in (1, 8, 64):
+            X = torch.from_numpy(np.concatenate([inputs.random_density(par["N"], 60 + r) for r in range(nrhs)])).to(dev)
+            Y = torch.empty_like(X)
+            for _ in range(3):
+                sgf.sgf_apply(op.ctx, X.data_ptr(), Y.data_ptr(), nrhs, 0)
+            torch.cuda.synchronize()
+            steps = max(3, min(args.steps, 20))
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                sgf.sgf_apply(op.ctx, X.data_ptr(), Y.data_ptr(), nrhs, 0)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            res[str(nrhs)] = {"value": nrhs * 1000.0 / ms, "unit": "matvecs/s", "ms_per_call": ms}
+        op.close()
+        out["mixed" if prec == 32 else "fp64"] = res
+    out["note"] = ("nrhs = 1 is the single-density path (captured graph); nrhs > 1 the multi-column path "
+                   "(direct launches, 8 columns per pass)")
+    return out
 
 
 def run_shifted(sgf, dev, stream, flush, args):
@@ -512,42 +633,99 @@ def run_field(dev, stream, n_side=256):
             "s_per_call": t, "value": len(xy) / t, "unit": "targets/s", "precision": "fp64"}
 
 
+def _table_rows():
+    """The paper's table rows (golden fixtures the tests use): sinusoid tables of Section 6.2 and the
+    composite-surface convergence table of Section 6.1, as (label, profile, k, theta_deg, N, j, h,
+    n_per, lambda, max|f'|, paper eps, paper s/iter or None, paper iters or None)."""
+    root = os.path.dirname(os.path.abspath(__file__))
+    rows = []
+    for ln in open(os.path.join(root, "tests", "golden", "sinusoid_littrow_energy_error.txt")):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        r = ln.split()
+        Hd, dl, N, hl, n_per = float(r[0]), float(r[2]), int(r[3]), float(r[4]), int(r[5])
+        d = 2 * math.pi
+        lam = d / dl
+        H = Hd * d
+        prof = {"d": d, "a": np.zeros(2), "b": np.array([0.0, H / 2])}
+        shifted = hl > 0
+        rows.append((f"sinusoid H/d={Hd} d/lambda={dl}", prof, dl, math.degrees(math.asin(1 / 3)), N,
+                     8 if shifted else 0, hl * lam if shifted else 0.5, n_per, lam, math.pi * Hd,
+                     float(r[8]), float(r[6]), int(r[7])))
+    comp = {"d": 2 * math.pi, "a": np.zeros(5), "b": -0.25 * np.array([0.0, 1.0, 1 / 2, 1 / 3, 1 / 4])}
+    slope = 0.25 * (1 + 1 + 1 + 1)
+    for ln in open(os.path.join(root, "tests", "golden", "composite_surface_energy_error.txt")):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        r = ln.split()
+        N, n_per = int(r[0]), int(r[1])
+        kw = 6.0 / (1.0 - math.sin(math.radians(45.0)))
+        rows.append((f"composite k=20 N={N}", comp, 20.0, 45.0, N, 0, 0.5, n_per, 2 * math.pi / 20.0, slope,
+                     float(r[2]), None, None))
+        rows.append((f"composite Wood N={N}", comp, kw, 45.0, N, 8, 0.16, n_per, 2 * math.pi / kw, slope,
+                     float(r[3]), None, None))
+    return rows
+
+
 def run_tables(dev, stream):
-    """The sinusoid tables of Section 6.2 (Littrow mount, H = d/4, d/2, d; non-Wood j = 0 and Wood
-    j = 8 rows) with the dense unaccelerated operator at the paper's N and twice its n_per: energy
-    error, GMRES iterations and time per application beside the paper's single-core values (read
-    from the golden fixture the tests use)."""
+    """The paper's tables (Section 6.1 composite-surface convergence, Section 6.2 sinusoid gratings)
+    with the accelerated operator (cells L <= 0.45 lambda, N rounded up to a multiple of the cell
+    columns, FP64, GMRES to 1e-12, twice the paper's n_per) and, for the sinusoids, with the dense
+    unaccelerated operator at the paper's N: energy error, iterations and time per iteration beside
+    the paper's single-core values."""
     import torch
 
     from paper_1707_04950_gb300 import sgf
 
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
-                        "sinusoid_littrow_energy_error.txt")
-    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
     out = []
-    for r in rows:
-        Hd, dl, N, hl, n_per = float(r[0]), float(r[2]), int(r[3]), float(r[4]), int(r[5])
-        par = inputs.wl_littrow(Hd, dl, N, hl, 2 * n_per)
-        ctx = sgf.sgf_create(dev.index, stream.cuda_stream)
-        sgf.sgf_set_profile_fourier(ctx, par["d"], par["a"], par["b"])
-        sgf.sgf_set_wave(ctx, par["k"], par["theta"], par["bc"])
-        sgf.sgf_set_params(ctx, sgf.params_from(par, 64))
-        t0 = time.perf_counter()
-        sgf.sgf_build_exact(ctx)
-        t_init = time.perf_counter() - t0
-        sgf.sgf_select_operator(ctx, 1)
-        mu = torch.zeros(N, dtype=torch.complex128, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, its, rr = sgf.sgf_solve(ctx, 1e-12, 2000, mu.data_ptr())
-        torch.cuda.synchronize()
-        t_solve = time.perf_counter() - t0
-        _, _, eps = sgf.sgf_rayleigh(ctx, mu.data_ptr(), -60, 60)
-        sgf.sgf_destroy(ctx)
-        out.append({"H_over_d": Hd, "d_over_lambda": dl, "N": N, "j": 8 if hl > 0 else 0, "n_per": 2 * n_per,
-                    "eps": abs(eps), "paper_eps": float(r[8]), "iters": its, "paper_iters": int(r[7]),
-                    "relres": rr, "status": st, "init_s": t_init, "s_per_iter": t_solve / max(1, its),
-                    "paper_s_per_iter": float(r[6])})
+    for (label, prof, k, th, N, j, h, n_per, lam, slope, peps, pit_s, pits) in _table_rows():
+        row = {"row": label, "paper_eps": peps, "paper_s_per_iter": pit_s, "paper_iters": pits}
+        try:
+            par = inputs.accel_table_params(prof, k, th, N, j, h, 2 * n_per, lam, slope)
+        except ValueError as e:
+            row["accelerated"] = {"skipped": str(e)}
+            par = None
+        try:
+            if par is None:
+                raise LookupError
+            op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=64)
+            mu = torch.zeros(par["N"], dtype=torch.complex128, device=dev)
+            sgf.sgf_solve(op.ctx, 1e-12, 2000, mu.data_ptr())
+            mu.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 2000, mu.data_ptr())
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            _, _, eps = sgf.sgf_rayleigh(op.ctx, mu.data_ptr(), -60, 60)
+            op.close()
+            row["accelerated"] = {"N": par["N"], "cells": par["nx"], "eps": abs(eps), "iters": its, "relres": rr,
+                                  "status": st, "s_per_iter": t / max(1, its)}
+        except LookupError:
+            pass
+        except sgf.SgfError as e:
+            row["accelerated"] = {"N": par["N"], "error": str(e)}
+        if label.startswith("sinusoid"):
+            dl = k
+            Hd = 2 * prof["b"][1] / prof["d"]
+            parx = inputs.wl_littrow(Hd, dl, N, h / lam if j else 0.0, 2 * n_per)
+            ctx = sgf.sgf_create(dev.index, stream.cuda_stream)
+            sgf.sgf_set_profile_fourier(ctx, parx["d"], parx["a"], parx["b"])
+            sgf.sgf_set_wave(ctx, parx["k"], parx["theta"], parx["bc"])
+            sgf.sgf_set_params(ctx, sgf.params_from(parx, 64))
+            sgf.sgf_build_exact(ctx)
+            sgf.sgf_select_operator(ctx, 1)
+            mu = torch.zeros(N, dtype=torch.complex128, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its, rr = sgf.sgf_solve(ctx, 1e-12, 2000, mu.data_ptr())
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            _, _, eps = sgf.sgf_rayleigh(ctx, mu.data_ptr(), -60, 60)
+            sgf.sgf_destroy(ctx)
+            row["dense"] = {"N": N, "eps": abs(eps), "iters": its, "relres": rr, "status": st,
+                            "s_per_iter": t / max(1, its)}
+        out.append(row)
     return out
 
 
@@ -834,9 +1012,11 @@ def main():
     ap.add_argument("--batch", type=int, default=16, help="problems of the batched block (0: skip)")
     ap.add_argument("--solve", type=int, default=1, help="1: time the headline FP64 and mixed solves")
     ap.add_argument("--shifted", type=int, default=1, help="1: time the j = 8 shifted kernel on the same geometry")
+    ap.add_argument("--multi", type=int, default=1, help="1: time several densities per call (nrhs 1, 8, 64)")
+    ap.add_argument("--sweep", type=int, default=1, help="1: the batched angle/Wood sweep over four surfaces")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
     ap.add_argument("--tables", type=int, default=0,
-                    help="1: the sinusoid tables of Section 6.2 with the dense operator (about a minute)")
+                    help="1: the paper's composite and sinusoid tables, accelerated and dense operators")
     ap.add_argument("--field", type=int, default=1,
                     help="1: time the scattered-field image and the dense unaccelerated operator blocks")
     ap.add_argument("--gemv-worker", nargs=4, help=argparse.SUPPRESS)

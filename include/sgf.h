@@ -233,14 +233,18 @@ typedef struct sgf_batch sgf_batch;
  * On failure *out still receives a batch whose sgf_batch_last_error() explains it; destroy it. */
 sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* cuda_stream);
 
-/* 1 if the batch shares one near operator among its problems, 0 otherwise. sgf_batch_create turns
- * this on when all problems have the same profile, wavenumber, boundary condition and parameters
- * and differ only in the incidence angle: their near operators then differ only by the
- * quasi-periodic phase e^{i alpha d w} of each block's period copy w, so one pass over the first
- * problem's blocks (with the phase applied to the densities) serves every angle, and the rest of
- * each forward map runs as before. The shared pass follows the problems' far-field work instead of
- * overlapping it, so sgf_batch_create times both forms on the eligible batch and keeps the faster;
- * the environment variable SGF_BATCH_SHARED=1 (or 0) forces the shared (or separate) form. */
+/* Which form the batch runs: 0 every problem's own forward map (child graphs side by side); 1 the
+ * same with one near operator shared among the problems; 2 the multi-column form. Forms 1 and 2
+ * apply when all problems have the same profile, wavenumber, boundary condition and parameters
+ * and differ only in the incidence angle (Algorithm 1 over several alpha on one surface): the
+ * projection P_q and the cell reconstruction rows do not depend on alpha (the twists e^{-i alpha x}
+ * of the scatter and e^{i alpha x} of the samples are applied per problem), and the near operators
+ * differ only by the quasi-periodic phase e^{i alpha d w} of each block's period copy w. Form 1
+ * makes one pass over the first problem's near blocks for every angle; form 2 runs the whole forward
+ * map on up to 8 problems per pass: P, the near rows and the reconstruction rows read once for
+ * all of them, each problem's spectra, twists and mode factors per column (the first problem's
+ * precision for all). sgf_batch_create times the eligible forms and keeps the fastest; the
+ * environment variables SGF_BATCH_SHARED=1 (or 0) and SGF_BATCH_MULTI=1 (or 0) force a form. */
 int sgf_batch_shared_near(const sgf_batch* batch);
 void sgf_batch_destroy(sgf_batch* batch);
 const char* sgf_batch_last_error(const sgf_batch* batch);
@@ -266,7 +270,10 @@ sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out);
  * Section 5.1: a < L, non-resonant cells). For the profile, wave and parameters set, tries each cell
  * count nx_list[i] (cells of side L = d/nx) with the quantities tied to L re-derived: box bottom
  * hmin = min f - L/2 and rows ny = floor((max f - hmin)/L) + 1, singular window
- * Ma = floor(0.75 L/dx), shift h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p and h0 the shift set.
+ * Ma = floor(0.75 L/dx); with shifts (j > 0) the shift follows the rule of sgf_suggest_params:
+ * h0 = max(h set, 1.2 a max|f'|) (clear of the singular window, Section 5.1), then
+ * h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p (off the grid lags), one dg more if still inside
+ * the window. Start from the parameters sgf_suggest_params gives for the problem.
  * Every candidate that builds is timed over `reps` applications; host ms[i] (may be NULL) receives
  * its time per application in milliseconds, or minus the build status for a candidate that does
  * not build. The context is left built with the fastest (*best_nx; sgf_get_params gives its

@@ -33,6 +33,14 @@ struct sgf_batch {
   cudaEvent_t ev_tab = nullptr;
   bool shared_near = false;  // problems differ only in the incidence angle: one shared near pass
   zd* d_ph = nullptr;        // [problem][period copy -1, 0, 1] phase relative to the first problem
+  // multi-column form (problems differ only in the incidence angle): the first problem's P, near
+  // operator and reconstruction rows serve every problem, MC_MAX problems per pass, with each
+  // problem's spectra (copied side by side), twists and mode factors
+  bool multi = false;
+  std::vector<MultiSpace<double>> ms64;
+  std::vector<MultiSpace<float>> ms32;
+  cplx<double>* K64[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cplx<float>* K32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   std::vector<void*> allocs;
   char err[1024] = {0};
 };
@@ -264,11 +272,26 @@ static sgf_status set_tables(sgf_batch* B, const void* const* a, const void* con
   return SGF_OK;
 }
 
+template <typename T>
+static void free_ms(std::vector<MultiSpace<T>>& v) {
+  for (auto& ms : v) {
+    for (int l = 0; l < 2; ++l) {
+      if (ms.grid[l]) cudaFree(ms.grid[l]);
+      if (ms.accg[l]) cudaFree(ms.accg[l]);
+    }
+    if (ms.mpart) cudaFree(ms.mpart);
+    if (ms.mpart_ff) cudaFree(ms.mpart_ff);
+  }
+  v.clear();
+}
+
 static void free_batch(sgf_batch* B) {
   for (int s = 0; s < 2; ++s) {
     if (B->exec[s]) cudaGraphExecDestroy(B->exec[s]);
     if (B->graph[s]) cudaGraphDestroy(B->graph[s]);
   }
+  free_ms(B->ms64);
+  free_ms(B->ms32);
   for (void* p : B->allocs) cudaFree(p);
   if (B->h_tab) cudaFreeHost(B->h_tab);
   if (B->ev_tab) cudaEventDestroy(B->ev_tab);
@@ -314,6 +337,85 @@ static sgf_status build_batch_graph(sgf_batch* B, int s, bool shared, cudaGraph_
   }
   BCU(cudaGraphInstantiate(xout, graph, cudaGraphInstantiateFlagUseNodePriority));
   *gout = graph;
+  return SGF_OK;
+}
+
+// The multi-column form of graph slot s (0: the problems' own precision, 1: FP64), captured once:
+// each pass of MC_MAX problems runs the first context's multi-column forward map on the problems'
+// staging buffers, the passes on forked streams of their own (each with its own work space).
+template <typename T>
+static sgf_status build_multi_graph(sgf_batch* B, std::vector<MultiSpace<T>>& msv, cplx<T>* (&K)[2][2],
+                                    cudaGraph_t* gout, cudaGraphExec_t* xout) {
+  const int n = B->n;
+  sgf_ctx* c0 = B->ctx[0];
+  constexpr bool F64 = sizeof(T) == 8;
+  const int npass = (n + MC_MAX - 1) / MC_MAX;
+  // spectra of every problem side by side (column r of a pass at K + r kstride)
+  const long kst[2] = {(long)c0->og[0].Px * c0->og[0].Py, (long)c0->og[1].Px * c0->og[1].Py};
+  for (int lam = 0; lam < 2; ++lam)
+    for (int kd = 0; kd < 2; ++kd) {
+      if (!K[lam][kd]) BTRY(balloc(B, &K[lam][kd], (size_t)n * kst[lam]));
+      for (int p = 0; p < n; ++p) {
+        const OpData<T>& od = *reinterpret_cast<const OpData<T>*>(F64 ? (const void*)&B->ctx[p]->o64
+                                                                       : (const void*)&B->ctx[p]->o32);
+        BCU(cudaMemcpyAsync(K[lam][kd] + (size_t)p * kst[lam], od.Khat[lam][kd], kst[lam] * sizeof(cplx<T>),
+                            cudaMemcpyDeviceToDevice, B->stream));
+      }
+    }
+  msv.resize(npass);
+  for (auto& ms : msv) BCU(multi_space<T>(c0, ms));
+  BCU(cudaStreamSynchronize(B->stream));
+  std::vector<cudaStream_t> st(npass, nullptr);
+  std::vector<cudaEvent_t> ev(npass + 1, nullptr);
+  cudaStream_t cap = nullptr;
+  BCU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  for (auto& x : st) BCU(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  for (auto& x : ev) BCU(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[npass], cap);
+    OpData<T>& od0 = *reinterpret_cast<OpData<T>*>(F64 ? (void*)&c0->o64 : (void*)&c0->o32);
+    for (int ps = 0; ps < npass && e == cudaSuccess; ++ps) {
+      cudaStreamWaitEvent(st[ps], ev[npass], 0);
+      MCols<T> cols;
+      const int p0 = ps * MC_MAX;
+      cols.n = std::min(MC_MAX, n - p0);
+      for (int r = 0; r < cols.n; ++r) {
+        sgf_ctx* c = B->ctx[p0 + r];
+        const OpData<T>& od = *reinterpret_cast<const OpData<T>*>(F64 ? (const void*)&c->o64 : (const void*)&c->o32);
+        MCol<T>& cr = cols.c[r];
+        cr.mu = c->d_mu_tmp;
+        cr.out = c->d_out_tmp;
+        cr.src_tw = od.src_tw;
+        cr.dalpha = c->alpha - c0->alpha;
+        cr.MT = c->d_MT;
+        cr.MS = c->d_MS;
+        cr.MTff = c->d_MTff;
+        cr.MSff = c->d_MSff;
+        cr.nm = c->nm;
+      }
+      // this pass's spectra: orientation lam's at K[lam] + p0 kst[lam], then kst[lam] apart (stride -1)
+      const cplx<T>* Kp[2][2];
+      for (int lam = 0; lam < 2; ++lam)
+        for (int kd = 0; kd < 2; ++kd) Kp[lam][kd] = K[lam][kd] + (size_t)p0 * kst[lam];
+      e = apply_multi_t<T>(c0, od0, msv[ps], cols, Kp, -1, st[ps]);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[ps], st[ps]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[ps], 0);
+    }
+    cudaError_t ee = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = ee;
+  }
+  for (auto& x : st) cudaStreamDestroy(x);
+  for (auto& x : ev) cudaEventDestroy(x);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return berr(B, SGF_ECUDA, "capture of the multi-column batch: %s", cudaGetErrorString(e));
+  }
+  BCU(cudaGraphInstantiate(xout, g, 0));
+  *gout = g;
   return SGF_OK;
 }
 
@@ -420,8 +522,55 @@ sgf_status sgf_batch_create(sgf_batch** out, int n, sgf_ctx* const* ctxs, void* 
       cudaGraphDestroy(gpl);
     }
   }
+  // multi-column form: every problem on the same surface (as for the shared near pass) and in one
+  // precision; timed against the child-graph form at creation and kept if faster
+  // (SGF_BATCH_MULTI=0 / 1 forces the choice)
+  bool same_surface = n > 1;
+  for (int p = 1; p < n && same_surface; ++p) {
+    const sgf_ctx* c = B->ctx[p];
+    same_surface = c->N == c0->N && c->d == c0->d && c->k == c0->k && c->bc == c0->bc && c->fa == c0->fa &&
+                   c->fb == c0->fb && same_params(c->prm, c0->prm) && c->nnz == c0->nnz &&
+                   c->n_items == c0->n_items && c->maxW == c0->maxW;
+  }
+  const bool multi_fits = (size_t)MC_MAX * (c0->maxW + 32) * 16 <= 200 * 1024;
+  const char* envm = getenv("SGF_BATCH_MULTI");
+  if (same_surface && multi_fits && !(envm && envm[0] == '0')) {
+    cudaGraph_t gm = nullptr;
+    cudaGraphExec_t xm = nullptr;
+    if (c0->prm.precision == 32)
+      BTRY(build_multi_graph<float>(B, B->ms32, B->K32, &gm, &xm));
+    else
+      BTRY(build_multi_graph<double>(B, B->ms64, B->K64, &gm, &xm));
+    bool keep = envm && envm[0] == '1';
+    if (!keep) {
+      cudaGraph_t go = nullptr;
+      cudaGraphExec_t xo = nullptr;
+      for (int p = 0; p < n; ++p)
+        BCU(cudaMemsetAsync(B->ctx[p]->d_mu_tmp, 0, B->N[p] * sizeof(zd), B->stream));
+      BTRY(build_batch_graph(B, 0, B->shared_near, &go, &xo));
+      double tm = 0, to = 0;
+      BTRY(time_exec(B, xm, &tm));
+      BTRY(time_exec(B, xo, &to));
+      keep = tm < to;
+      cudaGraphExecDestroy(xo);
+      cudaGraphDestroy(go);
+    }
+    if (keep) {
+      B->multi = true;
+      B->graph[0] = gm;
+      B->exec[0] = xm;
+    } else {
+      cudaGraphExecDestroy(xm);
+      cudaGraphDestroy(gm);
+    }
+  }
   for (int s = 0; s < 2; ++s) {
     if (s == 1 && !B->any_mixed) break;
+    if (s == 0 && B->multi) continue;
+    if (s == 1 && B->multi) {  // the FP64 slot of a mixed batch: the multi-column FP64 map
+      BTRY(build_multi_graph<double>(B, B->ms64, B->K64, &B->graph[1], &B->exec[1]));
+      continue;
+    }
     BTRY(build_batch_graph(B, s, B->shared_near, &B->graph[s], &B->exec[s]));
   }
   if (!B->any_mixed) B->exec[1] = nullptr;
@@ -440,7 +589,7 @@ void sgf_batch_destroy(sgf_batch* B) {
 
 const char* sgf_batch_last_error(const sgf_batch* B) { return B ? B->err : "null batch"; }
 
-int sgf_batch_shared_near(const sgf_batch* B) { return B && B->shared_near ? 1 : 0; }
+int sgf_batch_shared_near(const sgf_batch* B) { return B ? (B->multi ? 2 : (B->shared_near ? 1 : 0)) : 0; }
 
 sgf_status sgf_batch_apply(sgf_batch* B, const void* const* mu_devs, void* const* out_devs) {
   if (!B) return SGF_EINVAL;

@@ -48,8 +48,22 @@ static sgf_status dalloc(sgf_ctx* ctx, T** p, size_t count) {
       return set_err(ctx, SGF_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e__)); \
   } while (0)
 
+template <typename T>
+static void free_multi(MultiSpace<T>& ms) {
+  for (int l = 0; l < 2; ++l) {
+    if (ms.grid[l]) cudaFree(ms.grid[l]);
+    if (ms.accg[l]) cudaFree(ms.accg[l]);
+  }
+  if (ms.mpart) cudaFree(ms.mpart);
+  if (ms.mpart_ff) cudaFree(ms.mpart_ff);
+  ms = MultiSpace<T>();
+}
+
 static void free_all(sgf_ctx* ctx) {
   destroy_graphs(ctx);
+  if (ctx->ms64.ready || ctx->ms32.ready) cudaStreamSynchronize(ctx->stream);
+  free_multi(ctx->ms64);
+  free_multi(ctx->ms32);
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   ctx->o64 = OpData<double>();
@@ -805,6 +819,13 @@ extern "C" sgf_status sgf_apply(sgf_ctx* ctx, const void* mu_dev, void* out_dev,
   if (!op_ready(ctx)) return set_err(ctx, SGF_ESTATE, "operator not built");
   if (transpose_conj != 0 && transpose_conj != 1) return set_err(ctx, SGF_EINVAL, "transpose_conj must be 0 or 1");
   if (nrhs < 1 || !mu_dev || !out_dev) return set_err(ctx, SGF_EINVAL, "bad apply arguments");
+  if (nrhs > 1 && !transpose_conj && !ctx->op_exact && !ctx->profiling && ctx->debug_mask == 15) {
+    // several densities: one pass over the operator data per MC_MAX columns
+    cudaError_t e = ctx->prm.precision == 64 ? launch_apply_nrhs64(ctx, (const zd*)mu_dev, (zd*)out_dev, nrhs)
+                                             : launch_apply_nrhs32(ctx, (const zd*)mu_dev, (zd*)out_dev, nrhs);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "multi-column apply: %s", cudaGetErrorString(e));
+    return SGF_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const zd* mu = (const zd*)mu_dev + (size_t)r * ctx->N;
     zd* out = (zd*)out_dev + (size_t)r * ctx->N;
@@ -1434,16 +1455,21 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
   const int N = base.N;
   const double d = ctx->d, dx = d / N;
   // profile at the nodes x_l = l d / N, l = 1..N
-  double fmin = 1e300, fmax = -1e300;
+  double fmin = 1e300, fmax = -1e300, slope = 0;
   for (int l = 1; l <= N; ++l) {
-    double x = l * dx, f = ctx->fa[0];
+    double x = l * dx, f = ctx->fa[0], f1 = 0;
     for (size_t m = 1; m < ctx->fa.size(); ++m) {
-      double t = 2 * SGF_PI * m * x / d;
+      double w = 2 * SGF_PI * m / d, t = w * x;
       f += ctx->fa[m] * std::cos(t) + ctx->fb[m] * std::sin(t);
+      f1 += w * (-ctx->fa[m] * std::sin(t) + ctx->fb[m] * std::cos(t));
     }
     fmin = std::min(fmin, f);
     fmax = std::max(fmax, f);
+    slope = std::max(slope, std::fabs(f1));
   }
+  // the quantities tied to L are re-derived per candidate; with shifts (j > 0) h follows the
+  // parameter rule of sgf_suggest_params: at least the shift set, clear of the singular window
+  // (h >= 1.2 a max|f'|, Section 5.1), moved off the grid lags of the finest spacing L/p
   auto candidate = [&](int nx) {
     sgf_params P = base;
     const double L = d / nx;
@@ -1451,8 +1477,11 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
     P.hmin = fmin - 0.5 * L;
     P.ny = (int)std::floor((fmax - P.hmin) / L) + 1;
     P.Ma = (int)std::floor(0.75 * L / dx + 1e-9);
-    const double dg = L / base.p;
-    P.h = (std::round(base.h / dg) + 1.0 / (base.j + 1)) * dg;
+    const double dg = L / base.p, a_s = P.Ma * dx;
+    double h0 = base.h;
+    if (base.j > 0) h0 = std::max(h0, 1.2 * a_s * slope);
+    P.h = (std::round(h0 / dg) + 1.0 / (std::max(base.j, 1) + 1)) * dg;
+    if (base.j > 0 && !(P.h > a_s * slope)) P.h += dg;
     return P;
   };
   double best = 1e300;

@@ -268,21 +268,25 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // MAXR = 8 (PF) every global read is issued up front: the spectra K_m, K_d go to registers and the
 // zeta column to a second shared buffer by asynchronous copies, both in flight during the first
 // transform.
+// blockIdx.y selects a column set (several densities at once): its grids are gstride apart, its
+// spectra kstride apart (0: shared), its scratch columns Px Py apart.
 template <typename T, int MAXR, bool ACCG>
 __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ zeta,
                          const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int Py, int la, int lb,
-                         int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg) {
+                         int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg, long gstride,
+                         long kstride) {
   constexpr bool PF = !ACCG && MAXR <= 8;
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const long kx = blockIdx.x;
   cplx<T> acc[ACCG ? 1 : MAXR];
   cplx<T> pkm[PF ? MAXR : 1], pkd[PF ? MAXR : 1];
-  cplx<T>* col = xi + kx * nrow;
-  const cplx<T>* colz = zeta + kx * nrow;
-  const cplx<T>* km = Km + kx * Py;
-  const cplx<T>* kd = Kd + kx * Py;
-  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
+  const long cs = blockIdx.y;
+  cplx<T>* col = xi + cs * gstride + kx * nrow;
+  const cplx<T>* colz = zeta + cs * gstride + kx * nrow;
+  const cplx<T>* km = Km + cs * kstride + kx * Py;
+  const cplx<T>* kd = Kd + cs * kstride + kx * Py;
+  cplx<T>* ag = ACCG ? accg + (cs * gridDim.x + kx) * Py : nullptr;
   cplx<T>* s2 = s + splen(Py) + Py;  // PF: the zeta column (after the twiddle table)
   if (PF) {
     for (int i = threadIdx.x; i < Py; i += blockDim.x) {
@@ -374,7 +378,8 @@ __global__ void k_conv_y(cplx<T>* __restrict__ xi, const cplx<T>* __restrict__ z
 template <typename T, int MAXR, bool ACCG>
 __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zeta,
                              const cplx<T>* __restrict__ Km, const cplx<T>* __restrict__ Kd, int Py, int la, int lb,
-                             int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg) {
+                             int nrow, const cplx<T>* __restrict__ twy, cplx<T>* __restrict__ accg, long gstride,
+                             long kstride) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
   const long kx = blockIdx.x;
@@ -385,11 +390,12 @@ __global__ void k_conv_y_adj(cplx<T>* __restrict__ xi, cplx<T>* __restrict__ zet
     for (int i = threadIdx.x; i < Py; i += blockDim.x) tws[i] = twy[i];
     twf = tws;
   }
-  cplx<T>* col = xi + kx * nrow;
-  cplx<T>* colz = zeta + kx * nrow;
-  const cplx<T>* km = Km + kx * Py;
-  const cplx<T>* kd = Kd + kx * Py;
-  cplx<T>* ag = ACCG ? accg + kx * Py : nullptr;
+  const long cs = blockIdx.y;
+  cplx<T>* col = xi + cs * gstride + kx * nrow;
+  cplx<T>* colz = zeta + cs * gstride + kx * nrow;
+  const cplx<T>* km = Km + cs * kstride + kx * Py;
+  const cplx<T>* kd = Kd + cs * kstride + kx * Py;
+  cplx<T>* ag = ACCG ? accg + (cs * gridDim.x + kx) * Py : nullptr;
   for (int i = threadIdx.x; i < Py; i += blockDim.x) s[spad(i)] = (i < nrow) ? col[i] : cplx<T>(0, 0);
   __syncthreads();
   smem_fftn<T, MAXR>(s, Py, la, lb, 1, 1, 0, twf, Py, -1);

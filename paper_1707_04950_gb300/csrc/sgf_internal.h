@@ -36,6 +36,36 @@ struct OpData {
   cplx<T>* accg[2] = {nullptr, nullptr};  // [lam] Y-convolution scratch [Px][Py] (FP64, long columns)
 };
 
+// Per-column data of the multi-column forward map: the column's density and output, and what
+// depends on its problem's incidence angle (the scatter twist, alpha relative to the operator's, the
+// completion-mode factors). Passed by value (MC_MAX columns per launch).
+constexpr int MC_MAX = 8;
+template <typename T>
+struct MCol {
+  const zd* mu = nullptr;
+  zd* out = nullptr;
+  const cplx<T>* src_tw = nullptr;
+  double dalpha = 0.0;
+  const zd* MT = nullptr;
+  const zd* MS = nullptr;
+  const float4* MTff = nullptr;
+  const float4* MSff = nullptr;
+  int nm = 0;
+};
+template <typename T>
+struct MCols {
+  MCol<T> c[MC_MAX];
+  int n = 0;
+};
+template <typename T>
+struct MultiSpace {
+  cplx<T>* grid[2] = {nullptr, nullptr};
+  cplx<T>* accg[2] = {nullptr, nullptr};
+  zd* mpart = nullptr;
+  float4* mpart_ff = nullptr;
+  bool ready = false;
+};
+
 // One captured forward map: the kernel nodes that take mu/out are updated before each launch.
 struct GraphSlot {
   cudaGraph_t g = nullptr;
@@ -128,6 +158,8 @@ struct sgf_ctx {
   // precision-specific operator data
   OpData<double> o64;
   OpData<float> o32;
+  MultiSpace<double> ms64;  // multi-column forward map work space (allocated on first use)
+  MultiSpace<float> ms32;
   // FP64 kernel-table copies before the Y transform (testing)
   zd* d_Tx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   // workspace
@@ -203,6 +235,17 @@ cudaError_t launch_conj(const zd* x, zd* y, long n, cudaStream_t s);
 cudaError_t launch_grad_acc(zd* g, double s, const zd* a, const zd* u, const zd* v, long n, cudaStream_t st);
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out);
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out);
+// the multi-column forward map of the operator in c (its P, near operator and reconstruction rows)
+// on the columns `cols`, with column r's spectra at Khat + r kstride; the work space is allocated by
+// multi_space (before any stream capture)
+template <typename T>
+cudaError_t multi_space(sgf_ctx* c, MultiSpace<T>& ms);
+template <typename T>
+cudaError_t apply_multi_t(sgf_ctx* c, OpData<T>& od, MultiSpace<T>& ms, const MCols<T>& cols,
+                          const cplx<T>* const Khat[2][2], long kstride, cudaStream_t s);
+// nrhs densities (columns N apart) in passes of up to MC_MAX columns
+cudaError_t launch_apply_nrhs64(sgf_ctx* c, const zd* mu, zd* out, int nrhs);
+cudaError_t launch_apply_nrhs32(sgf_ctx* c, const zd* mu, zd* out, int nrhs);
 cudaError_t launch_far_grids64(sgf_ctx* c, const zd* mu);
 // the dense unaccelerated operator (sgf_exact.cu): entries of d_Aex; y = A x or A^H x
 cudaError_t launch_exact_entries(sgf_ctx* c, zd hk);

@@ -483,19 +483,19 @@ static int fftx_regs() {
 // chains in each stage) whenever the block stays within 1024 threads and the register file.
 template <typename T>
 static cudaError_t run_fft_x(cplx<T>* g, const Orient& o, int nrow, int narr, const cplx<T>* tw, int twlog, int dir,
-                             cudaStream_t s) {
+                             cudaStream_t s, long arr_stride = 0) {
   int ty = fftx_ty(o.Px, nrow, sizeof(cplx<T>));
   size_t sm = fftx_smem(o.Px, ty, sizeof(cplx<T>));
   dim3 grid(ceil_div(nrow, ty), narr);
+  if (arr_stride == 0) arr_stride = (long)o.Px * nrow;
   int t8 = fftx_threads(o.Px, ty, 8);
   const bool fits8 = t8 <= 1024 && (long)fftx_regs<T, 8>() * t8 <= 65536;
   if (o.force_vpt ? o.force_vpt == 8 : fits8) {
     cudaFuncSetAttribute(k_fft_x<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_fft_x<T, 8><<<grid, t8, sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog, dir);
+    k_fft_x<T, 8><<<grid, t8, sm, s>>>(g, o.logPx, nrow, ty, arr_stride, tw, twlog, dir);
   } else {
     cudaFuncSetAttribute(k_fft_x<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_fft_x<T, 16><<<grid, fftx_threads(o.Px, ty, 16), sm, s>>>(g, o.logPx, nrow, ty, (long)o.Px * nrow, tw, twlog,
-                                                                dir);
+    k_fft_x<T, 16><<<grid, fftx_threads(o.Px, ty, 16), sm, s>>>(g, o.logPx, nrow, ty, arr_stride, tw, twlog, dir);
   }
   return cudaGetLastError();
 }
@@ -990,8 +990,10 @@ __global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restr
 // block. It needs nothing but mu, so it runs beside the projection and the FFT convolution; the
 // far-field and mode terms are added afterwards by k_interp_far. T = double: FP64. T = float:
 // float-float on the FP32 pipes, converted to FP64 at the store.
+// Launch bounds: six 256-thread blocks per SM for the float-float path (40 registers), so that the
+// ~800 work items of the N = 16384 workload run in one wave with 48 warps per SM in flight.
 template <typename T>
-__global__ void k_near_rows(int mask, double half_sigma, const int* __restrict__ cell_start,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_near_rows(int mask, double half_sigma, const int* __restrict__ cell_start,
                             const int* __restrict__ node_idx, const int* __restrict__ cols,
                             const int* __restrict__ coloff, const long* __restrict__ cell_off,
                             const int* __restrict__ cell_W, const zd* __restrict__ C, const float4* __restrict__ Cff,
@@ -1023,21 +1025,19 @@ __global__ void k_near_rows(int mask, double half_sigma, const int* __restrict__
       dot2c a = {0.f, 0.f, 0.f, 0.f};
       if (mask & 2) {
         const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
-        dot2c b = {0.f, 0.f, 0.f, 0.f}, c2 = {0.f, 0.f, 0.f, 0.f}, d2 = {0.f, 0.f, 0.f, 0.f};
-        for (int c0 = lane; c0 < W; c0 += 256) {  // up to eight loads in flight per lane
-          float4 v[8];
+        dot2c b = {0.f, 0.f, 0.f, 0.f};
+        for (int c0 = lane; c0 < W; c0 += 128) {  // four loads in flight per lane, two chains
+          float4 v[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < 4; ++u)
             if (c0 + 32 * u < W) v[u] = Cr[c0 + 32 * u];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 4; ++u) {
             const int cc = c0 + 32 * u;
-            if (cc < W) dot2_mac(v[u], musf[cc], (u & 3) == 0 ? a : (u & 3) == 1 ? b : (u & 3) == 2 ? c2 : d2);
+            if (cc < W) dot2_mac(v[u], musf[cc], (u & 1) ? b : a);
           }
         }
         dot2_merge(a, b);
-        dot2_merge(c2, d2);
-        dot2_merge(a, c2);
         for (int o = 16; o > 0; o >>= 1) {
           dot2c t = {__shfl_down_sync(0xffffffffu, a.sr, o), __shfl_down_sync(0xffffffffu, a.si, o),
                      __shfl_down_sync(0xffffffffu, a.er, o), __shfl_down_sync(0xffffffffu, a.ei, o)};
@@ -1250,32 +1250,42 @@ int conv_y_variant_of(const Orient& o, int precision, bool adjoint) {
 // One launch of the Y convolution (ADJ: its adjoint) with the variant chosen by conv_y_variant.
 template <typename T, bool ADJ, int VPT, bool ACCG>
 static void conv_launch(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
-                        const cplx<T>* twy, cplx<T>* accg, int threads, cudaStream_t s) {
+                        const cplx<T>* twy, cplx<T>* accg, int threads, cudaStream_t s, int nset, long gstride,
+                        long kstride) {
   // column (+ twiddle table) (+ the prefetched zeta column of the forward 8-value variant)
   const size_t col = (size_t)splen(o.Py) * sizeof(cplx<T>), twb = (size_t)o.Py * sizeof(cplx<T>);
   size_t sm = ACCG ? col : col + twb + (!ADJ && VPT <= 8 ? col : 0);
+  const dim3 grid(o.Px, nset);
   if (ADJ) {
     cudaFuncSetAttribute(k_conv_y_adj<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y_adj<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
+    k_conv_y_adj<T, VPT, ACCG><<<grid, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg,
+                                                          gstride, kstride);
   } else {
     cudaFuncSetAttribute(k_conv_y<T, VPT, ACCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_y<T, VPT, ACCG><<<o.Px, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg);
+    k_conv_y<T, VPT, ACCG><<<grid, threads, sm, s>>>(xi, zeta, Km, Kd, o.Py, o.la, o.lb, o.nrow, twy, accg,
+                                                      gstride, kstride);
   }
 }
 
+// nset column sets (densities) at once: grids gstride apart, spectra kstride apart (0: shared),
+// the global-scratch variant's columns Px Py apart.
 template <typename T, bool ADJ>
 static cudaError_t conv_y_any(cplx<T>* xi, cplx<T>* zeta, const cplx<T>* Km, const cplx<T>* Kd, const Orient& o,
-                              const cplx<T>* twy, cplx<T>* accg, cudaStream_t s) {
+                              const cplx<T>* twy, cplx<T>* accg, cudaStream_t s, int nset = 1, long gstride = 0,
+                              long kstride = 0) {
   switch (o.force_conv ? o.force_conv : conv_y_variant<T, ADJ>(o)) {
     case 3:
-      conv_launch<T, ADJ, 8, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 8, o.lb), s);
+      conv_launch<T, ADJ, 8, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 8, o.lb), s, nset, gstride,
+                                    kstride);
       break;
     case 1:
-      conv_launch<T, ADJ, 16, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 16, o.lb), s);
+      conv_launch<T, ADJ, 16, false>(xi, zeta, Km, Kd, o, twy, nullptr, conv_threads(o.Py, 16, o.lb), s, nset,
+                                     gstride, kstride);
       break;
     case 2:
       if (!accg) return cudaErrorInvalidValue;
-      conv_launch<T, ADJ, 16, true>(xi, zeta, Km, Kd, o, twy, accg, conv_threads(o.Py, 16, o.lb), s);
+      conv_launch<T, ADJ, 16, true>(xi, zeta, Km, Kd, o, twy, accg, conv_threads(o.Py, 16, o.lb), s, nset, gstride,
+                                    kstride);
       break;
     default:
       return cudaErrorInvalidValue;
@@ -1378,6 +1388,366 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
 
 cudaError_t launch_apply64(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<double>(c, c->o64, mu, out); }
 cudaError_t launch_apply32(sgf_ctx* c, const zd* mu, zd* out) { return apply_t<float>(c, c->o32, mu, out); }
+
+// ============================================================== several densities at once
+// The forward map on up to MC_MAX density columns in one pass over the operator data: the
+// projection stages each chunk's P block in shared memory once for all columns, the near rows read
+// each block-sparse row once for all columns, the reconstruction rows stay in registers across
+// columns; the X passes and Y convolutions run every column's grids in one launch. Columns may
+// belong to problems that differ only in the incidence angle (same surface, wavenumber and
+// parameters): P, the reconstruction rows and the near operator are then shared, and the angle
+// enters through per-column twists, phases, spectra and mode factors (MCol).
+
+// Shared memory of k_near_multi: ncol staged density columns of W entries plus ncol results per row.
+static size_t near_multi_smem(int maxW, int ncol, size_t esz) { return ((size_t)ncol * maxW + 32 * ncol) * esz; }
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_project_multi(int neq, long N, const int* __restrict__ cell_start,
+                                                       const int* __restrict__ node_idx, const cplx<T>* __restrict__ P,
+                                                       const int* __restrict__ src_gidx, MCols<T> cols,
+                                                       cplx<T>* __restrict__ gH, long gH_stride, cplx<T>* __restrict__ gV,
+                                                       long gV_stride, zd* __restrict__ mpart, float4* __restrict__ mpart_ff,
+                                                       long mp_col, int MB, int nm_max, int n_items,
+                                                       const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                                                       const int* __restrict__ item_hi) {
+  extern __shared__ unsigned char smem_raw[];
+  if ((int)blockIdx.x >= n_items) {  // mode partials: (column, mode, chunk)
+    const int t = blockIdx.x - n_items;
+    const int r = t / (nm_max * MB), rem = t % (nm_max * MB);
+    const MCol<T>& cr = cols.c[r];
+    if (rem / MB < cr.nm)
+      mode_partial<T>(rem / MB, rem % MB, MB, N, cr.mu, cr.MS, cr.MSff, mpart + r * mp_col, mpart_ff + r * mp_col);
+    return;
+  }
+  const int nout = 4 * neq;
+  cplx<T>* Ps = reinterpret_cast<cplx<T>*>(smem_raw);  // [nq][nout] of this chunk
+  cplx<T>* mus = Ps + 32 * nout;                       // [32] densities of one column
+  const int q = item_cell[blockIdx.x];
+  const int lo = item_lo[blockIdx.x], nq = item_hi[blockIdx.x] - lo;
+  const int s0 = cell_start[q] + lo;
+  for (int e = threadIdx.x; e < nq * nout; e += blockDim.x) Ps[e] = P[(long)nout * s0 + e];
+  const int o = threadIdx.x;
+  long idx = 0, goff = 0;
+  int lam = 0;
+  if (o < nout) {
+    lam = o / (2 * neq);
+    const int sidx = o % (2 * neq), si = sidx % neq;
+    idx = ((long)q * 2 + lam) * neq + si;
+    goff = (sidx < neq ? 0 : (lam == 0 ? gH_stride : gV_stride)) + src_gidx[idx];
+  }
+  for (int r = 0; r < cols.n; ++r) {
+    __syncthreads();  // Ps staged; the previous column's densities consumed
+    for (int l = threadIdx.x; l < nq; l += blockDim.x) mus[l] = cplx<T>(cols.c[r].mu[node_idx[s0 + l]]);
+    __syncthreads();
+    if (o < nout) {
+      cplx<T> acc[4] = {cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0), cplx<T>(0, 0)};
+      for (int u = 0; u < nq; ++u) acc[u & 3] = fma_c(Ps[u * nout + o], mus[u], acc[u & 3]);
+      const cplx<T> v = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * cols.c[r].src_tw[idx];
+      cplx<T>* dst = (lam == 0 ? gH + r * 2 * gH_stride : gV + r * 2 * gV_stride) + goff;
+      atomicAdd(&dst->re, v.re);
+      atomicAdd(&dst->im, v.im);
+    }
+  }
+}
+
+// The block-sparse near rows plus the sigma/2 identity for ncol columns: each staged density of a
+// wrapped source cell carries its column's quasi-periodic phase relative to the operator's
+// (e^{i (alpha_col - alpha) d wrap}); each row of C is read once for all columns.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_near_multi(double half_sigma, double d, const int* __restrict__ cell_start,
+                                                    const int* __restrict__ node_idx, const int* __restrict__ cols_idx,
+                                                    const int* __restrict__ coloff, const signed char* __restrict__ colwrap,
+                                                    const long* __restrict__ cell_off, const int* __restrict__ cell_W,
+                                                    const zd* __restrict__ C, const float4* __restrict__ Cff,
+                                                    const int* __restrict__ item_cell, const int* __restrict__ item_lo,
+                                                    const int* __restrict__ item_hi, MCols<T> cols) {
+  constexpr bool FF = sizeof(T) == 4;
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  const int W = cell_W[q], nc = cols.n;
+  zd* mus = reinterpret_cast<zd*>(smem_raw);        // [nc][W] (FP64) or float4 pairs (float-float)
+  float4* musf = reinterpret_cast<float4*>(smem_raw);
+  zd* resd = mus + (long)nc * W;                    // [nq][nc]
+  float4* resf = musf + (long)nc * W;
+  const int* cq = cols_idx + coloff[q];
+  const signed char* wq = colwrap + coloff[q];
+  for (int e = threadIdx.x; e < nc * W; e += blockDim.x) {
+    const int r = e / W, cc = e - r * W;
+    zd m = cols.c[r].mu[cq[cc]];
+    const int w = wq[cc];
+    if (w != 0 && cols.c[r].dalpha != 0.0) m = m * expi(cols.c[r].dalpha * d * w);
+    if (FF)
+      musf[e] = cff_from(m);
+    else
+      mus[e] = m;
+  }
+  __syncthreads();
+  for (int il = warp; il < nq; il += nw) {
+    if (FF) {
+      dot2c a[NC];
+#pragma unroll
+      for (int r = 0; r < NC; ++r) a[r] = {0.f, 0.f, 0.f, 0.f};
+      const float4* Cr = Cff + cell_off[q] + (long)(rlo + il) * W;
+      for (int cc = lane; cc < W; cc += 32) {
+        const float4 v = Cr[cc];
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+          if (r < nc) dot2_mac(v, musf[r * W + cc], a[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NC; ++r) {
+        if (r >= nc) break;
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+          dot2c t = {__shfl_down_sync(0xffffffffu, a[r].sr, o2), __shfl_down_sync(0xffffffffu, a[r].si, o2),
+                     __shfl_down_sync(0xffffffffu, a[r].er, o2), __shfl_down_sync(0xffffffffu, a[r].ei, o2)};
+          dot2_merge(a[r], t);
+        }
+        if (lane == 0) {
+          ff vr = ff_add({a[r].sr, 0.f}, {a[r].er, 0.f}), vi = ff_add({a[r].si, 0.f}, {a[r].ei, 0.f});
+          resf[il * nc + r] = make_float4(vr.hi, vi.hi, vr.lo, vi.lo);
+        }
+      }
+    } else {
+      zd acc[NC];
+#pragma unroll
+      for (int r = 0; r < NC; ++r) acc[r] = zd(0, 0);
+      const zd* Cr = C + cell_off[q] + (long)(rlo + il) * W;
+      for (int cc = lane; cc < W; cc += 32) {
+        const zd v = Cr[cc];
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+          if (r < nc) acc[r] = fma_c(v, mus[r * W + cc], acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NC; ++r) {
+        if (r >= nc) break;
+        const zd t = warp_sum(acc[r]);
+        if (lane == 0) resd[il * nc + r] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
+    const int il = e / nc, r = e - il * nc;
+    const int i = node_idx[s0 + il];
+    const zd mi = cols.c[r].mu[i];
+    zd v;
+    if (FF) {
+      const float4 rr = resf[e];
+      ff vr = {rr.x, rr.z}, vi = {rr.y, rr.w};
+      const float4 m = cff_from(mi);
+      const float hs = (float)half_sigma;  // +-1/2: exact scaling
+      vr = ff_add(vr, {hs * m.x, hs * m.z});
+      vi = ff_add(vi, {hs * m.y, hs * m.w});
+      v = zd(ff_to_double(vr), ff_to_double(vi));
+    } else {
+      v = resd[e] + half_sigma * mi;
+    }
+    cols.c[r].out[i] = v;
+  }
+}
+
+// Combine-lambda + PlaneWaveWeights + NonIntersecting + EvalModes for ncol columns: the block's
+// reconstruction rows are loaded once; each column gathers its cell samples, times the untwist
+// e^{i (alpha_col - alpha) x_t} of sample t relative to the one folded into the rows, and adds its
+// far field and its modes.
+template <typename T>
+__global__ void __launch_bounds__(128) k_interp_multi(int nfit, long N, const int* __restrict__ cell_start,
+                                                      const int* __restrict__ node_idx, const int* __restrict__ samp_gidx,
+                                                      int pH, const cplx<T>* __restrict__ gH, long gH_col,
+                                                      const cplx<T>* __restrict__ gV, long gV_col,
+                                                      const cplx<T>* __restrict__ Ip, const int* __restrict__ occ_cx,
+                                                      double L, const double* __restrict__ samp_rel,
+                                                      const zd* __restrict__ mpart, const float4* __restrict__ mpart_ff,
+                                                      long mp_col, int MB, const int* __restrict__ item_cell,
+                                                      const int* __restrict__ item_lo, const int* __restrict__ item_hi,
+                                                      MCols<T> cols) {
+  constexpr bool FF = sizeof(T) == 4;
+  SGF_SHARED_ARRAY(cplx<T>, ph, 64);
+  SGF_SHARED_ARRAY(cplx<T>, far_s, 32);
+  __shared__ float4 msf[8];
+  SGF_SHARED_ARRAY(zd, msd, 8);
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const int q = item_cell[blockIdx.x];
+  const int rlo = item_lo[blockIdx.x];
+  const int s0 = cell_start[q] + rlo, nq = item_hi[blockIdx.x] - rlo;
+  const int il = threadIdx.x / 4, part = threadIdx.x % 4;
+  cplx<T> ir[16];
+  if (il < nq) {
+    const cplx<T>* Ir = Ip + (long)(s0 + il) * nfit;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (part + 4 * k < nfit) ir[k] = Ir[part + 4 * k];
+  }
+  int irow = 0;
+  if ((int)threadIdx.x < nq) irow = node_idx[s0 + threadIdx.x];
+  const double cxl = occ_cx[q] * L;
+  for (int r = 0; r < cols.n; ++r) {
+    const MCol<T>& cr = cols.c[r];
+    for (int t = threadIdx.x; t < nfit; t += blockDim.x) {
+      const long gi = samp_gidx[(long)q * nfit + t];
+      cplx<T> v = t < 2 * (pH + 1) ? gH[r * gH_col + gi] : gV[r * gV_col + gi];
+      if (cr.dalpha != 0.0) v = v * cplx<T>(expi(cr.dalpha * (cxl + samp_rel[2 * t])));
+      ph[t] = v;
+    }
+    if (warp < cr.nm) {  // mode sums from their chunk partials (warp per mode)
+      if (FF) {
+        ff sr = {0.f, 0.f}, si = {0.f, 0.f};
+        for (int cch = lane; cch < MB; cch += 32) {
+          float4 v = mpart_ff[r * mp_col + warp * MB + cch];
+          sr = ff_add(sr, {v.x, v.z});
+          si = ff_add(si, {v.y, v.w});
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
+          si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
+        }
+        if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+      } else {
+        zd a(0, 0);
+        for (int cch = lane; cch < MB; cch += 32) a += mpart[r * mp_col + warp * MB + cch];
+        a = warp_sum(a);
+        if (lane == 0) msd[warp] = a;
+      }
+    }
+    __syncthreads();
+    cplx<T> far(0, 0);
+    if (il < nq) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (part + 4 * k < nfit) far = fma_c(ir[k], ph[part + 4 * k], far);
+    }
+    for (int o = 2; o > 0; o >>= 1) {
+      far.re += __shfl_down_sync(0xffffffffu, far.re, o);
+      far.im += __shfl_down_sync(0xffffffffu, far.im, o);
+    }
+    if (part == 0 && il < nq) far_s[il] = far;
+    __syncthreads();
+    if ((int)threadIdx.x < nq) {
+      const int i = irow;
+      zd v = cr.out[i] + zd((double)far_s[threadIdx.x].re, (double)far_s[threadIdx.x].im);
+      if (FF) {
+        ff vr = {0.f, 0.f}, vi = {0.f, 0.f};
+        for (int n = 0; n < cr.nm; ++n) cff_mac(cr.MTff[(long)i * cr.nm + n], msf[n], vr, vi);
+        v += zd(ff_to_double(vr), ff_to_double(vi));
+      } else {
+        for (int n = 0; n < cr.nm; ++n) v += cr.MT[(long)i * cr.nm + n] * msd[n];
+      }
+      cr.out[i] = v;
+    }
+    __syncthreads();  // ph, far_s and the mode sums are reused by the next column
+  }
+}
+
+// Multi-column work space of one precision (allocated on first use): grids [col][xi, zeta][Px nrow]
+// per orientation, the global-scratch convolution columns, mode partials [col][mode][chunk].
+template <typename T>
+cudaError_t multi_space(sgf_ctx* c, MultiSpace<T>& ms) {
+  if (ms.ready) return cudaSuccess;
+  cudaError_t e;
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    if ((e = cudaMalloc(&ms.grid[lam], (size_t)MC_MAX * 2 * o.Px * o.nrow * sizeof(cplx<T>))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&ms.accg[lam], (size_t)MC_MAX * o.Px * o.Py * sizeof(cplx<T>))) != cudaSuccess) return e;
+  }
+  const size_t mp = (size_t)MC_MAX * 8 * c->mode_chunks;
+  if ((e = cudaMalloc(&ms.mpart, mp * sizeof(zd))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&ms.mpart_ff, mp * sizeof(float4))) != cudaSuccess) return e;
+  ms.ready = true;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t apply_multi_t(sgf_ctx* c, OpData<T>& od, MultiSpace<T>& ms, const MCols<T>& cols,
+                          const cplx<T>* const Khat[2][2], long kstride, cudaStream_t s) {
+  cudaError_t e = multi_space<T>(c, ms);
+  if (e != cudaSuccess) return e;
+  const int nc = cols.n;
+  if (nc < 1 || nc > MC_MAX) return cudaErrorInvalidValue;
+  int nm_max = 0;
+  for (int r = 0; r < nc; ++r) nm_max = std::max(nm_max, cols.c[r].nm);
+  const long mp_col = 8L * c->mode_chunks;
+  long sz[2];
+  for (int lam = 0; lam < 2; ++lam) {
+    sz[lam] = (long)c->og[lam].Px * c->og[lam].nrow;
+    cudaMemsetAsync(ms.grid[lam], 0, (size_t)nc * 2 * sz[lam] * sizeof(cplx<T>), s);
+  }
+  const int nout = 4 * c->neq;
+  const size_t smp = ((size_t)32 * nout + 32) * sizeof(cplx<T>);
+  cudaFuncSetAttribute(k_project_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+  k_project_multi<T><<<c->n_items + nc * nm_max * c->mode_chunks, 128, smp, s>>>(
+      c->neq, c->N, c->d_cell_start, c->d_node_idx, od.P, c->d_src_gidx, cols, ms.grid[0], sz[0], ms.grid[1], sz[1],
+      ms.mpart, ms.mpart_ff, mp_col, c->mode_chunks, nm_max, c->n_items, c->d_item_cell, c->d_item_lo,
+      c->d_item_hi);
+  for (int lam = 0; lam < 2; ++lam) {
+    const Orient& o = c->og[lam];
+    if ((e = run_fft_x<T>(ms.grid[lam], o, o.nrow, 2 * nc, od.tw, c->twlog, -1, s)) != cudaSuccess) return e;
+    // kstride < 0: every column's spectra side by side, P_x P_y apart in each orientation
+    const long ks = kstride < 0 ? (long)o.Px * o.Py : kstride;
+    if ((e = conv_y_any<T, false>(ms.grid[lam], ms.grid[lam] + sz[lam], Khat[lam][0], Khat[lam][1], o, od.twy[lam],
+                                  ms.accg[lam], s, nc, 2 * sz[lam], ks)) != cudaSuccess)
+      return e;
+    if ((e = run_fft_x<T>(ms.grid[lam], o, o.nrow, nc, od.tw, c->twlog, +1, s, 2 * sz[lam])) != cudaSuccess) return e;
+  }
+  const double hs = c->bc == 0 ? 0.5 : -0.5;
+  const size_t smn = near_multi_smem(c->maxW, nc, sizeof(cplx<T>) == 8 ? sizeof(float4) : sizeof(zd));
+  if (smn > 200 * 1024) return cudaErrorInvalidValue;
+  cudaFuncSetAttribute(k_near_multi<T, MC_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn);
+  k_near_multi<T, MC_MAX><<<c->n_items, 256, smn, s>>>(hs, c->d, c->d_cell_start, c->d_node_idx, c->d_cols,
+                                                        c->d_coloff, c->d_colwrap, c->d_cell_off, c->d_cell_W, c->d_C,
+                                                        c->d_Cff, c->d_item_cell, c->d_item_lo, c->d_item_hi, cols);
+  k_interp_multi<T><<<c->n_items, 128, 0, s>>>(c->nfit, c->N, c->d_cell_start, c->d_node_idx, c->d_samp_gidx, c->prm.p,
+                                               ms.grid[0], 2 * sz[0], ms.grid[1], 2 * sz[1], od.Ip, c->d_occ_cx, c->L,
+                                               c->keep.samp_rel, ms.mpart, ms.mpart_ff, mp_col, c->mode_chunks,
+                                               c->d_item_cell, c->d_item_lo, c->d_item_hi, cols);
+  return cudaGetLastError();
+}
+
+// nrhs densities of one operator (same alpha), MC_MAX columns per pass.
+template <typename T>
+static cudaError_t apply_nrhs_t(sgf_ctx* c, OpData<T>& od, MultiSpace<T>& ms, const zd* mu, zd* out, int nrhs) {
+  const cplx<T>* K[2][2] = {{od.Khat[0][0], od.Khat[0][1]}, {od.Khat[1][0], od.Khat[1][1]}};
+  // columns per pass: MC_MAX, or fewer when the staged densities of the longest near row would not
+  // fit the shared memory
+  const int nc_fit = (int)((200 * 1024) / (16 * ((size_t)c->maxW + 32)));
+  const int chunk = std::max(1, std::min(MC_MAX, nc_fit));
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    MCols<T> cols;
+    cols.n = std::min(chunk, nrhs - r0);
+    for (int r = 0; r < cols.n; ++r) {
+      MCol<T>& cr = cols.c[r];
+      cr.mu = mu + (size_t)(r0 + r) * c->N;
+      cr.out = out + (size_t)(r0 + r) * c->N;
+      cr.src_tw = od.src_tw;
+      cr.dalpha = 0.0;
+      cr.MT = c->d_MT;
+      cr.MS = c->d_MS;
+      cr.MTff = c->d_MTff;
+      cr.MSff = c->d_MSff;
+      cr.nm = c->nm;
+    }
+    cudaError_t e = apply_multi_t<T>(c, od, ms, cols, K, 0, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t multi_space<double>(sgf_ctx*, MultiSpace<double>&);
+template cudaError_t multi_space<float>(sgf_ctx*, MultiSpace<float>&);
+template cudaError_t apply_multi_t<double>(sgf_ctx*, OpData<double>&, MultiSpace<double>&, const MCols<double>&,
+                                           const cplx<double>* const[2][2], long, cudaStream_t);
+template cudaError_t apply_multi_t<float>(sgf_ctx*, OpData<float>&, MultiSpace<float>&, const MCols<float>&,
+                                          const cplx<float>* const[2][2], long, cudaStream_t);
+
+cudaError_t launch_apply_nrhs64(sgf_ctx* c, const zd* mu, zd* out, int nrhs) {
+  return apply_nrhs_t<double>(c, c->o64, c->ms64, mu, out, nrhs);
+}
+cudaError_t launch_apply_nrhs32(sgf_ctx* c, const zd* mu, zd* out, int nrhs) {
+  return apply_nrhs_t<float>(c, c->o32, c->ms32, mu, out, nrhs);
+}
 
 // EqSources + GlobalEqSMerge + GlobalFFT alone, in FP64 on the context's stream: leaves the
 // twisted phi^all of every grid point in o64.grid[lambda] (first array of each orientation) for

@@ -201,6 +201,38 @@ def wl_gaussian_angles(i, N=2048, d=10.0, nx=32, surface_seed=5000, **kw):
     return make_params(prof, 2 * math.pi, 89.0 * i / 63.0, DIRICHLET, N, nx=nx, **kw)
 
 
+# The batched sweep: Gaussian rough surfaces (rms 0.5, correlation length 2) of periods 10, 25, 50,
+# 100 with N = 2048, 4096, 8192, 16384, four surfaces per period (seeds 5000 + 4 i + s), each at 64
+# incidence angles theta = 89 deg i / 63 (k = 2 pi) and at 16 Wood wavenumbers: for theta_w = 5 w
+# deg (w = 1..16) the order n = -round(d (1 + sin theta_w)) meets alpha_n = -k exactly at
+# k = 2 pi |n| / (d (1 + sin theta_w)). Cells: n_x the smallest power of two with L <= 0.45 lambda.
+SWEEP_SURFACES = ((10.0, 2048), (25.0, 4096), (50.0, 8192), (100.0, 16384))
+
+
+def sweep_nx(d, lam=1.0):
+    nx = 4
+    while d / nx > 0.45 * lam:
+        nx *= 2
+    return nx
+
+
+def wl_sweep_angle(period_index, surface, i, **kw):
+    """Problem i (0..63) of the angle sweep on surface `surface` (0..3) of period SWEEP_SURFACES[period_index]."""
+    d, N = SWEEP_SURFACES[period_index]
+    prof = gaussian_surface(d, 0.5, 2.0, 5000 + 4 * period_index + surface)
+    return make_params(prof, 2 * math.pi, 89.0 * i / 63.0, DIRICHLET, N, nx=sweep_nx(d), **kw)
+
+
+def wl_sweep_wood(period_index, surface, w, **kw):
+    """Wood problem w (1..16) of the sweep: theta_w = 5 w deg at the wavenumber where alpha_n = -k."""
+    d, N = SWEEP_SURFACES[period_index]
+    prof = gaussian_surface(d, 0.5, 2.0, 5000 + 4 * period_index + surface)
+    th = 5.0 * w
+    n = -round(d * (1 + math.sin(math.radians(th))))
+    k = 2 * math.pi * abs(n) / (d * (1 + math.sin(math.radians(th))))
+    return make_params(prof, k, th, DIRICHLET, N, nx=sweep_nx(d, 2 * math.pi / k), **kw)
+
+
 def wl_harmonic_gradient(N=4096, d=20.0, n_harm=64, scale=0.05, nx=64, seed=4, **kw):
     """Gradient workload: sum_{m <= 64} c_m cos + s_m sin with c_m, s_m ~ N(0, (0.05/m)^2), period 20,
     k = 2 pi, theta = 20 deg, Dirichlet; the efficiency e_0 is differentiated with respect to the
@@ -249,6 +281,28 @@ def wl_littrow(H_over_d, d_over_lambda, N, h_over_lambda, n_per, **kw):
                       h=h_over_lambda * lam if shifted else 0.5, n_per=n_per, nx=4, hmin=-H, ny=8, **kw)
     dx = d / N
     par["Ma"] = max(2, int(a / dx))
+    par["a_s"] = par["Ma"] * dx
+    par["gamma"] = 0.5 * par["a_s"]
+    return par
+
+
+def accel_table_params(prof, k, theta_deg, N, j, h, n_per, lam, maxslope, ls_reg=1e-10):
+    """Accelerator parameters for one row of the paper's convergence and grating tables (Section
+    6): cells of side L <= 0.45 lambda (n_x a power of two, at least 4), N rounded up to a multiple
+    of n_x, the singular window a = 0.75 L, or less with shifts so that a max|f'| < 0.9 h."""
+    d = prof["d"]
+    nx = 4
+    while d / nx > 0.45 * lam:
+        nx *= 2
+    N = int(math.ceil(N / nx) * nx)
+    par = make_params(prof, k, theta_deg, DIRICHLET, N, nx=nx, j=j, h=h, n_per=n_per, ls_reg=ls_reg)
+    dx = d / N
+    a = 0.75 * par["L"]
+    if j > 0:
+        a = min(a, 0.9 * h / maxslope)
+    if a / dx < 2:
+        raise ValueError(f"N = {N} gives fewer than two nodes in the singular window of {nx} cells")
+    par["Ma"] = int(a / dx)
     par["a_s"] = par["Ma"] * dx
     par["gamma"] = 0.5 * par["a_s"]
     return par

@@ -295,7 +295,8 @@ def sgf_batch_destroy(batch):
 
 
 def sgf_batch_shared_near(batch):
-    return bool(load().sgf_batch_shared_near(batch))
+    """The batch's form: 0 child graphs, 1 shared near pass, 2 multi-column (sgf.h)."""
+    return int(load().sgf_batch_shared_near(batch))
 
 
 def sgf_batch_apply(batch, mu_ptrs, out_ptrs):

@@ -32,3 +32,21 @@ def test_autotune_keeps_fastest_built_candidate_and_matches_oracle():
     op.close()
     ref = ac.Accel(par2).apply(mu)
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_autotune_deep_corrugation_builds_every_candidate_and_keeps_accuracy():
+    # the N = 16384 benchmark workload (j = 0): 64, 128 and 256 cell columns all build (the box,
+    # window and grid are re-derived per candidate), and the solve with the chosen cells still meets
+    # the energy target of the configuration (1e-8)
+    torch = pytest.importorskip("torch")
+    par = I.wl_deep_corrugation_neumann()
+    op = sgf.Operator(par, precision=32)
+    cands = [64, 128, 256]
+    best, ms = sgf.sgf_autotune_cells(op.ctx, cands, reps=20)
+    assert np.all(ms > 0), ms
+    x = torch.zeros(par["N"], dtype=torch.complex128, device="cuda")
+    st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 4000, x.data_ptr())
+    _, _, eps = sgf.sgf_rayleigh(op.ctx, x.data_ptr(), -40, 40)
+    op.close()
+    assert st == 0 and rr <= 1e-12, (best, st, its, rr)
+    assert abs(eps) < 1e-8, (best, eps, ms)

@@ -160,12 +160,14 @@ def test_angle_batch_shares_the_near_operator(prec):
     import os
 
     os.environ["SGF_BATCH_SHARED"] = "1"  # force the shared form (creation otherwise keeps the faster)
+    os.environ["SGF_BATCH_MULTI"] = "0"
     try:
         b = sgf.sgf_batch_create([op.ctx for op in ops])
     finally:
         del os.environ["SGF_BATCH_SHARED"]
+        del os.environ["SGF_BATCH_MULTI"]
     try:
-        assert sgf.sgf_batch_shared_near(b)
+        assert sgf.sgf_batch_shared_near(b) == 1
         sgf.sgf_batch_apply(b, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys])
         torch.cuda.synchronize()
         mus = [torch.zeros(512, dtype=torch.complex128, device="cuda") for _ in ops]
@@ -190,3 +192,49 @@ def test_angle_batch_shares_the_near_operator(prec):
         sgf.sgf_batch_destroy(b)
     o1.close()
     o2.close()
+
+
+def _maxrel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_angle_batch_multi_column_form(prec):
+    # one surface at ten incidence angles in the multi-column form (two passes of at most eight
+    # columns): the first problem's P, near operator and reconstruction rows serve every angle, with
+    # each angle's twists, spectra and mode factors. Every angle must match its own forward map
+    # (FP64 1e-11 element-wise: the alpha phases are formed as a product of the first angle's and a
+    # relative one; mixed: the FP32 far field's summation order, 5e-5) and the oracle's Algorithm 3
+    # built for that angle (1e-9 / 5e-5 element-wise)
+    import os
+
+    thetas = [30.0, 10.0, 45.0, 60.0, 5.0, 20.0, 35.0, 50.0, 15.0, 25.0]
+    pars = [I.make_params(I.sinusoid(2.0, 0.25), 2 * np.pi, t, 0, 512, nx=16, ny=16, hmin=-1.0) for t in thetas]
+    ops = [sgf.Operator(par, precision=prec) for par in pars]
+    xs = [_dev(I.random_density(512, 60 + p)) for p in range(len(ops))]
+    ys = [torch.empty_like(x) for x in xs]
+    os.environ["SGF_BATCH_MULTI"] = "1"
+    try:
+        b = sgf.sgf_batch_create([op.ctx for op in ops])
+    finally:
+        del os.environ["SGF_BATCH_MULTI"]
+    try:
+        assert sgf.sgf_batch_shared_near(b) == 2
+        sgf.sgf_batch_apply(b, [x.data_ptr() for x in xs], [y.data_ptr() for y in ys])
+        torch.cuda.synchronize()
+        mus = [torch.zeros(512, dtype=torch.complex128, device="cuda") for _ in ops]
+        st, its, rr = sgf.sgf_batch_solve(b, 1e-11, 2000, [m.data_ptr() for m in mus])
+    finally:
+        sgf.sgf_batch_destroy(b)
+    assert st == 0 and np.all(rr <= 1e-11)
+    tol = 1e-11 if prec == 64 else 5e-5
+    for p, (op, x, y, m) in enumerate(zip(ops, xs, ys, mus)):
+        yh = y.cpu().numpy()
+        assert _maxrel(yh, _single_apply(op, x.cpu().numpy())) < tol, p
+        if p in (0, 3, 9):
+            ref = ac.Accel(pars[p]).apply(x.cpu().numpy())
+            assert _maxrel(yh, ref) < (1e-9 if prec == 64 else 5e-5), p
+        sol = torch.zeros(512, dtype=torch.complex128, device="cuda")
+        assert sgf.sgf_solve(op.ctx, 1e-11, 2000, sol.data_ptr())[0] == 0
+        assert _rel(m.cpu().numpy(), sol.cpu().numpy()) < (1e-8 if prec == 64 else 1e-6)
+        op.close()
