@@ -35,13 +35,14 @@ def test_autotune_keeps_fastest_built_candidate_and_matches_oracle():
 
 
 def test_autotune_deep_corrugation_builds_every_candidate_and_keeps_accuracy():
-    # the N = 16384 benchmark workload (j = 0): 64, 128 and 256 cell columns all build (the box,
+    # the N = 16384 benchmark workload (j = 0): 32, 64 and 128 cell columns all build (the box,
     # window and grid are re-derived per candidate), and the solve with the chosen cells still meets
-    # the energy target of the configuration (1e-8)
+    # the energy target of the configuration (1e-8). 256 columns would need a 9216-point FP64 Y
+    # transform, beyond one thread block's registers (SGF_EINVAL by design).
     torch = pytest.importorskip("torch")
     par = I.wl_deep_corrugation_neumann()
     op = sgf.Operator(par, precision=32)
-    cands = [64, 128, 256]
+    cands = [32, 64, 128]
     best, ms = sgf.sgf_autotune_cells(op.ctx, cands, reps=20)
     assert np.all(ms > 0), ms
     x = torch.zeros(par["N"], dtype=torch.complex128, device="cuda")
