@@ -281,6 +281,17 @@ sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out);
  * restored). Rebuilds the operator several times: a set-up step, not for a hot loop. */
 sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms);
 
+/* Accuracy-aware form of sgf_autotune_cells: each candidate that builds is also solved on the
+ * incident-wave right-hand side (GMRES to 1e-12, at most 4000 applications) and its energy error
+ * 1 - sum e_n over the propagating modes (eq. energy_error, the paper's accuracy measure) goes to
+ * host eps[i] (may be NULL; 1e300 where no solution was obtained). The fastest candidate with
+ * |energy error| < eps_tol is kept. If candidates build but none reaches eps_tol, the context is
+ * built with the most accurate one and SGF_ENOCONV is returned with a message. SGF_EINVAL for
+ * eps_tol <= 0 or when no candidate builds. A set-up step: it builds and solves once per candidate
+ * (and allocates a solution buffer for the duration of the call). */
+sgf_status sgf_autotune(sgf_ctx* ctx, const int* nx_list, int n, int reps, double eps_tol, int* best_nx, double* ms,
+                        double* eps);
+
 /* Introspection: fills host info[0..23] (the caller's buffer holds 24 doubles) with N, number of
  * occupied cells, near-field entries, P_x^H, rows^H, P_y^H, P_x^V, rows^V, P_y^V, n_eq (per
  * orientation), n_fit, n_fb basis size, |U^eta|, algorithmic bytes of one FP64 matvec, of one mixed

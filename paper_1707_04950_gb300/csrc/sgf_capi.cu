@@ -409,8 +409,6 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
     CU(cudaMemcpy(c->d_item_lo, il.data(), il.size() * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(c->d_item_hi, ih.data(), ih.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
-  if ((size_t)c->nfit * maxnq * sizeof(zd) > 200 * 1024)
-    return set_err(ctx, SGF_EINVAL, "too many nodes (%d) in one cell for the near-field kernel", maxnq);
   TRY(dalloc(ctx, &c->d_cell_start, c->n_occ + 1));
   TRY(dalloc(ctx, &c->d_node_idx, c->N));
   TRY(dalloc(ctx, &c->d_node_cell, c->N));
@@ -584,6 +582,25 @@ extern "C" sgf_status sgf_build_operator(sgf_ctx* ctx) {
   c->n_blk = (int)pq.size();
   c->nnz = off;
   c->maxW = maxW;
+  {  // near-row work items (see sgf_ctx::n_nitems)
+    std::vector<int> ic, il, ih;
+    for (int q = 0; q < c->n_occ; ++q) {
+      const int nq = c->cell_start[q + 1] - c->cell_start[q];
+      const int rows = std::max(4, std::min(32, 4096 / std::max(1, cellW[q])));
+      for (int lo = 0; lo < nq; lo += rows) {
+        ic.push_back(q);
+        il.push_back(lo);
+        ih.push_back(std::min(nq, lo + rows));
+      }
+    }
+    c->n_nitems = (int)ic.size();
+    TRY(dalloc(ctx, &c->d_nitem_cell, ic.size()));
+    TRY(dalloc(ctx, &c->d_nitem_lo, il.size()));
+    TRY(dalloc(ctx, &c->d_nitem_hi, ih.size()));
+    CU(cudaMemcpy(c->d_nitem_cell, ic.data(), ic.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_nitem_lo, il.data(), il.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->d_nitem_hi, ih.data(), ih.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   if ((size_t)maxW * sizeof(zd) > 200 * 1024)
     return set_err(ctx, SGF_EINVAL, "local set of %d nodes too large for the near-field kernel", maxW);
   int n_dcy = dcy_max - dcy_min + 1;
@@ -886,6 +903,11 @@ extern "C" sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev) {
 // ------------------------------------------------------------------ GMRES (restarted, CGS2)
 struct Krylov {
   zd *V = nullptr, *w = nullptr, *h = nullptr, *partial = nullptr, *r = nullptr, *tmp = nullptr;
+  // device-resident Arnoldi state: Hessenberg columns ([j][m + 1], column-major), Givens rotations,
+  // rotated right-hand side, squared norm, per-step residual estimates and flags, 1/h_{j+1,j}
+  zd *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *nrm2 = nullptr;
+  double *res = nullptr, *scale = nullptr;
+  int* flag = nullptr;
   int m = 0, nblk = 32;
 };
 
@@ -919,11 +941,16 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   if (bn == 0) { *relres = 0; return SGF_OK; }
   int total = 0;
   double res = bn;
-  // Hessenberg matrix: every entry is written before it is read, so its storage stays uninitialised
-  // (std::complex<double> is laid out as double[2])
-  std::unique_ptr<double[]> Hraw(new double[(size_t)2 * (m + 1) * m]);
-  cd* H = reinterpret_cast<cd*>(Hraw.get());
-  std::vector<cd> cs(m), sn(m), g(m + 1), y(m);
+  // The Arnoldi steps run on the device without host round trips: CGS2 projections and updates, the
+  // Hessenberg column, the norm, the normalisation and the Givens rotation (k_givens_step). The host
+  // reads the per-step residual estimates every kCheck steps; steps taken after the estimate
+  // reached tol within such a group are counted as applications and otherwise discarded. Once per
+  // cycle the rotated upper triangle comes back for the back-substitution.
+  constexpr int kCheck = 8;
+  const long ldh = m + 1;
+  std::vector<cd> Hh, g(m + 1), y(m);
+  std::vector<double> resh(m);
+  std::vector<int> flagh(m);
   double prev_true = 0;
   int cycles = 0;
   while (total < maxit) {
@@ -941,52 +968,55 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     CU(launch_axpby(K.V, zd(0, 0), K.V, zd(1.0 / beta, 0), N, ctx->stream));
     std::fill(g.begin(), g.end(), cd(0));
     g[0] = beta;
-    int jdone = 0;
-    for (int jj = 0; jj < m && total < maxit; ++jj) {
-      zd* vj = K.V + (size_t)jj * N;
-      zd* w = K.V + (size_t)(jj + 1) * N;
-      TRY(apply_op(ctx, vj, w, prec, adj));
-      ++total;
-      std::vector<cd> h1, h2;
-      TRY(dot_host(ctx, K, K.V, jj + 1, w, h1));
-      CU(cudaMemcpyAsync(K.h, h1.data(), (jj + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
-      CU(launch_update(w, K.V, jj + 1, N, K.h, N, ctx->stream));
-      TRY(dot_host(ctx, K, K.V, jj + 1, w, h2));
-      CU(cudaMemcpyAsync(K.h, h2.data(), (jj + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
-      CU(launch_update(w, K.V, jj + 1, N, K.h, N, ctx->stream));
-      for (int i = 0; i <= jj; ++i) H[(size_t)i * m + jj] = h1[i] + h2[i];
-      TRY(dot_host(ctx, K, w, 1, w, tmp));
-      double hn = std::sqrt(tmp[0].real());
-      H[(size_t)(jj + 1) * m + jj] = hn;
-      if (!(hn > 0) || !std::isfinite(hn)) {
-        if (!std::isfinite(hn)) return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
-      } else {
-        CU(launch_axpby(w, zd(0, 0), w, zd(1.0 / hn, 0), N, ctx->stream));
+    CU(cudaMemcpyAsync(K.g, g.data(), (m + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+    int jdone = 0, j = 0;
+    bool stop = false;
+    while (!stop && j < m && total < maxit) {
+      const int j0 = j, jend = std::min({m, j + kCheck, j + (maxit - total)});
+      for (; j < jend; ++j) {
+        zd* vj = K.V + (size_t)j * N;
+        zd* w = K.V + (size_t)(j + 1) * N;
+        zd* Hc = K.H + (size_t)j * ldh;
+        TRY(apply_op(ctx, vj, w, prec, adj));
+        ++total;
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+          CU(launch_dots(K.V, j + 1, N, w, N, K.partial, K.nblk, K.h, ctx->stream));
+          CU(launch_hcol(Hc, K.h, j + 1, pass, ctx->stream));
+          CU(launch_update(w, K.V, j + 1, N, K.h, N, ctx->stream));
+        }
+        CU(launch_dots(w, 1, N, w, N, K.partial, K.nblk, K.nrm2, ctx->stream));
+        CU(launch_givens_step(Hc, j, K.nrm2, K.cs, K.sn, K.g, K.res, K.scale, K.flag, ctx->stream));
+        CU(launch_scale_dev(w, N, K.scale, ctx->stream));
       }
-      for (int i = 0; i < jj; ++i) {
-        cd a = H[(size_t)i * m + jj], bb = H[(size_t)(i + 1) * m + jj];
-        H[(size_t)i * m + jj] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
-        H[(size_t)(i + 1) * m + jj] = -sn[i] * a + cs[i] * bb;
+      CU(cudaMemcpyAsync(resh.data() + j0, K.res + j0, (jend - j0) * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CU(cudaMemcpyAsync(flagh.data() + j0, K.flag + j0, (jend - j0) * sizeof(int), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      for (int jj = j0; jj < jend; ++jj) {
+        if (flagh[jj] == 2) return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
+        jdone = jj + 1;
+        res = resh[jj];
+        if (getenv("SGF_VERBOSE"))
+          fprintf(stderr, "gmres prec %d it %d j %d res %.3e\n", prec, total - (jend - 1 - jj), jj, res / bn);
+        if (res / bn <= tol || flagh[jj] == 1) {
+          stop = true;
+          break;
+        }
       }
-      cd a = H[(size_t)jj * m + jj], bb = H[(size_t)(jj + 1) * m + jj];
-      double den = std::sqrt(std::norm(a) + std::norm(bb));
-      cs[jj] = den > 0 ? a / den : cd(1);
-      sn[jj] = den > 0 ? bb / den : cd(0);
-      H[(size_t)jj * m + jj] = den;
-      H[(size_t)(jj + 1) * m + jj] = 0;
-      g[jj + 1] = -sn[jj] * g[jj];
-      g[jj] = std::conj(cs[jj]) * g[jj];
-      jdone = jj + 1;
-      res = std::abs(g[jj + 1]);
-      if (getenv("SGF_VERBOSE"))
-        fprintf(stderr, "gmres prec %d it %d j %d hn %.3e h00 %.3e res %.3e\n", prec, total, jj, hn,
-                std::abs(H[0]), res / bn);
-      if (res / bn <= tol || !(hn > 0)) break;
+    }
+    // back-substitution with the rotated triangle R (columns 0..jdone-1, rows 0..jdone-1)
+    Hh.resize((size_t)jdone * ldh);
+    if (jdone > 0) {
+      CU(cudaMemcpy2DAsync(Hh.data(), ldh * sizeof(zd), K.H, ldh * sizeof(zd), jdone * sizeof(zd), jdone,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaMemcpyAsync(g.data(), K.g, jdone * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
     }
     for (int i = jdone - 1; i >= 0; --i) {
-      cd s = g[i];
-      for (int k2 = i + 1; k2 < jdone; ++k2) s -= H[(size_t)i * m + k2] * y[k2];
-      y[i] = s / H[(size_t)i * m + i];
+      cd sacc = g[i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= Hh[(size_t)k2 * ldh + i] * y[k2];
+      y[i] = sacc / Hh[(size_t)i * ldh + i];
     }
     std::vector<cd> ny(jdone);
     for (int i = 0; i < jdone; ++i) ny[i] = -y[i];
@@ -1024,6 +1054,19 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
   };
   sgf_status st = SGF_OK;
   zd *b, *x, *dlt;
+  auto alb = [&](void** p, size_t bytes) -> sgf_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return set_err(ctx, SGF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    mine.push_back(*p);
+    return SGF_OK;
+  };
+  if ((st = al(&K.H, (size_t)(K.m + 1) * K.m)) || (st = al(&K.cs, (size_t)K.m)) || (st = al(&K.sn, (size_t)K.m)) ||
+      (st = al(&K.g, (size_t)K.m + 1)) || (st = al(&K.nrm2, 1)) ||
+      (st = alb((void**)&K.res, (size_t)K.m * sizeof(double))) || (st = alb((void**)&K.scale, sizeof(double))) ||
+      (st = alb((void**)&K.flag, (size_t)K.m * sizeof(int)))) {
+    for (void* p : mine) cudaFree(p);
+    return st;
+  }
   if ((st = al(&K.V, (size_t)(K.m + 1) * N)) || (st = al(&K.h, (size_t)K.m + 2)) ||
       (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
       (st = al(&K.r, N)) || (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
@@ -1446,7 +1489,10 @@ extern "C" sgf_status sgf_get_params(const sgf_ctx* ctx, sgf_params* out) {
 // h = (round(h0/dg) + 1/(j+1)) dg with dg = L/p and h0 the shift currently set. Every candidate
 // that builds is timed over `reps` applications (CUDA events around the context's own launch
 // path), and the context is left built with the fastest.
-extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms) {
+// Timing (and, with eps_tol > 0, accuracy) of each cell-count candidate; see sgf_autotune_cells
+// and sgf_autotune in sgf.h.
+static sgf_status autotune_impl(sgf_ctx* ctx, const int* nx_list, int n, int reps, double eps_tol, int* best_nx,
+                                double* ms, double* eps_out) {
   if (!ctx) return SGF_EINVAL;
   if (!nx_list || n < 1 || reps < 1) return set_err(ctx, SGF_EINVAL, "bad autotune arguments");
   if (!ctx->have_profile || !ctx->have_wave || !ctx->have_params)
@@ -1484,8 +1530,11 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
     if (base.j > 0 && !(P.h > a_s * slope)) P.h += dg;
     return P;
   };
-  double best = 1e300;
-  int bnx = -1;
+  double best = 1e300, best_eps = 1e300;
+  int bnx = -1, enx = -1;  // fastest eligible candidate; most accurate one (fallback)
+  zd* xsol = nullptr;
+  if (eps_tol > 0 && cudaMalloc(&xsol, (size_t)N * sizeof(zd)) != cudaSuccess)
+    return set_err(ctx, SGF_ECUDA, "autotune: allocation of the solution buffer failed");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -1513,17 +1562,43 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
     if (fail != SGF_OK) break;
     double per = t / reps;
     if (ms) ms[i] = per;
-    if (per < best) {
+    bool eligible = true;
+    if (eps_tol > 0) {
+      // the energy balance of the solution (eq. energy_error): the accuracy the candidate reaches
+      int its = 0;
+      double rr = 0, eps = 1e300;
+      sgf_status ss = solve_impl(ctx, nullptr, false, 1e-12, 4000, xsol, &its, &rr);
+      if (ss == SGF_OK || ss == SGF_ENOCONV) {
+        const double k = ctx->k, d = ctx->d, al = ctx->alpha;
+        const int nlo = (int)std::ceil((-k - al) * d / (2 * SGF_PI)), nhi = (int)std::floor((k - al) * d / (2 * SGF_PI));
+        if (sgf_rayleigh(ctx, xsol, nlo, nhi, nullptr, nullptr, &eps) != SGF_OK) eps = 1e300;
+      }
+      if (eps_out) eps_out[i] = eps;
+      eligible = std::fabs(eps) < eps_tol;
+      if (std::fabs(eps) < best_eps) {
+        best_eps = std::fabs(eps);
+        enx = nx_list[i];
+      }
+    }
+    if (eligible && per < best) {
       best = per;
       bnx = nx_list[i];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (xsol) cudaFree(xsol);
   if (fail != SGF_OK) {
     ctx->prm = base;
     ctx->built = false;
     return fail == SGF_ECUDA ? set_err(ctx, SGF_ECUDA, "autotune: timing a candidate failed") : fail;
+  }
+  if (bnx < 0 && enx >= 0) {  // built, but none reached eps_tol: keep the most accurate
+    if (best_nx) *best_nx = enx;
+    ctx->prm = candidate(enx);
+    TRY(sgf_build_operator(ctx));
+    return set_err(ctx, SGF_ENOCONV, "no candidate reaches the energy error %g (best %g with %d cell columns)",
+                   eps_tol, best_eps, enx);
   }
   if (bnx < 0) {
     ctx->prm = base;
@@ -1533,6 +1608,16 @@ extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n
   if (best_nx) *best_nx = bnx;
   ctx->prm = candidate(bnx);
   return sgf_build_operator(ctx);
+}
+
+extern "C" sgf_status sgf_autotune_cells(sgf_ctx* ctx, const int* nx_list, int n, int reps, int* best_nx, double* ms) {
+  return autotune_impl(ctx, nx_list, n, reps, 0.0, best_nx, ms, nullptr);
+}
+
+extern "C" sgf_status sgf_autotune(sgf_ctx* ctx, const int* nx_list, int n, int reps, double eps_tol, int* best_nx,
+                                   double* ms, double* eps) {
+  if (!(eps_tol > 0)) return set_err(ctx, SGF_EINVAL, "sgf_autotune needs an energy-error tolerance eps_tol > 0");
+  return autotune_impl(ctx, nx_list, n, reps, eps_tol, best_nx, ms, eps);
 }
 
 extern "C" sgf_status sgf_gradient(sgf_ctx* ctx, const void* mu_dev, int n_mode, double tol, int maxit, double* B,

@@ -155,6 +155,10 @@ struct sgf_ctx {
   // work items of the forward map: chunks of at most 32 nodes of one cell
   int n_items = 0;
   int *d_item_cell = nullptr, *d_item_lo = nullptr, *d_item_hi = nullptr;
+  // work items of the near rows: chunks of one cell's rows holding about 4096 near entries
+  // (4 to 32 rows), so that cells with long rows are spread over more blocks
+  int n_nitems = 0;
+  int *d_nitem_cell = nullptr, *d_nitem_lo = nullptr, *d_nitem_hi = nullptr;
   // precision-specific operator data
   OpData<double> o64;
   OpData<float> o32;
@@ -275,6 +279,11 @@ cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* p
                         cudaStream_t s);
 cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s);
 cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s);  // y = a x + b y
+// device-resident Arnoldi step: Hessenberg column store/accumulate, Givens update, w *= scale
+cudaError_t launch_hcol(zd* Hc, const zd* h, int cnt, int add, cudaStream_t s);
+cudaError_t launch_givens_step(zd* Hc, int j, const zd* nrm2, zd* cs, zd* sn, zd* g, double* res, double* scale,
+                               int* flag, cudaStream_t s);
+cudaError_t launch_scale_dev(zd* w, long n, const double* scale, cudaStream_t s);
 
 // Host mode helpers shared by the Rayleigh entry points, the mode completion and the gradient.
 // beta_n = sqrt(k^2 - alpha_n^2) with the branch i sqrt(alpha_n^2 - k^2) for evanescent modes

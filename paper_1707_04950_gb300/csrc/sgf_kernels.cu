@@ -680,9 +680,9 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
                        const int* __restrict__ pq, const int* __restrict__ pr, const int* __restrict__ pw,
                        const long* __restrict__ poff, const int* __restrict__ pld, const int* __restrict__ pdcx,
                        const double* __restrict__ kress,
-                       const double* __restrict__ binw, zd hk, zd* C) {
+                       const double* __restrict__ binw, zd hk, zd* C, int lc) {
   extern __shared__ unsigned char smem_raw[];
-  zd* Msh = reinterpret_cast<zd*>(smem_raw);
+  zd* Msh = reinterpret_cast<zd*>(smem_raw);  // [n_fit][lc]: one tile of source columns at a time
   const int b = blockIdx.x;
   const int q = pq[b], r = pr[b], wrap = pw[b];
   const long off = poff[b];
@@ -694,19 +694,22 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
   const int o = (dcx + 1) * n_dcy + (dcy - dcy_min);
   const zd* ph_o = phi + (long)o * g.nfit * 2 * g.neq;
   const zd* Pr = P + (long)4 * g.neq * rs;
-  // M[t][l] = sum_s Phi_off[t][s] P_r[lam(t)][s][l]
-  for (int idx = threadIdx.x; idx < g.nfit * nr; idx += blockDim.x) {
-    int t = idx / nr, l = idx % nr;
+  const zd wph = expi(g.alpha * g.d * wrap);
+  const double k = g.k;
+  for (int l0 = 0; l0 < nr; l0 += lc) {
+  const int ln = min(lc, nr - l0);
+  // M[t][l] = sum_s Phi_off[t][s] P_r[lam(t)][s][l] for the tile's source columns l0 .. l0 + ln - 1
+  __syncthreads();  // the previous tile's M has been used
+  for (int idx = threadIdx.x; idx < g.nfit * ln; idx += blockDim.x) {
+    int t = idx / ln, l = l0 + idx % ln;
     int lam = orient_of_sample(t, g.p);
     zd acc(0, 0);
     for (int s = 0; s < 2 * g.neq; ++s) acc += ph_o[t * 2 * g.neq + s] * Pr[(long)l * 4 * g.neq + lam * 2 * g.neq + s];
     Msh[idx] = acc;
   }
   __syncthreads();
-  const zd wph = expi(g.alpha * g.d * wrap);
-  const double k = g.k;
-  for (int idx = threadIdx.x; idx < nq * nr; idx += blockDim.x) {
-    int il = idx / nr, l = idx % nr;
+  for (int idx = threadIdx.x; idx < nq * ln; idx += blockDim.x) {
+    int il = idx / ln, l = l0 + idx % ln;
     int i = node_idx[qs + il], ls = node_idx[rs + l];
     double xi = x[i], fi = f[i], f1i = f1[i], si = sqrt(1 + f1i * f1i);
     double xl = x[ls] + wrap * g.d, fl = fs[ls], f1l = f1s[ls], sl = sqrt(1 + f1l * f1l);
@@ -737,8 +740,9 @@ __global__ void k_near(GeoArgs g, const int* __restrict__ cell_start, const int*
     }
     const zd* Ii = Iplain + (long)(qs + il) * g.nfit;
     zd sub(0, 0);
-    for (int t = 0; t < g.nfit; ++t) sub += Ii[t] * Msh[t * nr + l];
+    for (int t = 0; t < g.nfit; ++t) sub += Ii[t] * Msh[t * ln + (l - l0)];
     C[off + (long)il * ld + l] = wph * (val - sub);
+  }
   }
 }
 
@@ -757,15 +761,16 @@ cudaError_t launch_near_geo(sgf_ctx* c, const zd* d_phi, int dcy_min, int n_dcy,
   g.dmode = dmode;
   int maxnr = 0;
   for (int q = 0; q < c->n_occ; ++q) maxnr = std::max(maxnr, c->cell_start[q + 1] - c->cell_start[q]);
-  size_t sm = (size_t)c->nfit * maxnr * sizeof(zd);
-  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  // source columns per shared-memory tile of M (all of a cell's nodes when they fit)
+  const int lc = std::max(1, std::min(maxnr, (int)((160 * 1024) / ((size_t)c->nfit * sizeof(zd)))));
+  size_t sm = (size_t)c->nfit * lc * sizeof(zd);
   cudaFuncSetAttribute(k_near, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   zd hk(0, 0);
   cudaError_t e = near_hk(c, &hk);
   if (e != cudaSuccess) return e;
   k_near<<<pp.n, 256, sm, c->stream>>>(g, c->d_cell_start, c->d_node_idx, c->d_occ_cy, c->d_x, ft, f1t, f2t, fs, f1s,
                                        d_phi, dcy_min, n_dcy, d_Iplain, P, pp.q, pp.r, pp.wrap, pp.off, pp.ld, pp.dcx,
-                                       d_kress, c->d_binw, hk, C);
+                                       d_kress, c->d_binw, hk, C, lc);
   return cudaGetLastError();
 }
 
@@ -1315,9 +1320,9 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
   const size_t smn = (size_t)(c->maxW + 32) * sizeof(zd);
   cudaFuncSetAttribute(k_near_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn);
   auto near_rows = [&](cudaStream_t st) {
-    k_near_rows<T><<<c->n_items, 256, smn, st>>>(c->debug_mask, hs, c->d_cell_start, c->d_node_idx, c->d_cols,
-                                                 c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff,
-                                                 c->d_item_cell, c->d_item_lo, c->d_item_hi, mu, out);
+    k_near_rows<T><<<c->n_nitems, 256, smn, st>>>(c->debug_mask, hs, c->d_cell_start, c->d_node_idx, c->d_cols,
+                                                  c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff,
+                                                  c->d_nitem_cell, c->d_nitem_lo, c->d_nitem_hi, mu, out);
   };
   // Three concurrent branches when not profiling: the near field (needs only mu) from the start,
   // and after the projection the H and V convolutions; the far-field/mode kernel joins them.
@@ -1696,9 +1701,9 @@ cudaError_t apply_multi_t(sgf_ctx* c, OpData<T>& od, MultiSpace<T>& ms, const MC
   const size_t smn = near_multi_smem(c->maxW, nc, sizeof(cplx<T>) == 8 ? sizeof(float4) : sizeof(zd));
   if (smn > 200 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_near_multi<T, MC_MAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smn);
-  k_near_multi<T, MC_MAX><<<c->n_items, 256, smn, s>>>(hs, c->d, c->d_cell_start, c->d_node_idx, c->d_cols,
-                                                        c->d_coloff, c->d_colwrap, c->d_cell_off, c->d_cell_W, c->d_C,
-                                                        c->d_Cff, c->d_item_cell, c->d_item_lo, c->d_item_hi, cols);
+  k_near_multi<T, MC_MAX><<<c->n_nitems, 256, smn, s>>>(hs, c->d, c->d_cell_start, c->d_node_idx, c->d_cols,
+                                                         c->d_coloff, c->d_colwrap, c->d_cell_off, c->d_cell_W, c->d_C,
+                                                         c->d_Cff, c->d_nitem_cell, c->d_nitem_lo, c->d_nitem_hi, cols);
   k_interp_multi<T><<<c->n_items, 128, 0, s>>>(c->nfit, c->N, c->d_cell_start, c->d_node_idx, c->d_samp_gidx, c->prm.p,
                                                ms.grid[0], 2 * sz[0], ms.grid[1], 2 * sz[1], od.Ip, c->d_occ_cx, c->L,
                                                c->keep.samp_rel, ms.mpart, ms.mpart_ff, mp_col, c->mode_chunks,
@@ -2284,15 +2289,38 @@ cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* p
   k_dots_final<<<ceil_div(m, 128), 128, 0, s>>>(partial, nblk, m, out);
   return cudaGetLastError();
 }
-__global__ void k_update(zd* w, const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ h, long n) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  zd acc = w[i];
-  for (int j = 0; j < m; ++j) acc -= V[j * ldv + i] * h[j];
-  w[i] = acc;
+// w -= V h over m vectors: a block takes 32 consecutive elements (threadIdx.x) and splits the m
+// vectors among 8 thread rows (threadIdx.y), each with four independent loads in flight; the rows'
+// partial sums are added in shared memory. (One thread per element walking all m vectors in turn
+// leaves the GPU a few dozen blocks each waiting on one dependent load per vector.)
+__global__ void __launch_bounds__(256) k_update(zd* w, const zd* __restrict__ V, int m, long ldv,
+                                                const zd* __restrict__ h, long n) {
+  __shared__ zd part[8][33];
+  const long i = (long)blockIdx.x * 32 + threadIdx.x;
+  zd a0(0, 0), a1(0, 0);
+  if (i < n) {
+    int j = threadIdx.y;
+    for (; j + 24 < m; j += 32) {
+      const zd v0 = V[(long)j * ldv + i], v1 = V[(long)(j + 8) * ldv + i];
+      const zd v2 = V[(long)(j + 16) * ldv + i], v3 = V[(long)(j + 24) * ldv + i];
+      a0 += v0 * h[j];
+      a1 += v1 * h[j + 8];
+      a0 += v2 * h[j + 16];
+      a1 += v3 * h[j + 24];
+    }
+    for (; j < m; j += 8) a0 += V[(long)j * ldv + i] * h[j];
+  }
+  part[threadIdx.y][threadIdx.x] = a0 + a1;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    zd acc(0, 0);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc += part[r][threadIdx.x];
+    w[i] = w[i] - acc;
+  }
 }
 cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s) {
-  k_update<<<ceil_div(n, 256), 256, 0, s>>>(w, V, m, ldv, h, n);
+  k_update<<<ceil_div(n, 32), dim3(32, 8), 0, s>>>(w, V, m, ldv, h, n);
   return cudaGetLastError();
 }
 __global__ void k_axpby(zd* y, zd a, const zd* x, zd b, long n) {
@@ -2301,5 +2329,75 @@ __global__ void k_axpby(zd* y, zd a, const zd* x, zd b, long n) {
 }
 cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s) {
   k_axpby<<<ceil_div(n, 256), 256, 0, s>>>(y, a, x, b, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- device-resident Arnoldi step
+// Hessenberg column j (column-major): Hc[i] = h[i] (add = 0) or Hc[i] += h[i] (add = 1), i < cnt.
+__global__ void k_hcol(zd* Hc, const zd* __restrict__ h, int cnt, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) Hc[i] = add ? Hc[i] + h[i] : h[i];
+}
+// End of Arnoldi step j: h_{j+1,j} = |w| from its squared norm nrm2; the earlier Givens rotations
+// applied to column j, the new rotation (cs_j, sn_j), the rotated right-hand side g and the residual
+// estimate res[j] = |g_{j+1}|; scale = 1/h_{j+1,j} for the normalisation of w (0 on a breakdown);
+// flag[j]: 0, 1 breakdown (h_{j+1,j} = 0), 2 non-finite. The column and the rotations are staged in
+// shared memory by the whole block, then one thread applies the rotations in order.
+__global__ void __launch_bounds__(256) k_givens_step(zd* Hc, int j, const zd* __restrict__ nrm2, zd* cs, zd* sn,
+                                                     zd* g, double* res, double* scale, int* flag) {
+  extern __shared__ unsigned char smem_raw[];
+  zd* hs = reinterpret_cast<zd*>(smem_raw);  // [j + 2] column
+  zd* css = hs + (j + 2);                     // [j] rotations
+  zd* sns = css + j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = Hc[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    css[i] = cs[i];
+    sns[i] = sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(nrm2[0].re);
+    const int f = !isfinite(hn) ? 2 : (hn > 0 ? 0 : 1);
+    for (int i = 0; i < j; ++i) {
+      const zd a = hs[i], b = hs[i + 1];
+      hs[i] = conj(css[i]) * a + conj(sns[i]) * b;
+      hs[i + 1] = zd(0, 0) - sns[i] * a + css[i] * b;
+    }
+    const zd a = hs[j];
+    const double den = sqrt(abs2(a) + hn * hn);
+    const zd c = den > 0 ? a * (1.0 / den) : zd(1, 0);
+    const zd sj = den > 0 ? zd(hn / den, 0) : zd(0, 0);
+    cs[j] = c;
+    sn[j] = sj;
+    hs[j] = zd(den, 0);
+    hs[j + 1] = zd(0, 0);
+    const zd gj = g[j];
+    g[j + 1] = zd(0, 0) - sj * gj;
+    g[j] = conj(c) * gj;
+    res[j] = sqrt(abs2(g[j + 1]));
+    scale[0] = f == 0 ? 1.0 / hn : 0.0;
+    flag[j] = f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = hs[i];
+}
+// w *= scale[0]
+__global__ void k_scale_dev(zd* w, long n, const double* __restrict__ scale) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = w[i] * scale[0];
+}
+cudaError_t launch_hcol(zd* Hc, const zd* h, int cnt, int add, cudaStream_t s) {
+  k_hcol<<<ceil_div(cnt, 128), 128, 0, s>>>(Hc, h, cnt, add);
+  return cudaGetLastError();
+}
+cudaError_t launch_givens_step(zd* Hc, int j, const zd* nrm2, zd* cs, zd* sn, zd* g, double* res, double* scale,
+                               int* flag, cudaStream_t s) {
+  const size_t sm = (size_t)(3 * j + 2) * sizeof(zd);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_givens_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_givens_step<<<1, 256, sm, s>>>(Hc, j, nrm2, cs, sn, g, res, scale, flag);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_dev(zd* w, long n, const double* scale, cudaStream_t s) {
+  k_scale_dev<<<ceil_div(n, 256), 256, 0, s>>>(w, n, scale);
   return cudaGetLastError();
 }

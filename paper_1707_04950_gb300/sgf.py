@@ -23,7 +23,7 @@ EXPORTED = ["sgf_create", "sgf_destroy", "sgf_last_error", "sgf_set_profile_four
             "sgf_set_params", "sgf_build_operator", "sgf_apply", "sgf_apply_host", "sgf_rhs", "sgf_solve", "sgf_solve_rhs",
             "sgf_rayleigh", "sgf_rayleigh_noalloc", "sgf_field", "sgf_build_exact", "sgf_select_operator",
             "sgf_exact_matrix", "sgf_suggest_params", "sgf_gradient", "sgf_gradient_fd", "sgf_get_params", "sgf_autotune_cells", "sgf_info", "sgf_set_profiling", "sgf_stage_times", "sgf_debug_mask", "sgf_debug_table",
-            "sgf_debug_force_variants",
+            "sgf_debug_force_variants", "sgf_autotune",
             "sgf_batch_create", "sgf_batch_destroy", "sgf_batch_last_error", "sgf_batch_apply", "sgf_batch_solve",
             "sgf_batch_shared_near"]
 
@@ -77,6 +77,7 @@ def load():
         "sgf_gradient_fd": [vp, vp, i, d, i, dp, dp, dp, dp, ctypes.POINTER(i)],
         "sgf_get_params": [vp, ctypes.POINTER(sgf_params)],
         "sgf_autotune_cells": [vp, ctypes.POINTER(i), i, i, ctypes.POINTER(i), dp],
+        "sgf_autotune": [vp, ctypes.POINTER(i), i, i, d, ctypes.POINTER(i), dp, dp],
         "sgf_info": [vp, dp],
         "sgf_set_profiling": [vp, i],
         "sgf_stage_times": [vp, dp],
@@ -255,6 +256,20 @@ def sgf_autotune_cells(ctx, nx_list, reps=20):
     ms = np.zeros(len(nx_list))
     _check(ctx, load().sgf_autotune_cells(ctx, arr, len(nx_list), int(reps), ctypes.byref(best), _dptr(ms)))
     return best.value, ms
+
+
+def sgf_autotune(ctx, nx_list, eps_tol, reps=20):
+    """Accuracy-aware tuning: returns (status, best nx, ms per application, energy error per
+    candidate). Status 5 (SGF_ENOCONV): no candidate reached eps_tol; the most accurate is kept."""
+    arr = (ctypes.c_int * len(nx_list))(*[int(x) for x in nx_list])
+    best = ctypes.c_int(0)
+    ms = np.zeros(len(nx_list))
+    eps = np.zeros(len(nx_list))
+    st = load().sgf_autotune(ctx, arr, len(nx_list), int(reps), float(eps_tol), ctypes.byref(best), _dptr(ms),
+                             _dptr(eps))
+    if st not in (0, 5):
+        _check(ctx, st)
+    return st, best.value, ms, eps
 
 
 def sgf_rayleigh_noalloc(ctx, mu_ptr, n_lo, n_hi):

@@ -35,19 +35,24 @@ def test_autotune_keeps_fastest_built_candidate_and_matches_oracle():
 
 
 def test_autotune_deep_corrugation_builds_every_candidate_and_keeps_accuracy():
-    # the N = 16384 benchmark workload (j = 0): 32, 64 and 128 cell columns all build (the box,
-    # window and grid are re-derived per candidate), and the solve with the chosen cells still meets
-    # the energy target of the configuration (1e-8). 256 columns would need a 9216-point FP64 Y
-    # transform, beyond one thread block's registers (SGF_EINVAL by design).
+    # the N = 16384 benchmark workload (j = 0): 32, 64 and 128 cell columns all build (box, window
+    # and grid re-derived per candidate; large cells tile the near-operator build). Timed alone, 64
+    # columns are fastest but reach an energy error of 4.3e-8 only; the accuracy-aware tuner keeps
+    # the fastest candidate below the configuration's target (1e-8), and its solve meets it.
     torch = pytest.importorskip("torch")
     par = I.wl_deep_corrugation_neumann()
     op = sgf.Operator(par, precision=32)
     cands = [32, 64, 128]
-    best, ms = sgf.sgf_autotune_cells(op.ctx, cands, reps=20)
-    assert np.all(ms > 0), ms
+    best_t, ms_t = sgf.sgf_autotune_cells(op.ctx, cands, reps=20)
+    assert np.all(ms_t > 0), ms_t
+    st, best, ms, eps = sgf.sgf_autotune(op.ctx, cands, 1e-8, reps=20)
+    assert st == 0 and np.all(ms > 0), (st, ms, eps)
+    i = cands.index(best)
+    assert abs(eps[i]) < 1e-8
+    assert all(ms[i] <= ms[c] for c in range(len(cands)) if abs(eps[c]) < 1e-8)
     x = torch.zeros(par["N"], dtype=torch.complex128, device="cuda")
     st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 4000, x.data_ptr())
-    _, _, eps = sgf.sgf_rayleigh(op.ctx, x.data_ptr(), -40, 40)
+    _, _, e = sgf.sgf_rayleigh(op.ctx, x.data_ptr(), -40, 40)
     op.close()
     assert st == 0 and rr <= 1e-12, (best, st, its, rr)
-    assert abs(eps) < 1e-8, (best, eps, ms)
+    assert abs(e) < 1e-8, (best, e, ms, eps)
