@@ -156,12 +156,16 @@ def stage_bytes(info, s):
 
 # launches per stage of one application (two orientations where a stage has two)
 LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "near": 1, "interp": 1}
-# DRAM bytes (read + write) per launch of the current mixed-path kernels, from one ncu capture of the
-# benchmark workload (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-# -k regex:k_ python bench.py --steps 3 --warmup 3 --batch 0 --gradient 0 --field 0
-# --no-cpu-baseline`); None where no capture of the current kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"project": None, "fft_x": None, "conv_y": None, "ifft_x": None, "near": None,
-                         "interp": None}
+# DRAM bytes (read + write) per launch of the current mixed-path kernels at the benchmark workload,
+# from one ncu capture of the first mixed application (graph capture off, so that ncu sees the
+# launches): `SGF_NO_GRAPH=1 ncu --set full --clock-control none -k regex:"k_(near_rows|conv_y|fft_x|
+# project|interp_far)" -s 89 -c 9 -o prof_mixed python bench.py --steps 3 --warmup 3 --batch 0
+# --gradient 0 --field 0 --solve 0 --shifted 0 --sweep 0 --multi 0 --no-cpu-baseline`. Two-launch
+# stages give the mean of their H and V launches. Each kernel's writes stay in the 129 MB L2 while it
+# runs (ncu reports 0 bytes written), so these are the reads. None where no capture of the current
+# kernel exists.
+DRAM_BYTES_PER_LAUNCH = {"project": 12.703e6, "fft_x": 4.263e6, "conv_y": 13.743e6, "ifft_x": 2.152e6,
+                         "near": 36.591e6, "interp": 5.438e6}
 
 
 def peaks():
