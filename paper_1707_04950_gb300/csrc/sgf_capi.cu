@@ -902,12 +902,10 @@ extern "C" sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev) {
 
 // ------------------------------------------------------------------ GMRES (restarted, CGS2)
 struct Krylov {
-  zd *V = nullptr, *w = nullptr, *h = nullptr, *partial = nullptr, *r = nullptr, *tmp = nullptr;
-  // device-resident Arnoldi state: Hessenberg columns ([j][m + 1], column-major), Givens rotations,
-  // rotated right-hand side, squared norm, per-step residual estimates and flags, 1/h_{j+1,j}
-  zd *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *nrm2 = nullptr;
-  double *res = nullptr, *scale = nullptr;
-  int* flag = nullptr;
+  zd *V = nullptr, *h = nullptr, *partial = nullptr, *r = nullptr;
+  zd* H = nullptr;  // Hessenberg columns written by the device, [m][m + 1] column-major
+  float4 *part = nullptr, *npart = nullptr;  // float-float partial sums of the Arnoldi kernels
+  unsigned* ticket = nullptr;                 // completion counters of k_kdots (zero between launches)
   int m = 0, nblk = 32;
 };
 
@@ -941,16 +939,15 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   if (bn == 0) { *relres = 0; return SGF_OK; }
   int total = 0;
   double res = bn;
-  // The Arnoldi steps run on the device without host round trips: CGS2 projections and updates, the
-  // Hessenberg column, the norm, the normalisation and the Givens rotation (k_givens_step). The host
-  // reads the per-step residual estimates every kCheck steps; steps taken after the estimate
-  // reached tol within such a group are counted as applications and otherwise discarded. Once per
-  // cycle the rotated upper triangle comes back for the back-substitution.
+  // The Arnoldi steps run on the device without host round trips: CGS2 projections and updates in
+  // float-float arithmetic, the Hessenberg column, the norm and the normalisation. Every kCheck
+  // steps the host reads the new Hessenberg columns, applies the Givens rotations to them (FP64,
+  // on the host) and takes the residual estimates; steps taken after the estimate reached tol
+  // within such a group are counted as applications and otherwise discarded.
   constexpr int kCheck = 8;
   const long ldh = m + 1;
-  std::vector<cd> Hh, g(m + 1), y(m);
-  std::vector<double> resh(m);
-  std::vector<int> flagh(m);
+  const int nparts = kupdate_blocks(N);
+  std::vector<cd> Hh, g(m + 1), y(m), cs(m), sn(m);  // Hh grows with the columns in use
   double prev_true = 0;
   int cycles = 0;
   while (total < maxit) {
@@ -968,7 +965,6 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     CU(launch_axpby(K.V, zd(0, 0), K.V, zd(1.0 / beta, 0), N, ctx->stream));
     std::fill(g.begin(), g.end(), cd(0));
     g[0] = beta;
-    CU(cudaMemcpyAsync(K.g, g.data(), (m + 1) * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
     int jdone = 0, j = 0;
     bool stop = false;
     while (!stop && j < m && total < maxit) {
@@ -980,39 +976,45 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
         TRY(apply_op(ctx, vj, w, prec, adj));
         ++total;
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          CU(launch_dots(K.V, j + 1, N, w, N, K.partial, K.nblk, K.h, ctx->stream));
-          CU(launch_hcol(Hc, K.h, j + 1, pass, ctx->stream));
-          CU(launch_update(w, K.V, j + 1, N, K.h, N, ctx->stream));
+          CU(launch_kdots(K.V, j + 1, N, w, N, K.part, K.h, Hc, pass, K.ticket, ctx->stream));
+          CU(launch_kupdate(w, K.V, j + 1, N, K.h, N, pass == 1 ? K.npart : nullptr, ctx->stream));
         }
-        CU(launch_dots(w, 1, N, w, N, K.partial, K.nblk, K.nrm2, ctx->stream));
-        CU(launch_givens_step(Hc, j, K.nrm2, K.cs, K.sn, K.g, K.res, K.scale, K.flag, ctx->stream));
-        CU(launch_scale_dev(w, N, K.scale, ctx->stream));
+        CU(launch_kscale(w, N, K.npart, nparts, Hc + j + 1, ctx->stream));
       }
-      CU(cudaMemcpyAsync(resh.data() + j0, K.res + j0, (jend - j0) * sizeof(double), cudaMemcpyDeviceToHost,
-                         ctx->stream));
-      CU(cudaMemcpyAsync(flagh.data() + j0, K.flag + j0, (jend - j0) * sizeof(int), cudaMemcpyDeviceToHost,
-                         ctx->stream));
+      if (Hh.size() < (size_t)jend * ldh) Hh.resize((size_t)jend * ldh);
+      CU(cudaMemcpy2DAsync(Hh.data() + (size_t)j0 * ldh, ldh * sizeof(zd), K.H + (size_t)j0 * ldh, ldh * sizeof(zd),
+                           (jend + 1) * sizeof(zd), jend - j0, cudaMemcpyDeviceToHost, ctx->stream));
       CU(cudaStreamSynchronize(ctx->stream));
       for (int jj = j0; jj < jend; ++jj) {
-        if (flagh[jj] == 2) return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
+        cd* col = Hh.data() + (size_t)jj * ldh;
+        for (int i = 0; i <= jj + 1; ++i)
+          if (!std::isfinite(col[i].real()) || !std::isfinite(col[i].imag()))
+            return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
+        for (int i = 0; i < jj; ++i) {  // earlier rotations
+          const cd a = col[i], bb = col[i + 1];
+          col[i] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
+          col[i + 1] = -sn[i] * a + cs[i] * bb;
+        }
+        const double hn = col[jj + 1].real();
+        const cd a = col[jj];
+        const double den = std::sqrt(std::norm(a) + hn * hn);
+        cs[jj] = den > 0 ? a / den : cd(1);
+        sn[jj] = den > 0 ? cd(hn / den) : cd(0);
+        col[jj] = den;
+        col[jj + 1] = 0;
+        g[jj + 1] = -sn[jj] * g[jj];
+        g[jj] = std::conj(cs[jj]) * g[jj];
         jdone = jj + 1;
-        res = resh[jj];
+        res = std::abs(g[jj + 1]);
         if (getenv("SGF_VERBOSE"))
           fprintf(stderr, "gmres prec %d it %d j %d res %.3e\n", prec, total - (jend - 1 - jj), jj, res / bn);
-        if (res / bn <= tol || flagh[jj] == 1) {
+        if (res / bn <= tol || hn == 0) {  // converged, or breakdown (the Krylov space is invariant)
           stop = true;
           break;
         }
       }
     }
     // back-substitution with the rotated triangle R (columns 0..jdone-1, rows 0..jdone-1)
-    Hh.resize((size_t)jdone * ldh);
-    if (jdone > 0) {
-      CU(cudaMemcpy2DAsync(Hh.data(), ldh * sizeof(zd), K.H, ldh * sizeof(zd), jdone * sizeof(zd), jdone,
-                           cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaMemcpyAsync(g.data(), K.g, jdone * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
-    }
     for (int i = jdone - 1; i >= 0; --i) {
       cd sacc = g[i];
       for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= Hh[(size_t)k2 * ldh + i] * y[k2];
@@ -1020,8 +1022,10 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     }
     std::vector<cd> ny(jdone);
     for (int i = 0; i < jdone; ++i) ny[i] = -y[i];
-    CU(cudaMemcpyAsync(K.h, ny.data(), jdone * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
-    CU(launch_update(x, K.V, jdone, N, K.h, N, ctx->stream));
+    if (jdone > 0) {
+      CU(cudaMemcpyAsync(K.h, ny.data(), jdone * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+      CU(launch_kupdate(x, K.V, jdone, N, K.h, N, nullptr, ctx->stream));
+    }
     CU(cudaStreamSynchronize(ctx->stream));
     if (!true_check && res / bn <= tol) break;
   }
@@ -1060,19 +1064,18 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
     mine.push_back(*p);
     return SGF_OK;
   };
-  if ((st = al(&K.H, (size_t)(K.m + 1) * K.m)) || (st = al(&K.cs, (size_t)K.m)) || (st = al(&K.sn, (size_t)K.m)) ||
-      (st = al(&K.g, (size_t)K.m + 1)) || (st = al(&K.nrm2, 1)) ||
-      (st = alb((void**)&K.res, (size_t)K.m * sizeof(double))) || (st = alb((void**)&K.scale, sizeof(double))) ||
-      (st = alb((void**)&K.flag, (size_t)K.m * sizeof(int)))) {
+  const long nchunk = (N + 511) / 512;
+  if ((st = al(&K.H, (size_t)(K.m + 1) * K.m)) || (st = al(&K.V, (size_t)(K.m + 1) * N)) ||
+      (st = al(&K.h, (size_t)K.m + 2)) || (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
+      (st = alb((void**)&K.part, (size_t)nchunk * (K.m + 1) * sizeof(float4))) ||
+      (st = alb((void**)&K.npart, (size_t)kupdate_blocks(N) * sizeof(float4))) ||
+      (st = alb((void**)&K.ticket, (size_t)kdots_groups(K.m + 1) * sizeof(unsigned))) ||
+      (st = al(&K.r, N)) ||
+      (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
     for (void* p : mine) cudaFree(p);
     return st;
   }
-  if ((st = al(&K.V, (size_t)(K.m + 1) * N)) || (st = al(&K.h, (size_t)K.m + 2)) ||
-      (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
-      (st = al(&K.r, N)) || (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
-    for (void* p : mine) cudaFree(p);
-    return st;
-  }
+  cudaMemsetAsync(K.ticket, 0, (size_t)kdots_groups(K.m + 1) * sizeof(unsigned), ctx->stream);
   int its = 0;
   double rr = 1;
   if (b_in)

@@ -277,13 +277,18 @@ cudaError_t launch_debug_table(sgf_ctx* c, int lam, int kind, zd* out);
 // Krylov helpers
 cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* partial, int nblk, zd* out,
                         cudaStream_t s);
-cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s);
 cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s);  // y = a x + b y
-// device-resident Arnoldi step: Hessenberg column store/accumulate, Givens update, w *= scale
-cudaError_t launch_hcol(zd* Hc, const zd* h, int cnt, int add, cudaStream_t s);
-cudaError_t launch_givens_step(zd* Hc, int j, const zd* nrm2, zd* cs, zd* sn, zd* g, double* res, double* scale,
-                               int* flag, cudaStream_t s);
-cudaError_t launch_scale_dev(zd* w, long n, const double* scale, cudaStream_t s);
+// Arnoldi step in float-float arithmetic on FP64 vectors: h = V^H w over m basis vectors (part: at
+// least ceil(n / 512) * m float4 partials; Hc, when given, stores or accumulates h; ticket: at least
+// kdots_groups(m) counters, zero on entry and on return); w -= V h (with npart, kupdate_blocks(n)
+// float4 partials of |w|^2 are written too); w /= |w| with hsub = |w|.
+cudaError_t launch_kdots(const zd* V, int m, long ldv, const zd* w, long n, float4* part, zd* h, zd* Hc, int add,
+                         unsigned* ticket, cudaStream_t s);
+int kdots_groups(int m);
+
+cudaError_t launch_kupdate(zd* w, const zd* V, int m, long ldv, const zd* h, long n, float4* npart, cudaStream_t s);
+cudaError_t launch_kscale(zd* w, long n, const float4* npart, int nparts, zd* hsub, cudaStream_t s);
+int kupdate_blocks(long n);
 
 // Host mode helpers shared by the Rayleigh entry points, the mode completion and the gradient.
 // beta_n = sqrt(k^2 - alpha_n^2) with the branch i sqrt(alpha_n^2 - k^2) for evanescent modes

@@ -1324,18 +1324,20 @@ static cudaError_t apply_t(sgf_ctx* c, OpData<T>& od, const zd* mu, zd* out) {
                                                   c->d_coloff, c->d_cell_off, c->d_cell_W, c->d_C, c->d_Cff,
                                                   c->d_nitem_cell, c->d_nitem_lo, c->d_nitem_hi, mu, out);
   };
-  // Three concurrent branches when not profiling: the near field (needs only mu) from the start,
-  // and after the projection the H and V convolutions; the far-field/mode kernel joins them.
+  // Three concurrent branches when not profiling: the near field (needs only mu) once the grids are
+  // cleared, and after the projection the H and V convolutions; the far-field/mode kernel joins
+  // them. (Forked before the clears, the near kernel's blocks fill every SM and hold back the
+  // clears and the projection, which start the longer chain.)
   const bool branches = !c->profiling && c->side && c->side2;
+  if (c->profiling) cudaEventRecord(c->ev[0], s);
+  cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(cplx<T>), s);
+  cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(cplx<T>), s);
   if (branches) {
     cudaEventRecord(c->ev_fork0, s);
     cudaStreamWaitEvent(c->side2, c->ev_fork0, 0);
     near_rows(c->side2);
     cudaEventRecord(c->ev_join2, c->side2);
   }
-  if (c->profiling) cudaEventRecord(c->ev[0], s);
-  cudaMemsetAsync(od.grid[0], 0, 2 * szH * sizeof(cplx<T>), s);
-  cudaMemsetAsync(od.grid[1], 0, 2 * szV * sizeof(cplx<T>), s);
   k_project<T><<<c->n_items + c->nm * c->mode_chunks, 128, (size_t)32 * sizeof(cplx<T>), s>>>(
       c->n_occ, c->neq, c->nm, c->N, c->d_cell_start, c->d_node_idx, mu, od.P, c->d_src_gidx, od.src_tw, od.grid[0],
       szH, od.grid[1], szV, c->d_MS, c->d_MSff, c->d_mpart, c->d_mpart_ff, nullptr, c->mode_chunks, c->n_items,
@@ -2289,40 +2291,6 @@ cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* p
   k_dots_final<<<ceil_div(m, 128), 128, 0, s>>>(partial, nblk, m, out);
   return cudaGetLastError();
 }
-// w -= V h over m vectors: a block takes 32 consecutive elements (threadIdx.x) and splits the m
-// vectors among 8 thread rows (threadIdx.y), each with four independent loads in flight; the rows'
-// partial sums are added in shared memory. (One thread per element walking all m vectors in turn
-// leaves the GPU a few dozen blocks each waiting on one dependent load per vector.)
-__global__ void __launch_bounds__(256) k_update(zd* w, const zd* __restrict__ V, int m, long ldv,
-                                                const zd* __restrict__ h, long n) {
-  __shared__ zd part[8][33];
-  const long i = (long)blockIdx.x * 32 + threadIdx.x;
-  zd a0(0, 0), a1(0, 0);
-  if (i < n) {
-    int j = threadIdx.y;
-    for (; j + 24 < m; j += 32) {
-      const zd v0 = V[(long)j * ldv + i], v1 = V[(long)(j + 8) * ldv + i];
-      const zd v2 = V[(long)(j + 16) * ldv + i], v3 = V[(long)(j + 24) * ldv + i];
-      a0 += v0 * h[j];
-      a1 += v1 * h[j + 8];
-      a0 += v2 * h[j + 16];
-      a1 += v3 * h[j + 24];
-    }
-    for (; j < m; j += 8) a0 += V[(long)j * ldv + i] * h[j];
-  }
-  part[threadIdx.y][threadIdx.x] = a0 + a1;
-  __syncthreads();
-  if (threadIdx.y == 0 && i < n) {
-    zd acc(0, 0);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) acc += part[r][threadIdx.x];
-    w[i] = w[i] - acc;
-  }
-}
-cudaError_t launch_update(zd* w, const zd* V, int m, long ldv, const zd* h, long n, cudaStream_t s) {
-  k_update<<<ceil_div(n, 32), dim3(32, 8), 0, s>>>(w, V, m, ldv, h, n);
-  return cudaGetLastError();
-}
 __global__ void k_axpby(zd* y, zd a, const zd* x, zd b, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = a * x[i] + b * y[i];
@@ -2332,72 +2300,203 @@ cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s)
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- device-resident Arnoldi step
-// Hessenberg column j (column-major): Hc[i] = h[i] (add = 0) or Hc[i] += h[i] (add = 1), i < cnt.
-__global__ void k_hcol(zd* Hc, const zd* __restrict__ h, int cnt, int add) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < cnt) Hc[i] = add ? Hc[i] + h[i] : h[i];
-}
-// End of Arnoldi step j: h_{j+1,j} = |w| from its squared norm nrm2; the earlier Givens rotations
-// applied to column j, the new rotation (cs_j, sn_j), the rotated right-hand side g and the residual
-// estimate res[j] = |g_{j+1}|; scale = 1/h_{j+1,j} for the normalisation of w (0 on a breakdown);
-// flag[j]: 0, 1 breakdown (h_{j+1,j} = 0), 2 non-finite. The column and the rotations are staged in
-// shared memory by the whole block, then one thread applies the rotations in order.
-__global__ void __launch_bounds__(256) k_givens_step(zd* Hc, int j, const zd* __restrict__ nrm2, zd* cs, zd* sn,
-                                                     zd* g, double* res, double* scale, int* flag) {
-  extern __shared__ unsigned char smem_raw[];
-  zd* hs = reinterpret_cast<zd*>(smem_raw);  // [j + 2] column
-  zd* css = hs + (j + 2);                     // [j] rotations
-  zd* sns = css + j;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = Hc[i];
-  for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    css[i] = cs[i];
-    sns[i] = sn[i];
+// ---------------------------------------------------------------- Arnoldi step in float-float
+// The Gram-Schmidt projections of the FP64 Krylov vectors run on the FP32 pipes: each FP64 value is
+// split into two floats with integer instructions only, and the products are accumulated with the
+// compensated dot product (dot2_mac), about 48 significant bits. This GPU issues an FP64 warp
+// instruction about once per 64 cycles per scheduler and an FP32 or integer one every cycle, so the
+// four complex FP64 multiply-adds per element and basis vector of CGS2 would cost more than reading
+// the vectors; this way the step moves at memory speed. Results are written back in FP64.
+
+// x = hi + lo: hi keeps the top 24 significant bits of x (truncated), lo the remaining 29 rounded to
+// 24, so hi + lo matches x to 2^-48 relative. |x| < 2^-126 gives 0 (the vectors are normalised,
+// so this drops less than 1.2e-38); |x| >= 2^128, infinities and NaN give a NaN hi, so that a
+// non-finite vector still yields a non-finite inner product.
+__device__ __forceinline__ float2 split_d(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sg = hw & 0x80000000u;
+  const int ex = (int)((hw >> 20) & 0x7ffu);  // biased FP64 exponent
+  if (ex < 897) return make_float2(0.f, 0.f);
+  if (ex > 1150) return make_float2(__int_as_float(0x7fc00000), 0.f);
+  const float hi = __uint_as_float(sg | ((unsigned)(ex - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  float lo = 0.f;
+  if (ex >= 949) {  // 2^(ex - 1075), the weight of the remainder's last bit, is a normal float
+    const float sc = __uint_as_float((unsigned)(ex - 948) << 23);
+    lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(lw & 0x1fffffffu), sc)) | sg);
   }
+  return make_float2(hi, lo);
+}
+// complex double -> {re.hi, im.hi, re.lo, im.lo}; conj negates the imaginary parts
+__device__ __forceinline__ float4 split_z(zd z, bool conj_ = false) {
+  const float2 r = split_d(z.re), i = split_d(z.im);
+  return conj_ ? make_float4(r.x, -i.x, r.y, -i.y) : make_float4(r.x, i.x, r.y, i.y);
+}
+__device__ __forceinline__ float4 pack_dot2(const dot2c& a) { return make_float4(a.sr, a.si, a.er, a.ei); }
+__device__ __forceinline__ dot2c unpack_dot2(float4 v) { return dot2c{v.x, v.y, v.z, v.w}; }
+// the warp's 32 partial sums folded into lane 0
+__device__ __forceinline__ void warp_merge(dot2c& a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    dot2c b{__shfl_down_sync(0xffffffffu, a.sr, o), __shfl_down_sync(0xffffffffu, a.si, o),
+            __shfl_down_sync(0xffffffffu, a.er, o), __shfl_down_sync(0xffffffffu, a.ei, o)};
+    dot2_merge(a, b);
+  }
+}
+__device__ __forceinline__ zd dot2_value(const dot2c& a) {
+  return zd((double)a.sr + (double)a.er, (double)a.si + (double)a.ei);
+}
+
+constexpr int KDOT_CHUNK = 512;  // elements of w per block of k_kdots
+constexpr int KDOT_VECS = 8;     // basis vectors per block (one per warp)
+
+// h[jj] = sum over i < n of conj(V[jj][i]) w[i], jj < m; Hc[jj] = h[jj] (add = 0) or += h[jj].
+// Grid (chunks of 512 elements) x (groups of 8 basis vectors), warp q of a block takes vector
+// 8 blockIdx.y + q, each lane 16 elements 32 apart; the V loads are issued before the block splits
+// its chunk of w into shared memory, so that both latencies overlap. Each block writes its partial
+// sums to part[jj][chunk]; the block that finishes its vector group last (ticket[group], reset by it
+// for the next launch; the usual fence-and-counter pattern, no waiting) folds the group's partials.
+__global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ w,
+                                               long n, float4* part, zd* h, zd* Hc, int add, unsigned* ticket) {
+  __shared__ float4 ws[KDOT_CHUNK];
+  __shared__ bool last;
+  const long i0 = (long)blockIdx.x * KDOT_CHUNK;
+  const int lane = threadIdx.x & 31;
+  const int jj = blockIdx.y * KDOT_VECS + (threadIdx.x >> 5);
+  const int cnt = (int)min((long)KDOT_CHUNK, n - i0);
+  zd vr[KDOT_CHUNK / 32];
+  if (jj < m) {
+    const zd* v = V + (long)jj * ldv + i0;
+#pragma unroll
+    for (int k = 0; k < KDOT_CHUNK / 32; ++k) {
+      const int t = lane + 32 * k;
+      vr[k] = t < cnt ? v[t] : zd(0, 0);
+    }
+  }
+  for (int t = threadIdx.x; t < KDOT_CHUNK; t += blockDim.x)
+    ws[t] = t < cnt ? split_z(w[i0 + t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  if (jj < m) {
+    dot2c acc{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < KDOT_CHUNK / 32; ++k) dot2_mac(split_z(vr[k], true), ws[lane + 32 * k], acc);
+    warp_merge(acc);
+    if (lane == 0) part[(long)jj * gridDim.x + blockIdx.x] = pack_dot2(acc);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&ticket[blockIdx.y], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (jj < m) {
+    dot2c acc{0.f, 0.f, 0.f, 0.f};
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const float4 pv = __ldcg(&part[(long)jj * gridDim.x + b]);
+      dot2_merge(acc, unpack_dot2(pv));
+    }
+    warp_merge(acc);
+    if (lane == 0) {
+      const zd v = dot2_value(acc);
+      h[jj] = v;
+      if (Hc) Hc[jj] = add ? Hc[jj] + v : v;
+    }
+  }
+  if (threadIdx.x == 0) ticket[blockIdx.y] = 0;
+}
+// tickets: one counter per group of 8 basis vectors, zero before the first launch
+int kdots_groups(int m) { return (int)ceil_div(m, KDOT_VECS); }
+cudaError_t launch_kdots(const zd* V, int m, long ldv, const zd* w, long n, float4* part, zd* h, zd* Hc, int add,
+                         unsigned* ticket, cudaStream_t s) {
+  const int nchunk = (int)ceil_div(n, (long)KDOT_CHUNK);
+  k_kdots<<<dim3(nchunk, kdots_groups(m)), 256, 0, s>>>(V, m, ldv, w, n, part, h, Hc, add, ticket);
+  return cudaGetLastError();
+}
+int kupdate_blocks(long n) { return (int)ceil_div(n, 32L); }
+
+// w[i] -= sum_jj V[jj][i] h[jj], jj < m. A block takes 32 consecutive elements (threadIdx.x) and
+// splits the basis vectors among its 8 thread rows (threadIdx.y), four loads in flight per thread;
+// the first four are issued before h (the previous kernel's output) is read and split into shared
+// memory. The rows' sums are merged in shared memory and the FP64 result written once. With npart,
+// the block also writes the compensated sum of |w_new[i]|^2 over its elements to npart[blockIdx.x]
+// (the norm of the orthogonalised vector, for k_kscale).
+__global__ void __launch_bounds__(256) k_kupdate(zd* w, const zd* __restrict__ V, int m, long ldv,
+                                                 const zd* __restrict__ h, long n, float4* npart) {
+  __shared__ float4 hs[256];
+  __shared__ float4 rows[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+  const long i = (long)blockIdx.x * 32 + tx;
+  zd pre[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int jj = ty + 8 * u;
+    pre[u] = i < n && jj < m ? V[(long)jj * ldv + i] : zd(0, 0);
+  }
+  dot2c acc{0.f, 0.f, 0.f, 0.f};
+  for (int j0 = 0; j0 < m; j0 += 256) {
+    const int cnt = min(256, m - j0);
+    __syncthreads();
+    if (t < cnt) hs[t] = split_z(h[j0 + t]);
+    __syncthreads();
+    if (i >= n) continue;
+    for (int jb = ty; jb < cnt; jb += 32) {
+      zd v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = jb + 8 * u;
+        v[u] = j0 == 0 && jb == ty ? pre[u] : (jj < cnt ? V[(long)(j0 + jj) * ldv + i] : zd(0, 0));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (jb + 8 * u < cnt) dot2_mac(split_z(v[u]), hs[jb + 8 * u], acc);
+    }
+  }
+  rows[ty][tx] = pack_dot2(acc);
+  __syncthreads();
+  if (ty == 0) {
+    dot2c a = unpack_dot2(rows[0][tx]);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) dot2_merge(a, unpack_dot2(rows[r][tx]));
+    zd wn(0, 0);
+    if (i < n) {
+      wn = w[i] - dot2_value(a);
+      w[i] = wn;
+    }
+    if (npart) {
+      dot2c q{0.f, 0.f, 0.f, 0.f};
+      dot2_mac(split_z(wn, true), split_z(wn), q);
+      warp_merge(q);
+      if (tx == 0) npart[blockIdx.x] = pack_dot2(q);
+    }
+  }
+}
+cudaError_t launch_kupdate(zd* w, const zd* V, int m, long ldv, const zd* h, long n, float4* npart, cudaStream_t s) {
+  k_kupdate<<<kupdate_blocks(n), dim3(32, 8), 0, s>>>(w, V, m, ldv, h, n, npart);
+  return cudaGetLastError();
+}
+// |w| from the norm partials of k_kupdate (each block folds them itself); w /= |w|, or w = 0 when
+// |w| = 0 (breakdown); hsub = |w| (the subdiagonal entry h_{j+1,j}), written by block 0. A
+// non-finite |w| is stored as it is and propagates into w.
+__global__ void __launch_bounds__(256) k_kscale(zd* w, long n, const float4* __restrict__ npart, int nparts,
+                                                zd* hsub) {
+  __shared__ float4 red[8];
+  __shared__ double sc;
+  dot2c a{0.f, 0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) dot2_merge(a, unpack_dot2(npart[b]));
+  warp_merge(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pack_dot2(a);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double hn = sqrt(nrm2[0].re);
-    const int f = !isfinite(hn) ? 2 : (hn > 0 ? 0 : 1);
-    for (int i = 0; i < j; ++i) {
-      const zd a = hs[i], b = hs[i + 1];
-      hs[i] = conj(css[i]) * a + conj(sns[i]) * b;
-      hs[i + 1] = zd(0, 0) - sns[i] * a + css[i] * b;
-    }
-    const zd a = hs[j];
-    const double den = sqrt(abs2(a) + hn * hn);
-    const zd c = den > 0 ? a * (1.0 / den) : zd(1, 0);
-    const zd sj = den > 0 ? zd(hn / den, 0) : zd(0, 0);
-    cs[j] = c;
-    sn[j] = sj;
-    hs[j] = zd(den, 0);
-    hs[j + 1] = zd(0, 0);
-    const zd gj = g[j];
-    g[j + 1] = zd(0, 0) - sj * gj;
-    g[j] = conj(c) * gj;
-    res[j] = sqrt(abs2(g[j + 1]));
-    scale[0] = f == 0 ? 1.0 / hn : 0.0;
-    flag[j] = f;
+    dot2c q = unpack_dot2(red[0]);
+    for (int r = 1; r < (int)(blockDim.x >> 5); ++r) dot2_merge(q, unpack_dot2(red[r]));
+    const double hn = sqrt(dot2_value(q).re);
+    sc = hn > 0 ? 1.0 / hn : (hn == 0 ? 0.0 : hn);
+    if (blockIdx.x == 0) *hsub = zd(hn, 0);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hc[i] = hs[i];
-}
-// w *= scale[0]
-__global__ void k_scale_dev(zd* w, long n, const double* __restrict__ scale) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) w[i] = w[i] * scale[0];
+  if (i < n) w[i] = w[i] * sc;
 }
-cudaError_t launch_hcol(zd* Hc, const zd* h, int cnt, int add, cudaStream_t s) {
-  k_hcol<<<ceil_div(cnt, 128), 128, 0, s>>>(Hc, h, cnt, add);
-  return cudaGetLastError();
-}
-cudaError_t launch_givens_step(zd* Hc, int j, const zd* nrm2, zd* cs, zd* sn, zd* g, double* res, double* scale,
-                               int* flag, cudaStream_t s) {
-  const size_t sm = (size_t)(3 * j + 2) * sizeof(zd);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_givens_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_givens_step<<<1, 256, sm, s>>>(Hc, j, nrm2, cs, sn, g, res, scale, flag);
-  return cudaGetLastError();
-}
-cudaError_t launch_scale_dev(zd* w, long n, const double* scale, cudaStream_t s) {
-  k_scale_dev<<<ceil_div(n, 256), 256, 0, s>>>(w, n, scale);
+cudaError_t launch_kscale(zd* w, long n, const float4* npart, int nparts, zd* hsub, cudaStream_t s) {
+  k_kscale<<<ceil_div(n, 256L), 256, 0, s>>>(w, n, npart, nparts, hsub);
   return cudaGetLastError();
 }

@@ -48,3 +48,29 @@ def test_solves_reach_residual_and_energy_balance(name, make, eps_max, relres_ma
         sols[prec] = x
     d = float(torch.linalg.norm(sols[32] - sols[64]) / torch.linalg.norm(sols[64]))
     assert d < 1e-6, d
+
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_solve_residual_with_ragged_krylov_tiles(prec):
+    """GMRES with its float-float Arnoldi kernels on N = 1200 (ragged 512-element chunks and
+    32-element tiles): the solution's residual b - A x, recomputed with a separate application of
+    the FP64 operator, matches the reported relative residual and the 1e-12 target."""
+    par = I.wl_sinusoid_dirichlet(N=1200)
+    op = sgf.Operator(par, precision=prec)
+    try:
+        x = torch.zeros(par["N"], dtype=torch.complex128, device="cuda")
+        st, its, rr = sgf.sgf_solve(op.ctx, 1e-12, 4000, x.data_ptr())
+        assert st == 0 and rr <= 1e-12, (st, its, rr)
+        b = torch.empty_like(x)
+        sgf.sgf_rhs(op.ctx, b.data_ptr())
+    finally:
+        op.close()
+    op64 = sgf.Operator(par, precision=64)
+    try:
+        ax = torch.empty_like(x)
+        sgf.sgf_apply(op64.ctx, x.data_ptr(), ax.data_ptr())
+    finally:
+        op64.close()
+    res = float(torch.linalg.norm(b - ax) / torch.linalg.norm(b))
+    assert res < 2e-12, (res, rr)
