@@ -903,11 +903,40 @@ extern "C" sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev) {
 // ------------------------------------------------------------------ GMRES (restarted, CGS2)
 struct Krylov {
   zd *V = nullptr, *h = nullptr, *partial = nullptr, *r = nullptr;
-  zd* H = nullptr;  // Hessenberg columns written by the device, [m][m + 1] column-major
+  zd* H = nullptr;  // Hessenberg columns written by the device, [m][mrec + m + 1] column-major
+  zd* Q = nullptr;  // (mrec + 1) x mrec: the recycled space's combination coefficients
   float4 *part = nullptr, *npart = nullptr;  // float-float partial sums of the Arnoldi kernels
   unsigned* ticket = nullptr;                 // completion counters of k_kdots (zero between launches)
   int m = 0, nblk = 32;
+  int mrec = 0;  // vector slots in front of V for a recycled space C (C then V, contiguous)
 };
+
+// A Krylov space recycled from an earlier solve with the same operator, in the GCRO form of Parks,
+// de Sturler, Mackey, Johnson and Maiti ("Recycling Krylov subspaces for sequences of linear
+// systems", SIAM J. Sci. Comput. 28, 2006): C = A U with orthonormal columns (stored in the m slots
+// just before the Krylov basis V) and U = Vold R^{-1}, from that solve's Arnoldi relation
+// A V_m = V_{m+1} Hbar_m = (V_{m+1} Q_m) R. A later solve projects each cycle's residual onto the
+// complement of range(C) (adding U C^H r to x) and orthogonalises every new Arnoldi vector against
+// C together with its own basis; the coefficients against C, B = C^H A V_k, enter the solution as
+// x -= U B y. The mixed path's refinement solves one correction system per step with the same
+// operator; GMRES spends most of its first solve finding the few slow components of that
+// operator, and the recycled space carries them into the later corrections.
+struct Recycle {
+  int m = 0;           // columns of C and U
+  zd* Vold = nullptr;  // V_m of the solve it came from
+  std::vector<cd> R;   // m x m upper triangle (column-major, leading dimension m)
+};
+
+// z = R^{-1} c for the recycled triangle
+static void rec_solve(const Recycle& rc, const std::vector<cd>& c, std::vector<cd>& z) {
+  const int m = rc.m;
+  z.assign(m, cd(0));
+  for (int i = m - 1; i >= 0; --i) {
+    cd acc = c[i];
+    for (int k = i + 1; k < m; ++k) acc -= rc.R[(size_t)k * m + i] * z[k];
+    z[i] = acc / rc.R[(size_t)i * m + i];
+  }
+}
 
 static sgf_status dot_host(sgf_ctx* ctx, Krylov& K, const zd* V, int m, const zd* w, std::vector<cd>& out) {
   CU(launch_dots(V, m, ctx->N, w, ctx->N, K.partial, K.nblk, K.h, ctx->stream));
@@ -927,10 +956,15 @@ static sgf_status apply_op(sgf_ctx* ctx, const zd* x, zd* out, int prec, bool ad
 // true residual b - A x: if that is still above tol another cycle runs. Without it (inner solves
 // of the refinement) the estimate decides. Either way a cycle that reduces the true residual by
 // less than 10% ends the solve (attainable accuracy reached, or restarted GMRES stagnating).
+// rc: a recycled space of the same operator to deflate with; harvest: receives the space of this
+// solve's last cycle (its C is written in front of K.V, where a later solve with rc reads it).
 static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b, zd* x, double tol, int maxit,
-                        int* its, double* relres, bool true_check = true) {
+                        int* its, double* relres, bool true_check = true, const Recycle* rc = nullptr,
+                        Recycle* harvest = nullptr) {
   const long N = ctx->N;
   const int m = K.m;
+  const int mr = rc ? rc->m : 0;
+  const zd* Cb = K.V - (size_t)mr * N;  // [C | V]: the recycled space, then this solve's basis
   std::vector<cd> tmp;
   TRY(dot_host(ctx, K, b, 1, b, tmp));
   double bn = std::sqrt(tmp[0].real());
@@ -939,21 +973,39 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
   if (bn == 0) { *relres = 0; return SGF_OK; }
   int total = 0;
   double res = bn;
+  // x -= Vold z (z on the host)
+  auto sub_vold = [&](const std::vector<cd>& z) -> sgf_status {
+    CU(cudaMemcpyAsync(K.h, z.data(), z.size() * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+    CU(launch_kupdate(x, rc->Vold, (int)z.size(), N, K.h, N, nullptr, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return SGF_OK;
+  };
   // The Arnoldi steps run on the device without host round trips: CGS2 projections and updates in
   // float-float arithmetic, the Hessenberg column, the norm and the normalisation. Every kCheck
   // steps the host reads the new Hessenberg columns, applies the Givens rotations to them (FP64,
   // on the host) and takes the residual estimates; steps taken after the estimate reached tol
   // within such a group are counted as applications and otherwise discarded.
   constexpr int kCheck = 8;
-  const long ldh = m + 1;
+  const long ldh = mr + m + 1;  // column: mr coefficients against C, then the Hessenberg column
   const int nparts = kupdate_blocks(N);
-  std::vector<cd> Hh, g(m + 1), y(m), cs(m), sn(m);  // Hh grows with the columns in use
+  std::vector<cd> Hh, g(m + 1), y(m), cs(m), sn(m), z;  // Hh grows with the columns in use
   double prev_true = 0;
-  int cycles = 0;
+  int cycles = 0, jdone = 0;
   while (total < maxit) {
     // r = b - A x
     TRY(apply_op(ctx, x, K.r, prec, adj));
     CU(launch_axpby(K.r, zd(1, 0), b, zd(-1, 0), N, ctx->stream));
+    if (mr > 0) {
+      // c = C^H r; r -= C c; x += U c = Vold R^{-1} c
+      CU(launch_kdots(Cb, mr, N, K.r, N, K.part, K.h, nullptr, 0, K.ticket, ctx->stream));
+      CU(launch_kupdate(K.r, Cb, mr, N, K.h, N, nullptr, ctx->stream));
+      tmp.resize(mr);
+      CU(cudaMemcpyAsync(tmp.data(), K.h, mr * sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+      rec_solve(*rc, tmp, z);
+      for (auto& v : z) v = -v;
+      TRY(sub_vold(z));
+    }
     TRY(dot_host(ctx, K, K.r, 1, K.r, tmp));
     double beta = std::sqrt(tmp[0].real());
     res = beta;
@@ -965,7 +1017,8 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     CU(launch_axpby(K.V, zd(0, 0), K.V, zd(1.0 / beta, 0), N, ctx->stream));
     std::fill(g.begin(), g.end(), cd(0));
     g[0] = beta;
-    int jdone = 0, j = 0;
+    int j = 0;
+    jdone = 0;
     bool stop = false;
     while (!stop && j < m && total < maxit) {
       const int j0 = j, jend = std::min({m, j + kCheck, j + (maxit - total)});
@@ -975,20 +1028,21 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
         zd* Hc = K.H + (size_t)j * ldh;
         TRY(apply_op(ctx, vj, w, prec, adj));
         ++total;
-        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          CU(launch_kdots(K.V, j + 1, N, w, N, K.part, K.h, Hc, pass, K.ticket, ctx->stream));
-          CU(launch_kupdate(w, K.V, j + 1, N, K.h, N, pass == 1 ? K.npart : nullptr, ctx->stream));
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt against [C | V_0..V_j], twice
+          CU(launch_kdots(Cb, mr + j + 1, N, w, N, K.part, K.h, Hc, pass, K.ticket, ctx->stream));
+          CU(launch_kupdate(w, Cb, mr + j + 1, N, K.h, N, pass == 1 ? K.npart : nullptr, ctx->stream));
         }
-        CU(launch_kscale(w, N, K.npart, nparts, Hc + j + 1, ctx->stream));
+        CU(launch_kscale(w, N, K.npart, nparts, Hc + mr + j + 1, ctx->stream));
       }
       if (Hh.size() < (size_t)jend * ldh) Hh.resize((size_t)jend * ldh);
       CU(cudaMemcpy2DAsync(Hh.data() + (size_t)j0 * ldh, ldh * sizeof(zd), K.H + (size_t)j0 * ldh, ldh * sizeof(zd),
-                           (jend + 1) * sizeof(zd), jend - j0, cudaMemcpyDeviceToHost, ctx->stream));
+                           (mr + jend + 1) * sizeof(zd), jend - j0, cudaMemcpyDeviceToHost, ctx->stream));
       CU(cudaStreamSynchronize(ctx->stream));
       for (int jj = j0; jj < jend; ++jj) {
-        cd* col = Hh.data() + (size_t)jj * ldh;
-        for (int i = 0; i <= jj + 1; ++i)
-          if (!std::isfinite(col[i].real()) || !std::isfinite(col[i].imag()))
+        cd* colB = Hh.data() + (size_t)jj * ldh;
+        cd* col = colB + mr;
+        for (int i = 0; i <= mr + jj + 1; ++i)
+          if (!std::isfinite(colB[i].real()) || !std::isfinite(colB[i].imag()))
             return set_err(ctx, SGF_ENONFINITE, "non-finite Krylov vector");
         for (int i = 0; i < jj; ++i) {  // earlier rotations
           const cd a = col[i], bb = col[i + 1];
@@ -1007,7 +1061,8 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
         jdone = jj + 1;
         res = std::abs(g[jj + 1]);
         if (getenv("SGF_VERBOSE"))
-          fprintf(stderr, "gmres prec %d it %d j %d res %.3e\n", prec, total - (jend - 1 - jj), jj, res / bn);
+          fprintf(stderr, "gmres prec %d rec %d it %d j %d res %.3e\n", prec, mr, total - (jend - 1 - jj), jj,
+                  res / bn);
         if (res / bn <= tol || hn == 0) {  // converged, or breakdown (the Krylov space is invariant)
           stop = true;
           break;
@@ -1017,8 +1072,8 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     // back-substitution with the rotated triangle R (columns 0..jdone-1, rows 0..jdone-1)
     for (int i = jdone - 1; i >= 0; --i) {
       cd sacc = g[i];
-      for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= Hh[(size_t)k2 * ldh + i] * y[k2];
-      y[i] = sacc / Hh[(size_t)i * ldh + i];
+      for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= Hh[(size_t)k2 * ldh + mr + i] * y[k2];
+      y[i] = sacc / Hh[(size_t)i * ldh + mr + i];
     }
     std::vector<cd> ny(jdone);
     for (int i = 0; i < jdone; ++i) ny[i] = -y[i];
@@ -1026,8 +1081,43 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
       CU(cudaMemcpyAsync(K.h, ny.data(), jdone * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
       CU(launch_kupdate(x, K.V, jdone, N, K.h, N, nullptr, ctx->stream));
     }
+    if (mr > 0 && jdone > 0) {
+      // x -= U B y = Vold R^{-1} (B y)
+      std::vector<cd> t(mr, cd(0));
+      for (int k2 = 0; k2 < jdone; ++k2)
+        for (int i = 0; i < mr; ++i) t[i] += Hh[(size_t)k2 * ldh + i] * y[k2];
+      rec_solve(*rc, t, z);
+      TRY(sub_vold(z));
+    }
     CU(cudaStreamSynchronize(ctx->stream));
     if (!true_check && res / bn <= tol) break;
+  }
+  if (harvest && mr == 0 && jdone >= 4 && harvest->Vold) {
+    // the last cycle's space: m_h <= K.mrec leading columns of its Arnoldi relation, whose QR is
+    // given by the first m_h Givens rotations: R (rotated columns) and Q_m = G_1^H ... G_m^H [I; 0]
+    const int mh = std::min(jdone, K.mrec);
+    harvest->m = mh;
+    harvest->R.assign((size_t)mh * mh, cd(0));
+    for (int k2 = 0; k2 < mh; ++k2)
+      for (int i = 0; i <= k2; ++i) harvest->R[(size_t)k2 * mh + i] = Hh[(size_t)k2 * ldh + i];
+    std::vector<cd> q((size_t)(mh + 1) * mh, cd(0));
+    for (int k2 = 0; k2 < mh; ++k2) {
+      cd* qc = q.data() + (size_t)k2 * (mh + 1);
+      qc[k2] = 1;
+      for (int i = mh - 1; i >= 0; --i) {  // G_i^H on rows (i, i+1)
+        const cd a = qc[i], bb = qc[i + 1];
+        qc[i] = cs[i] * a - std::conj(sn[i]) * bb;
+        qc[i + 1] = sn[i] * a + std::conj(cs[i]) * bb;
+      }
+      for (int i = 0; i <= mh; ++i) qc[i] = -qc[i];  // kupdate subtracts
+    }
+    zd* C = K.V - (size_t)mh * N;
+    CU(cudaMemcpyAsync(K.Q, q.data(), q.size() * sizeof(zd), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(C, 0, (size_t)mh * N * sizeof(zd), ctx->stream));
+    for (int k2 = 0; k2 < mh; ++k2)  // C_k = V_{m+1} Q[:, k]
+      CU(launch_kupdate(C + (size_t)k2 * N, K.V, mh + 1, N, K.Q + (size_t)k2 * (mh + 1), N, nullptr, ctx->stream));
+    CU(cudaMemcpyAsync(harvest->Vold, K.V, (size_t)mh * N * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
   }
   // true residual
   TRY(apply_op(ctx, x, K.r, prec, adj));
@@ -1064,18 +1154,26 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
     mine.push_back(*p);
     return SGF_OK;
   };
+  // the mixed path's refinement recycles up to 256 vectors of its first correction solve
+  const bool mixed = !(ctx->prm.precision == 64 || ctx->op_exact);
+  K.mrec = mixed && !getenv("SGF_NO_RECYCLE") ? std::min(K.m, 256) : 0;
   const long nchunk = (N + 511) / 512;
-  if ((st = al(&K.H, (size_t)(K.m + 1) * K.m)) || (st = al(&K.V, (size_t)(K.m + 1) * N)) ||
-      (st = al(&K.h, (size_t)K.m + 2)) || (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
-      (st = alb((void**)&K.part, (size_t)nchunk * (K.m + 1) * sizeof(float4))) ||
+  const size_t nvec = (size_t)K.mrec + K.m + 1;  // [recycled C | Krylov basis V]
+  zd* W = nullptr;
+  Recycle rc;
+  if ((st = al(&K.H, (size_t)(K.mrec + K.m + 1) * K.m)) || (st = al(&W, nvec * N)) ||
+      (st = al(&K.h, (size_t)K.mrec + K.m + 2)) || (st = al(&K.partial, (size_t)(K.m + 2) * K.nblk)) ||
+      (st = alb((void**)&K.part, (size_t)nchunk * nvec * sizeof(float4))) ||
       (st = alb((void**)&K.npart, (size_t)kupdate_blocks(N) * sizeof(float4))) ||
-      (st = alb((void**)&K.ticket, (size_t)kdots_groups(K.m + 1) * sizeof(unsigned))) ||
+      (st = alb((void**)&K.ticket, (size_t)kdots_groups((int)nvec) * sizeof(unsigned))) ||
+      (K.mrec > 0 && ((st = al(&K.Q, (size_t)(K.mrec + 1) * K.mrec)) || (st = al(&rc.Vold, (size_t)K.mrec * N)))) ||
       (st = al(&K.r, N)) ||
       (st = al(&b, N)) || (st = al(&x, N)) || (st = al(&dlt, N))) {
     for (void* p : mine) cudaFree(p);
     return st;
   }
-  cudaMemsetAsync(K.ticket, 0, (size_t)kdots_groups(K.m + 1) * sizeof(unsigned), ctx->stream);
+  K.V = W + (size_t)K.mrec * N;
+  cudaMemsetAsync(K.ticket, 0, (size_t)kdots_groups((int)nvec) * sizeof(unsigned), ctx->stream);
   int its = 0;
   double rr = 1;
   if (b_in)
@@ -1106,8 +1204,10 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
       int it_in = 0;
       double rr_in = 1;
       double itol = fp64_inner ? std::min(0.5, tol / rr_prev) : 1e-6;
+      // the first mixed correction solve leaves its Krylov space for the later ones
+      const bool use_rc = !fp64_inner && rc.m > 0;
       st = gmres(ctx, K, fp64_inner ? 64 : 32, adj, r, dlt, itol, maxit - its > 0 ? maxit - its : 1, &it_in, &rr_in,
-                 fp64_inner);
+                 fp64_inner, use_rc ? &rc : nullptr, !fp64_inner && outer == 0 && K.mrec > 0 ? &rc : nullptr);
       if (st != SGF_OK) break;
       its += it_in;
       launch_axpby(x, zd(1, 0), dlt, zd(1, 0), N, ctx->stream);
@@ -1118,8 +1218,8 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
       st = dot_host(ctx, K, r, 1, r, tmp);
       rr = std::sqrt(tmp[0].real()) / bn;
       if (getenv("SGF_VERBOSE"))
-        fprintf(stderr, "refinement %d inner %s its %d outer rr %.3e\n", outer, fp64_inner ? "fp64" : "mixed", it_in,
-                rr);
+        fprintf(stderr, "refinement %d inner %s (recycled %d) its %d outer rr %.3e\n", outer,
+                fp64_inner ? "fp64" : "mixed", use_rc ? rc.m : 0, it_in, rr);
       if (rr <= tol || its >= maxit) break;
       if (fp64_inner && rr > 0.5 * rr_prev) break;  // the FP64 correction stagnated as well
       if (rr > 0.1 * rr_prev) fp64_inner = true;

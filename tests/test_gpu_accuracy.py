@@ -74,3 +74,26 @@ def test_solve_residual_with_ragged_krylov_tiles(prec):
         op64.close()
     res = float(torch.linalg.norm(b - ax) / torch.linalg.norm(b))
     assert res < 2e-12, (res, rr)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("deep_corrugation", I.wl_deep_corrugation_neumann),
+    ("double_wood_sinusoid", I.wl_sinusoid_dirichlet_energy),
+])
+def test_recycled_refinement_matches_plain_refinement(monkeypatch, name, make):
+    """The mixed path's later correction solves deflate with the Krylov space of the first one
+    (GCRO form): the solution is the same to the solve tolerance as with plain refinement, and on
+    the deep corrugation, whose GMRES spends most iterations finding a few slow components, it takes
+    fewer applications."""
+    par = make()
+    monkeypatch.delenv("SGF_NO_RECYCLE", raising=False)
+    st1, its1, rr1, eps1, x1 = _solve(par, 32)
+    monkeypatch.setenv("SGF_NO_RECYCLE", "1")
+    st2, its2, rr2, eps2, x2 = _solve(par, 32)
+    assert st1 == st2 == 0, (st1, st2)
+    assert rr1 <= 1e-12 and rr2 <= 1e-12, (rr1, rr2)
+    d = float(torch.linalg.norm(x1 - x2) / torch.linalg.norm(x2))
+    assert d < 1e-10, d
+    assert abs(eps1 - eps2) < 1e-10, (eps1, eps2)
+    if name == "deep_corrugation":
+        assert its1 < 0.8 * its2, (its1, its2)
