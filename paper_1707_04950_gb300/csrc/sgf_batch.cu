@@ -606,11 +606,18 @@ sgf_status sgf_batch_apply(sgf_batch* B, const void* const* mu_devs, void* const
 // ------------------------------------------------------------------ lockstep GMRES
 struct BWork {
   int m = 0;
-  zd** d_V = nullptr;   // [p] Krylov basis, (m + 1) vectors of N_p
+  int mrec = 0;         // recycled-vector slots in front of every problem's basis
+  int rec_m = 0;        // columns of the recycled space in use (common to the batch; 0: none)
+  zd** d_V = nullptr;   // [p] Krylov basis, (m + 1) vectors of N_p, after mrec recycled slots
+  zd** d_C = nullptr;   // [p] the recycled space C_p = V_p - rec_m N_p
+  zd** d_Vold = nullptr;  // [p] V_m of the solve the recycled space came from
   zd** d_r = nullptr;   // [p] residual / work vector
-  zd* d_h = nullptr;    // [p][m + 1] coefficients
+  zd* d_h = nullptr;    // [p][mrec + m + 2] coefficients of the FP64 helpers
   double* d_s = nullptr;
-  std::vector<zd*> V, r;
+  KStep* d_ks = nullptr;  // [p] state of the float-float Arnoldi step
+  std::vector<KStep> ks;
+  std::vector<zd*> V, Vold;
+  std::vector<std::vector<cd>> R;  // [p] rec_m x rec_m upper triangles (column-major)
 };
 
 // h_out[p][j] = V_p[j0 + j]^H w_p (j < m), synchronised to the host.
@@ -630,12 +637,22 @@ static sgf_status bscale(sgf_batch* B, BWork& W, zd** t, int k, const std::vecto
   return SGF_OK;
 }
 
-// w_p[wk] -= V_p[0..m) h[p][.] with host coefficients (m_stride entries per problem)
+// w_p[wk] -= V_p[0..m) h[p][.] with host coefficients (m entries per problem)
 static sgf_status bupdate(sgf_batch* B, BWork& W, zd** wt, int wk, zd** Vt, int m, const std::vector<cd>& h) {
   BCU(cudaMemcpyAsync(W.d_h, h.data(), (size_t)B->n * m * sizeof(zd), cudaMemcpyHostToDevice, B->stream));
   k_bupdate<<<bgrid(B), 256, 0, B->stream>>>(wt, wk, Vt, m, W.d_h, B->d_N);
   BCU(cudaGetLastError());
+  BCU(cudaStreamSynchronize(B->stream));  // h is host memory of the caller
   return SGF_OK;
+}
+
+// z = R^{-1} c for an rm x rm upper triangle (column-major)
+static void btri_solve(const std::vector<cd>& R, int rm, const cd* c, cd* z) {
+  for (int i = rm - 1; i >= 0; --i) {
+    cd acc = c[i];
+    for (int k = i + 1; k < rm; ++k) acc -= R[(size_t)k * rm + i] * z[k];
+    z[i] = acc / R[(size_t)i * rm + i];
+  }
 }
 
 // Lockstep restarted GMRES from x = 0 on A_p x_p = b_p for every problem, operators of graph slot
@@ -643,10 +660,15 @@ static sgf_status bupdate(sgf_batch* B, BWork& W, zd** wt, int wk, zd** Vt, int 
 // reaches its tolerance: with true_check the true residual at the start of a cycle decides,
 // without (inner solves of the refinement) the Arnoldi estimate does. A cycle that reduces the true
 // residual by less than 10% also ends the problem (attainable accuracy or stagnation).
+// The Arnoldi steps are those of sgf_solve for all problems at once (float-float CGS2 on the
+// device, Givens rotations on the host every 8 steps). use_rc: deflate with the recycled spaces
+// (GCRO form, as in sgf_solve); harvest: leave this solve's spaces (the leading columns common to
+// every problem) for later solves with the same operators.
 static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, const std::vector<zd*>& xs,
                          const std::vector<double>& tolv, bool true_check, int maxit, std::vector<int>& its,
-                         std::vector<double>& rr) {
+                         std::vector<double>& rr, bool use_rc = false, bool harvest = false) {
   const int n = B->n, m = W.m;
+  const int mr = use_rc ? W.rec_m : 0;
   std::vector<cd> tmp;
   for (int p = 0; p < n; ++p) BCU(cudaMemsetAsync(xs[p], 0, B->N[p] * sizeof(zd), B->stream));  // x = 0
   BTRY(bdots(B, W, bt, 1, bt, 0, tmp));
@@ -655,13 +677,21 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
   for (int p = 0; p < n; ++p) {
     bn[p] = std::sqrt(tmp[p].real());
     its[p] = 0;
+    if (!std::isfinite(bn[p])) return berr(B, SGF_ENONFINITE, "non-finite right-hand side (problem %d)", p);
     if (bn[p] == 0) done[p] = 1;
   }
-  // Hessenberg matrices: every entry is written before it is read, so the (large, mostly untouched
-  // for short solves) storage is left uninitialised; std::complex<double> is laid out as double[2]
-  std::unique_ptr<double[]> Hraw(new double[(size_t)2 * n * (m + 1) * m]);
-  cd* H = reinterpret_cast<cd*>(Hraw.get());
-  std::vector<cd> cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
+  // the step kernels' table: problem p's basis starts at its mr recycled vectors
+  const long ldh = (long)W.mrec + m + 1;
+  for (int p = 0; p < n; ++p) {
+    W.ks[p].W = W.V[p] - (size_t)mr * B->N[p];
+    W.ks[p].mr = mr;
+    W.ks[p].ldh = ldh;
+  }
+  BCU(cudaMemcpyAsync(W.d_ks, W.ks.data(), n * sizeof(KStep), cudaMemcpyHostToDevice, B->stream));
+  BCU(cudaStreamSynchronize(B->stream));
+  constexpr int kCheck = 8;
+  std::vector<std::vector<cd>> Hh(n);
+  std::vector<cd> cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1)), z((size_t)n * std::max(1, mr));
   std::vector<int> jdone(n, 0);
   std::vector<double> sc(n), prev_true(n, 0.0);
   int total = 0, cycles = 0;
@@ -677,6 +707,19 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
       BCU(cudaGetLastError());
     }
     first = false;
+    if (mr > 0) {
+      // c = C^H r; r -= C c; x += U c = Vold R^{-1} c
+      BTRY(bdots(B, W, W.d_C, mr, W.d_r, 0, tmp));
+      std::vector<cd> c(tmp), nz((size_t)n * mr);
+      for (int p = 0; p < n; ++p) {
+        if (done[p] || tolv[p] >= 1.0)  // nothing to do for this problem: leave its iterate alone
+          std::fill(c.begin() + (size_t)p * mr, c.begin() + (size_t)(p + 1) * mr, cd(0));
+        btri_solve(W.R[p], mr, c.data() + (size_t)p * mr, nz.data() + (size_t)p * mr);
+        for (int i = 0; i < mr; ++i) nz[(size_t)p * mr + i] = -nz[(size_t)p * mr + i];
+      }
+      BTRY(bupdate(B, W, W.d_r, 0, W.d_C, mr, c));
+      BTRY(bupdate(B, W, xt, 0, W.d_Vold, mr, nz));
+    }
     BTRY(bdots(B, W, W.d_r, 1, W.d_r, 0, tmp));
     bool any = false;
     for (int p = 0; p < n; ++p) {
@@ -698,73 +741,83 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
     BTRY(bscale(B, W, W.d_V, 0, sc));
     std::vector<char> live(n);
     for (int p = 0; p < n; ++p) live[p] = !done[p];
-    int jj = 0;
-    for (; jj < m && total < maxit; ++jj) {
-      BTRY(bapply(B, slot, W.d_V, jj, W.d_V, jj + 1));
-      ++total;
-      for (int p = 0; p < n; ++p)
-        if (live[p]) ++its[p];
-      std::vector<cd> h1, h2;
-      BTRY(bdots(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h1));
-      BTRY(bupdate(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h1));
-      BTRY(bdots(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h2));
-      BTRY(bupdate(B, W, W.d_V, jj + 1, W.d_V, jj + 1, h2));
-      BTRY(bdots(B, W, W.d_V, 1, W.d_V, jj + 1, tmp, jj + 1));  // |w|^2
-      bool any_live = false;
+    int j = 0;
+    bool any_live = true;
+    while (any_live && j < m && total < maxit) {
+      const int j0 = j, jend = std::min({m, j + kCheck, j + (maxit - total)});
+      for (; j < jend; ++j) {
+        BTRY(bapply(B, slot, W.d_V, j, W.d_V, j + 1));
+        ++total;
+        for (int p = 0; p < n; ++p)
+          if (live[p]) ++its[p];
+        BCU(launch_batch_arnoldi_step(W.d_ks, n, j, mr, B->maxN, B->stream));
+      }
       for (int p = 0; p < n; ++p) {
-        double hn = std::sqrt(std::max(0.0, tmp[p].real()));
-        sc[p] = 0.0;
         if (!live[p]) continue;
-        if (!std::isfinite(hn)) return berr(B, SGF_ENONFINITE, "non-finite Krylov vector (problem %d)", p);
-        cd* Hp = &H[(size_t)p * (m + 1) * m];
-        for (int i = 0; i <= jj; ++i) Hp[(size_t)i * m + jj] = h1[(size_t)p * (jj + 1) + i] + h2[(size_t)p * (jj + 1) + i];
-        Hp[(size_t)(jj + 1) * m + jj] = hn;
+        if (Hh[p].size() < (size_t)jend * ldh) Hh[p].resize((size_t)jend * ldh);
+        BCU(cudaMemcpy2DAsync(Hh[p].data() + (size_t)j0 * ldh, ldh * sizeof(zd), W.ks[p].H + (size_t)j0 * ldh,
+                              ldh * sizeof(zd), (mr + jend + 1) * sizeof(zd), jend - j0, cudaMemcpyDeviceToHost,
+                              B->stream));
+      }
+      BCU(cudaStreamSynchronize(B->stream));
+      any_live = false;
+      for (int p = 0; p < n; ++p) {
+        if (!live[p]) continue;
         cd* csp = &cs[(size_t)p * m];
         cd* snp = &sn[(size_t)p * m];
         cd* gp = &g[(size_t)p * (m + 1)];
-        for (int i = 0; i < jj; ++i) {
-          cd a = Hp[(size_t)i * m + jj], bb = Hp[(size_t)(i + 1) * m + jj];
-          Hp[(size_t)i * m + jj] = std::conj(csp[i]) * a + std::conj(snp[i]) * bb;
-          Hp[(size_t)(i + 1) * m + jj] = -snp[i] * a + csp[i] * bb;
+        for (int jj = j0; jj < jend && live[p]; ++jj) {
+          cd* colB = Hh[p].data() + (size_t)jj * ldh;
+          cd* col = colB + mr;
+          for (int i = 0; i <= mr + jj + 1; ++i)
+            if (!std::isfinite(colB[i].real()) || !std::isfinite(colB[i].imag()))
+              return berr(B, SGF_ENONFINITE, "non-finite Krylov vector (problem %d)", p);
+          for (int i = 0; i < jj; ++i) {
+            const cd a = col[i], bb = col[i + 1];
+            col[i] = std::conj(csp[i]) * a + std::conj(snp[i]) * bb;
+            col[i + 1] = -snp[i] * a + csp[i] * bb;
+          }
+          const double hn = col[jj + 1].real();
+          const cd a = col[jj];
+          const double den = std::sqrt(std::norm(a) + hn * hn);
+          csp[jj] = den > 0 ? a / den : cd(1);
+          snp[jj] = den > 0 ? cd(hn / den) : cd(0);
+          col[jj] = den;
+          col[jj + 1] = 0;
+          gp[jj + 1] = -snp[jj] * gp[jj];
+          gp[jj] = std::conj(csp[jj]) * gp[jj];
+          jdone[p] = jj + 1;
+          res[p] = std::abs(gp[jj + 1]);
+          if (res[p] / bn[p] <= tolv[p] || !(hn > 0)) live[p] = 0;
         }
-        cd a = Hp[(size_t)jj * m + jj], bb = Hp[(size_t)(jj + 1) * m + jj];
-        double den = std::sqrt(std::norm(a) + std::norm(bb));
-        csp[jj] = den > 0 ? a / den : cd(1);
-        snp[jj] = den > 0 ? bb / den : cd(0);
-        Hp[(size_t)jj * m + jj] = den;
-        Hp[(size_t)(jj + 1) * m + jj] = 0;
-        gp[jj + 1] = -snp[jj] * gp[jj];
-        gp[jj] = std::conj(csp[jj]) * gp[jj];
-        jdone[p] = jj + 1;
-        res[p] = std::abs(gp[jj + 1]);
-        if (res[p] / bn[p] <= tolv[p] || !(hn > 0)) live[p] = 0;
-        if (live[p]) sc[p] = 1.0 / hn;
         any_live = any_live || live[p];
       }
-      BTRY(bscale(B, W, W.d_V, jj + 1, sc));
-      if (!any_live) {
-        ++jj;
-        break;
-      }
     }
-    // x_p += V_p y_p (back substitution per problem; coefficients zero past jdone_p)
+    // x_p += V_p y_p - U_p B_p y_p (back substitution per problem; coefficients zero past jdone_p)
     int mm = 0;
     for (int p = 0; p < n; ++p) mm = std::max(mm, jdone[p]);
     if (mm > 0) {
-      std::vector<cd> ny((size_t)n * mm, cd(0));
+      std::vector<cd> ny((size_t)n * mm, cd(0)), nz((size_t)n * std::max(1, mr), cd(0));
       for (int p = 0; p < n; ++p) {
-        if (done[p]) continue;
-        const cd* Hp = &H[(size_t)p * (m + 1) * m];
+        if (done[p] || jdone[p] == 0) continue;
+        const cd* Hp = Hh[p].data();
         const cd* gp = &g[(size_t)p * (m + 1)];
         std::vector<cd> y(jdone[p]);
         for (int i = jdone[p] - 1; i >= 0; --i) {
-          cd s = gp[i];
-          for (int k2 = i + 1; k2 < jdone[p]; ++k2) s -= Hp[(size_t)i * m + k2] * y[k2];
-          y[i] = s / Hp[(size_t)i * m + i];
+          cd acc = gp[i];
+          for (int k2 = i + 1; k2 < jdone[p]; ++k2) acc -= Hp[(size_t)k2 * ldh + mr + i] * y[k2];
+          y[i] = acc / Hp[(size_t)i * ldh + mr + i];
         }
         for (int i = 0; i < jdone[p]; ++i) ny[(size_t)p * mm + i] = -y[i];
+        if (mr > 0) {
+          std::vector<cd> t(mr, cd(0));
+          for (int k2 = 0; k2 < jdone[p]; ++k2)
+            for (int i = 0; i < mr; ++i) t[i] += Hp[(size_t)k2 * ldh + i] * y[k2];
+          btri_solve(W.R[p], mr, t.data(), nz.data() + (size_t)p * mr);
+        }
       }
       BTRY(bupdate(B, W, xt, 0, W.d_V, mm, ny));
+      if (mr > 0) BTRY(bupdate(B, W, xt, 0, W.d_Vold, mr, nz));
     }
     if (!true_check) {
       bool all = true;
@@ -773,6 +826,47 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
         all = all && done[p];
       }
       if (all) break;
+    }
+  }
+  if (harvest && mr == 0 && W.mrec > 0) {
+    // leading columns common to the batch of every problem's last cycle: R_p (rotated columns),
+    // C_p = V_p Q_p with Q_p = G_1^H ... G_mh^H [I; 0], written just in front of V_p
+    int mh = W.mrec;
+    for (int p = 0; p < n; ++p)
+      if (bn[p] > 0) mh = std::min(mh, jdone[p]);
+    W.rec_m = 0;
+    if (mh >= 4) {
+      std::vector<std::vector<cd>> hq((size_t)mh, std::vector<cd>((size_t)n * (mh + 1), cd(0)));
+      for (int p = 0; p < n; ++p) {
+        W.R[p].assign((size_t)mh * mh, cd(1));
+        if (bn[p] == 0) continue;  // zero right-hand side: C_p = 0 columns are never used (c = 0)
+        const cd* Hp = Hh[p].data();
+        for (int k2 = 0; k2 < mh; ++k2)
+          for (int i = 0; i < mh; ++i) W.R[p][(size_t)k2 * mh + i] = i <= k2 ? Hp[(size_t)k2 * ldh + i] : cd(0);
+        const cd* csp = &cs[(size_t)p * m];
+        const cd* snp = &sn[(size_t)p * m];
+        std::vector<cd> q(mh + 1);
+        for (int k2 = 0; k2 < mh; ++k2) {
+          std::fill(q.begin(), q.end(), cd(0));
+          q[k2] = 1;
+          for (int i = mh - 1; i >= 0; --i) {
+            const cd a = q[i], bb = q[i + 1];
+            q[i] = csp[i] * a - std::conj(snp[i]) * bb;
+            q[i + 1] = snp[i] * a + std::conj(csp[i]) * bb;
+          }
+          for (int i = 0; i <= mh; ++i) hq[k2][(size_t)p * (mh + 1) + i] = -q[i];
+        }
+      }
+      std::vector<zd*> Ch(n);
+      for (int p = 0; p < n; ++p) {
+        Ch[p] = W.V[p] - (size_t)mh * B->N[p];
+        BCU(cudaMemsetAsync(Ch[p], 0, (size_t)mh * B->N[p] * sizeof(zd), B->stream));
+        BCU(cudaMemcpyAsync(W.Vold[p], W.V[p], (size_t)mh * B->N[p] * sizeof(zd), cudaMemcpyDeviceToDevice,
+                            B->stream));
+      }
+      BCU(cudaMemcpyAsync(W.d_C, Ch.data(), n * sizeof(zd*), cudaMemcpyHostToDevice, B->stream));
+      for (int k2 = 0; k2 < mh; ++k2) BTRY(bupdate(B, W, W.d_C, k2, W.d_V, mh + 1, hq[k2]));
+      W.rec_m = mh;
     }
   }
   // true residuals
@@ -811,11 +905,28 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
   sgf_status st = SGF_OK;
   std::vector<zd*> bv(n), xv(n), dv(n), rv(n), Vv(n), r2(n);
   zd **d_bt = nullptr, **d_xt = nullptr, **d_dt = nullptr, **d_r2 = nullptr;
+  // the mixed refinement's later correction solves recycle up to 256 vectors of the first one
+  W.mrec = B->any_mixed && !getenv("SGF_NO_RECYCLE") ? std::min(W.m, 256) : 0;
+  const size_t nvec = (size_t)W.mrec + W.m + 1;
+  const int nchunk = (int)((B->maxN + 511) / 512);
+  W.ks.assign(n, KStep{});
+  W.V.assign(n, nullptr);
+  W.Vold.assign(n, nullptr);
+  W.R.assign(n, std::vector<cd>());
   for (int p = 0; p < n && st == SGF_OK; ++p) {
     long N = B->N[p];
-    if ((st = al(&Vv[p], (size_t)(W.m + 1) * N)) || (st = al(&rv[p], N)) || (st = al(&bv[p], N)) ||
-        (st = al(&dv[p], N)) || (st = al(&r2[p], N)))
+    zd* base = nullptr;
+    if ((st = al(&base, nvec * N)) || (st = al(&rv[p], N)) || (st = al(&bv[p], N)) || (st = al(&dv[p], N)) ||
+        (st = al(&r2[p], N)) || (st = al(&W.ks[p].H, nvec * W.m)) || (st = al(&W.ks[p].h, nvec + 1)) ||
+        (st = al((zd**)&W.ks[p].part, (size_t)nchunk * nvec)) ||
+        (st = al((zd**)&W.ks[p].npart, (size_t)kupdate_blocks(B->maxN))) ||
+        (st = al((zd**)&W.ks[p].ticket, (size_t)kdots_groups((int)nvec) / 4 + 1)) ||
+        (W.mrec > 0 && (st = al(&W.Vold[p], (size_t)W.mrec * N))))
       break;
+    cudaMemsetAsync(W.ks[p].ticket, 0, (size_t)kdots_groups((int)nvec) * sizeof(unsigned), B->stream);
+    Vv[p] = base + (size_t)W.mrec * N;
+    W.V[p] = Vv[p];
+    W.ks[p].n = N;
     xv[p] = (zd*)mu_devs[p];
   }
   auto tab = [&](zd*** d, const std::vector<zd*>& h) -> sgf_status {
@@ -825,13 +936,16 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
     return e == cudaSuccess ? SGF_OK : berr(B, SGF_ECUDA, "table upload: %s", cudaGetErrorString(e));
   };
   if (st == SGF_OK) st = tab(&W.d_V, Vv);
+  if (st == SGF_OK) st = tab(&W.d_C, Vv);
+  if (st == SGF_OK) st = tab(&W.d_Vold, W.mrec > 0 ? W.Vold : Vv);
   if (st == SGF_OK) st = tab(&W.d_r, rv);
   if (st == SGF_OK) st = tab(&d_bt, bv);
   if (st == SGF_OK) st = tab(&d_xt, xv);
   if (st == SGF_OK) st = tab(&d_dt, dv);
   if (st == SGF_OK) st = tab(&d_r2, r2);
-  if (st == SGF_OK) st = al(&W.d_h, (size_t)n * (W.m + 2));
+  if (st == SGF_OK) st = al(&W.d_h, (size_t)n * (nvec + 1));
   if (st == SGF_OK) st = al((zd**)&W.d_s, (n + 1) / 2 + 1);
+  if (st == SGF_OK) st = al((zd**)&W.d_ks, (n * sizeof(KStep) + sizeof(zd) - 1) / sizeof(zd));
   if (st != SGF_OK) {
     cleanup();
     return st;
@@ -868,8 +982,9 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
     for (int outer = 0; outer < 30 && st == SGF_OK; ++outer) {
       for (int p = 0; p < n; ++p)
         tolv[p] = fin[p] ? 1.0 : (fp64_inner ? std::min(0.5, tol / rr_prev[p]) : 1e-6);
+      // the first mixed correction solve leaves its Krylov spaces for the later ones
       st = bgmres(B, W, fp64_inner ? 1 : 0, d_r2, d_dt, dv, tolv, fp64_inner, std::max(1, maxit - used), it_in,
-                  rr_in);
+                  rr_in, !fp64_inner && W.rec_m > 0, !fp64_inner && outer == 0);
       if (st != SGF_OK) break;
       int mx = 0;
       for (int p = 0; p < n; ++p) {

@@ -285,6 +285,24 @@ cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s)
 cudaError_t launch_kdots(const zd* V, int m, long ldv, const zd* w, long n, float4* part, zd* h, zd* Hc, int add,
                          unsigned* ticket, cudaStream_t s);
 int kdots_groups(int m);
+// One problem's state for the batched Arnoldi step: basis [C | V] (mr recycled vectors, then the
+// Krylov vectors, n apart), Hessenberg storage (column j at H + j ldh: mr coefficients against C,
+// then the column), coefficient scratch h, float-float partials (part: ceil(n_max / 512) per basis
+// vector; npart: kupdate_blocks(n_max)), k_kdots tickets (kdots_groups(mr + m + 1), zero).
+struct KStep {
+  zd* W;
+  zd* H;
+  zd* h;
+  float4* part;
+  float4* npart;
+  unsigned* ticket;
+  long n, ldh;
+  int mr, pad_;
+};
+// Step j of every problem of the table (device array of nprob entries): CGS2 against
+// [C | V_0..V_j], the norm and the normalisation of V_{j+1}; n_max the largest n, mr_max the
+// largest mr.
+cudaError_t launch_batch_arnoldi_step(const KStep* d_tab, int nprob, int j, int mr_max, long n_max, cudaStream_t s);
 
 cudaError_t launch_kupdate(zd* w, const zd* V, int m, long ldv, const zd* h, long n, float4* npart, cudaStream_t s);
 cudaError_t launch_kscale(zd* w, long n, const float4* npart, int nparts, zd* hsub, cudaStream_t s);

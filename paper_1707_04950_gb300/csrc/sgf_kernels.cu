@@ -1137,11 +1137,12 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
     long gi = samp_gidx[(long)q * nfit + t];
     ph[t] = t < 2 * (pH + 1) ? phiH[gi] : phiV[gi];
   }
-  if (warp < nm && (mask & 4)) {  // mode sums from their chunk partials (warp per mode)
+  // mode sums from their chunk partials: warp w folds modes w, w + 4, ... (up to 8 modes, 4 warps)
+  for (int n = warp; n < nm && (mask & 4); n += blockDim.x / 32) {
     if (FF) {
       ff sr = {0.f, 0.f}, si = {0.f, 0.f};
       for (int cch = lane; cch < MB; cch += 32) {
-        float4 v = mpart_ff[warp * MB + cch];
+        float4 v = mpart_ff[n * MB + cch];
         sr = ff_add(sr, {v.x, v.z});
         si = ff_add(si, {v.y, v.w});
       }
@@ -1149,12 +1150,12 @@ __global__ void k_interp_far(int mask, int nfit, int nm, const int* __restrict__
         sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
         si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
       }
-      if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+      if (lane == 0) msf[n] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
     } else {
       zd a(0, 0);
-      for (int cch = lane; cch < MB; cch += 32) a += mpart[warp * MB + cch];
+      for (int cch = lane; cch < MB; cch += 32) a += mpart[n * MB + cch];
       a = warp_sum(a);
-      if (lane == 0) msd[warp] = a;
+      if (lane == 0) msd[n] = a;
     }
   }
   __syncthreads();
@@ -1600,11 +1601,12 @@ __global__ void __launch_bounds__(128) k_interp_multi(int nfit, long N, const in
       if (cr.dalpha != 0.0) v = v * cplx<T>(expi(cr.dalpha * (cxl + samp_rel[2 * t])));
       ph[t] = v;
     }
-    if (warp < cr.nm) {  // mode sums from their chunk partials (warp per mode)
+    // mode sums from their chunk partials: warp w folds modes w, w + 4, ... (up to 8 modes, 4 warps)
+    for (int n = warp; n < cr.nm; n += blockDim.x / 32) {
       if (FF) {
         ff sr = {0.f, 0.f}, si = {0.f, 0.f};
         for (int cch = lane; cch < MB; cch += 32) {
-          float4 v = mpart_ff[r * mp_col + warp * MB + cch];
+          float4 v = mpart_ff[r * mp_col + n * MB + cch];
           sr = ff_add(sr, {v.x, v.z});
           si = ff_add(si, {v.y, v.w});
         }
@@ -1612,12 +1614,12 @@ __global__ void __launch_bounds__(128) k_interp_multi(int nfit, long N, const in
           sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
           si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
         }
-        if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+        if (lane == 0) msf[n] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
       } else {
         zd a(0, 0);
-        for (int cch = lane; cch < MB; cch += 32) a += mpart[r * mp_col + warp * MB + cch];
+        for (int cch = lane; cch < MB; cch += 32) a += mpart[r * mp_col + n * MB + cch];
         a = warp_sum(a);
-        if (lane == 0) msd[warp] = a;
+        if (lane == 0) msd[n] = a;
       }
     }
     __syncthreads();
@@ -1909,11 +1911,11 @@ __global__ void k_project_adj(int mask, int neq, int nm, double half_sigma, cons
     const cplx<T>* base = lam == 0 ? gH + (sidx < neq ? 0 : gH_stride) : gV + (sidx < neq ? 0 : gV_stride);
     g[o] = mulc(base[src_gidx[idx]], src_tw[idx]);
   }
-  if (warp < nm && (mask & 4)) {
+  for (int n = warp; n < nm && (mask & 4); n += nw) {  // mode sums: warp w folds modes w, w + nw, ...
     if (FF) {
       ff sr = {0.f, 0.f}, si = {0.f, 0.f};
       for (int cch = lane; cch < MB; cch += 32) {
-        float4 a = mpart_ff[warp * MB + cch];
+        float4 a = mpart_ff[n * MB + cch];
         sr = ff_add(sr, {a.x, a.z});
         si = ff_add(si, {a.y, a.w});
       }
@@ -1921,12 +1923,12 @@ __global__ void k_project_adj(int mask, int neq, int nm, double half_sigma, cons
         sr = ff_add(sr, {__shfl_down_sync(0xffffffffu, sr.hi, o), __shfl_down_sync(0xffffffffu, sr.lo, o)});
         si = ff_add(si, {__shfl_down_sync(0xffffffffu, si.hi, o), __shfl_down_sync(0xffffffffu, si.lo, o)});
       }
-      if (lane == 0) msf[warp] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
+      if (lane == 0) msf[n] = make_float4(sr.hi, si.hi, sr.lo, si.lo);
     } else {
       zd a(0, 0);
-      for (int cch = lane; cch < MB; cch += 32) a += mpart[warp * MB + cch];
+      for (int cch = lane; cch < MB; cch += 32) a += mpart[n * MB + cch];
       a = warp_sum(a);
-      if (lane == 0) msd[warp] = a;
+      if (lane == 0) msd[n] = a;
     }
   }
   const int* cq = colsT + coloffT[q];
@@ -2355,14 +2357,17 @@ constexpr int KDOT_VECS = 8;     // basis vectors per block (one per warp)
 // its chunk of w into shared memory, so that both latencies overlap. Each block writes its partial
 // sums to part[jj][chunk]; the block that finishes its vector group last (ticket[group], reset by it
 // for the next launch; the usual fence-and-counter pattern, no waiting) folds the group's partials.
-__global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ w,
-                                               long n, float4* part, zd* h, zd* Hc, int add, unsigned* ticket) {
+// Block (bx, by) of a grid of gx chunks: the body shared by the one-problem and batched kernels.
+// A chunk past the end of the vector (batched problems of different sizes) adds zeros.
+__device__ __forceinline__ void kdots_body(const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ w,
+                                           long n, float4* part, zd* h, zd* Hc, int add, unsigned* ticket, int bx,
+                                           int by, int gx) {
   __shared__ float4 ws[KDOT_CHUNK];
   __shared__ bool last;
-  const long i0 = (long)blockIdx.x * KDOT_CHUNK;
+  const long i0 = (long)bx * KDOT_CHUNK;
   const int lane = threadIdx.x & 31;
-  const int jj = blockIdx.y * KDOT_VECS + (threadIdx.x >> 5);
-  const int cnt = (int)min((long)KDOT_CHUNK, n - i0);
+  const int jj = by * KDOT_VECS + (threadIdx.x >> 5);
+  const int cnt = (int)max(0L, min((long)KDOT_CHUNK, n - i0));
   zd vr[KDOT_CHUNK / 32];
   if (jj < m) {
     const zd* v = V + (long)jj * ldv + i0;
@@ -2380,18 +2385,18 @@ __global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, 
 #pragma unroll
     for (int k = 0; k < KDOT_CHUNK / 32; ++k) dot2_mac(split_z(vr[k], true), ws[lane + 32 * k], acc);
     warp_merge(acc);
-    if (lane == 0) part[(long)jj * gridDim.x + blockIdx.x] = pack_dot2(acc);
+    if (lane == 0) part[(long)jj * gx + bx] = pack_dot2(acc);
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&ticket[blockIdx.y], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(&ticket[by], 1u) == (unsigned)gx - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
   if (jj < m) {
     dot2c acc{0.f, 0.f, 0.f, 0.f};
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-      const float4 pv = __ldcg(&part[(long)jj * gridDim.x + b]);
+    for (int b = lane; b < gx; b += 32) {
+      const float4 pv = __ldcg(&part[(long)jj * gx + b]);
       dot2_merge(acc, unpack_dot2(pv));
     }
     warp_merge(acc);
@@ -2401,7 +2406,11 @@ __global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, 
       if (Hc) Hc[jj] = add ? Hc[jj] + v : v;
     }
   }
-  if (threadIdx.x == 0) ticket[blockIdx.y] = 0;
+  if (threadIdx.x == 0) ticket[by] = 0;
+}
+__global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, long ldv, const zd* __restrict__ w,
+                                               long n, float4* part, zd* h, zd* Hc, int add, unsigned* ticket) {
+  kdots_body(V, m, ldv, w, n, part, h, Hc, add, ticket, blockIdx.x, blockIdx.y, gridDim.x);
 }
 // tickets: one counter per group of 8 basis vectors, zero before the first launch
 int kdots_groups(int m) { return (int)ceil_div(m, KDOT_VECS); }
@@ -2419,12 +2428,12 @@ int kupdate_blocks(long n) { return (int)ceil_div(n, 32L); }
 // memory. The rows' sums are merged in shared memory and the FP64 result written once. With npart,
 // the block also writes the compensated sum of |w_new[i]|^2 over its elements to npart[blockIdx.x]
 // (the norm of the orthogonalised vector, for k_kscale).
-__global__ void __launch_bounds__(256) k_kupdate(zd* w, const zd* __restrict__ V, int m, long ldv,
-                                                 const zd* __restrict__ h, long n, float4* npart) {
+__device__ __forceinline__ void kupdate_body(zd* w, const zd* __restrict__ V, int m, long ldv,
+                                             const zd* __restrict__ h, long n, float4* npart, int bx) {
   __shared__ float4 hs[256];
   __shared__ float4 rows[8][33];
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-  const long i = (long)blockIdx.x * 32 + tx;
+  const long i = (long)bx * 32 + tx;
   zd pre[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -2465,9 +2474,13 @@ __global__ void __launch_bounds__(256) k_kupdate(zd* w, const zd* __restrict__ V
       dot2c q{0.f, 0.f, 0.f, 0.f};
       dot2_mac(split_z(wn, true), split_z(wn), q);
       warp_merge(q);
-      if (tx == 0) npart[blockIdx.x] = pack_dot2(q);
+      if (tx == 0) npart[bx] = pack_dot2(q);
     }
   }
+}
+__global__ void __launch_bounds__(256) k_kupdate(zd* w, const zd* __restrict__ V, int m, long ldv,
+                                                 const zd* __restrict__ h, long n, float4* npart) {
+  kupdate_body(w, V, m, ldv, h, n, npart, blockIdx.x);
 }
 cudaError_t launch_kupdate(zd* w, const zd* V, int m, long ldv, const zd* h, long n, float4* npart, cudaStream_t s) {
   k_kupdate<<<kupdate_blocks(n), dim3(32, 8), 0, s>>>(w, V, m, ldv, h, n, npart);
@@ -2476,8 +2489,8 @@ cudaError_t launch_kupdate(zd* w, const zd* V, int m, long ldv, const zd* h, lon
 // |w| from the norm partials of k_kupdate (each block folds them itself); w /= |w|, or w = 0 when
 // |w| = 0 (breakdown); hsub = |w| (the subdiagonal entry h_{j+1,j}), written by block 0. A
 // non-finite |w| is stored as it is and propagates into w.
-__global__ void __launch_bounds__(256) k_kscale(zd* w, long n, const float4* __restrict__ npart, int nparts,
-                                                zd* hsub) {
+__device__ __forceinline__ void kscale_body(zd* w, long n, const float4* __restrict__ npart, int nparts, zd* hsub,
+                                            int bx) {
   __shared__ float4 red[8];
   __shared__ double sc;
   dot2c a{0.f, 0.f, 0.f, 0.f};
@@ -2490,13 +2503,51 @@ __global__ void __launch_bounds__(256) k_kscale(zd* w, long n, const float4* __r
     for (int r = 1; r < (int)(blockDim.x >> 5); ++r) dot2_merge(q, unpack_dot2(red[r]));
     const double hn = sqrt(dot2_value(q).re);
     sc = hn > 0 ? 1.0 / hn : (hn == 0 ? 0.0 : hn);
-    if (blockIdx.x == 0) *hsub = zd(hn, 0);
+    if (bx == 0) *hsub = zd(hn, 0);
   }
   __syncthreads();
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long i = (long)bx * blockDim.x + threadIdx.x;
   if (i < n) w[i] = w[i] * sc;
+}
+__global__ void __launch_bounds__(256) k_kscale(zd* w, long n, const float4* __restrict__ npart, int nparts,
+                                                zd* hsub) {
+  kscale_body(w, n, npart, nparts, hsub, blockIdx.x);
 }
 cudaError_t launch_kscale(zd* w, long n, const float4* npart, int nparts, zd* hsub, cudaStream_t s) {
   k_kscale<<<ceil_div(n, 256L), 256, 0, s>>>(w, n, npart, nparts, hsub);
+  return cudaGetLastError();
+}
+
+// The same Arnoldi step for a batch of problems in lockstep (step j of every problem at once):
+// problem p = blockIdx.z (dots) or blockIdx.y (update, scale) reads its entry of the table; its
+// basis [C | V] has mr recycled vectors in front, so the step projects w = V_{j+1} against
+// m = mr + j + 1 vectors. The grids cover the largest problem; blocks past a smaller problem's end
+// add zeros (dots, partial norms) or do nothing (scale).
+__global__ void __launch_bounds__(256) k_bkdots(const KStep* __restrict__ tab, int j, int add) {
+  const KStep a = tab[blockIdx.z];
+  const int m = a.mr + j + 1;
+  if ((int)blockIdx.y * KDOT_VECS >= m) return;  // this vector group is empty for this problem
+  kdots_body(a.W, m, a.n, a.W + (long)m * a.n, a.n, a.part, a.h, a.H + (long)j * a.ldh, add, a.ticket, blockIdx.x,
+             blockIdx.y, gridDim.x);
+}
+__global__ void __launch_bounds__(256) k_bkupdate(const KStep* __restrict__ tab, int j, int norm) {
+  const KStep a = tab[blockIdx.y];
+  const int m = a.mr + j + 1;
+  kupdate_body(a.W + (long)m * a.n, a.W, m, a.n, a.h, a.n, norm ? a.npart : nullptr, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) k_bkscale(const KStep* __restrict__ tab, int j, int nparts) {
+  const KStep a = tab[blockIdx.y];
+  if ((long)blockIdx.x * blockDim.x >= a.n) return;
+  const int m = a.mr + j + 1;
+  kscale_body(a.W + (long)m * a.n, a.n, a.npart, nparts, a.H + (long)j * a.ldh + m, blockIdx.x);
+}
+cudaError_t launch_batch_arnoldi_step(const KStep* d_tab, int nprob, int j, int mr_max, long n_max, cudaStream_t s) {
+  const int m_max = mr_max + j + 1;
+  const int nchunk = (int)ceil_div(n_max, (long)KDOT_CHUNK), ntile = kupdate_blocks(n_max);
+  for (int pass = 0; pass < 2; ++pass) {
+    k_bkdots<<<dim3(nchunk, kdots_groups(m_max), nprob), 256, 0, s>>>(d_tab, j, pass);
+    k_bkupdate<<<dim3(ntile, nprob), dim3(32, 8), 0, s>>>(d_tab, j, pass);
+  }
+  k_bkscale<<<dim3((unsigned)ceil_div(n_max, 256L), nprob), 256, 0, s>>>(d_tab, j, ntile);
   return cudaGetLastError();
 }
