@@ -908,7 +908,7 @@ extern "C" sgf_status sgf_batch_solve(sgf_batch* B, double tol, int maxit, void*
   // the mixed refinement's later correction solves recycle up to 256 vectors of the first one
   W.mrec = B->any_mixed && !getenv("SGF_NO_RECYCLE") ? std::min(W.m, 256) : 0;
   const size_t nvec = (size_t)W.mrec + W.m + 1;
-  const int nchunk = (int)((B->maxN + 511) / 512);
+  const int nchunk = kdots_chunks(B->maxN);
   W.ks.assign(n, KStep{});
   W.V.assign(n, nullptr);
   W.Vold.assign(n, nullptr);

@@ -1157,7 +1157,7 @@ static sgf_status solve_impl(sgf_ctx* ctx, const zd* b_in, bool adj, double tol,
   // the mixed path's refinement recycles up to 256 vectors of its first correction solve
   const bool mixed = !(ctx->prm.precision == 64 || ctx->op_exact);
   K.mrec = mixed && !getenv("SGF_NO_RECYCLE") ? std::min(K.m, 256) : 0;
-  const long nchunk = (N + 511) / 512;
+  const long nchunk = kdots_chunks(N);
   const size_t nvec = (size_t)K.mrec + K.m + 1;  // [recycled C | Krylov basis V]
   zd* W = nullptr;
   Recycle rc;

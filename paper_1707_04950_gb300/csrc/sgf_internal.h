@@ -279,15 +279,16 @@ cudaError_t launch_dots(const zd* V, int m, long ldv, const zd* w, long n, zd* p
                         cudaStream_t s);
 cudaError_t launch_axpby(zd* y, zd a, const zd* x, zd b, long n, cudaStream_t s);  // y = a x + b y
 // Arnoldi step in float-float arithmetic on FP64 vectors: h = V^H w over m basis vectors (part: at
-// least ceil(n / 512) * m float4 partials; Hc, when given, stores or accumulates h; ticket: at least
+// least kdots_chunks(n) * m float4 partials; Hc, when given, stores or accumulates h; ticket: at least
 // kdots_groups(m) counters, zero on entry and on return); w -= V h (with npart, kupdate_blocks(n)
 // float4 partials of |w|^2 are written too); w /= |w| with hsub = |w|.
 cudaError_t launch_kdots(const zd* V, int m, long ldv, const zd* w, long n, float4* part, zd* h, zd* Hc, int add,
                          unsigned* ticket, cudaStream_t s);
 int kdots_groups(int m);
+int kdots_chunks(long n);  // blocks of k_kdots along a vector of n elements
 // One problem's state for the batched Arnoldi step: basis [C | V] (mr recycled vectors, then the
 // Krylov vectors, n apart), Hessenberg storage (column j at H + j ldh: mr coefficients against C,
-// then the column), coefficient scratch h, float-float partials (part: ceil(n_max / 512) per basis
+// then the column), coefficient scratch h, float-float partials (part: kdots_chunks(n_max) per basis
 // vector; npart: kupdate_blocks(n_max)), k_kdots tickets (kdots_groups(mr + m + 1), zero).
 struct KStep {
   zd* W;

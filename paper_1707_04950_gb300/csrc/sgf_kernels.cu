@@ -2348,12 +2348,12 @@ __device__ __forceinline__ zd dot2_value(const dot2c& a) {
   return zd((double)a.sr + (double)a.er, (double)a.si + (double)a.ei);
 }
 
-constexpr int KDOT_CHUNK = 512;  // elements of w per block of k_kdots
+constexpr int KDOT_CHUNK = 256;  // elements of w per block of k_kdots
 constexpr int KDOT_VECS = 8;     // basis vectors per block (one per warp)
 
 // h[jj] = sum over i < n of conj(V[jj][i]) w[i], jj < m; Hc[jj] = h[jj] (add = 0) or += h[jj].
-// Grid (chunks of 512 elements) x (groups of 8 basis vectors), warp q of a block takes vector
-// 8 blockIdx.y + q, each lane 16 elements 32 apart; the V loads are issued before the block splits
+// Grid (chunks of 256 elements) x (groups of 8 basis vectors), warp q of a block takes vector
+// 8 blockIdx.y + q, each lane 8 elements 32 apart; the V loads are issued before the block splits
 // its chunk of w into shared memory, so that both latencies overlap. Each block writes its partial
 // sums to part[jj][chunk]; the block that finishes its vector group last (ticket[group], reset by it
 // for the next launch; the usual fence-and-counter pattern, no waiting) folds the group's partials.
@@ -2414,9 +2414,10 @@ __global__ void __launch_bounds__(256) k_kdots(const zd* __restrict__ V, int m, 
 }
 // tickets: one counter per group of 8 basis vectors, zero before the first launch
 int kdots_groups(int m) { return (int)ceil_div(m, KDOT_VECS); }
+int kdots_chunks(long n) { return (int)ceil_div(n, (long)KDOT_CHUNK); }
 cudaError_t launch_kdots(const zd* V, int m, long ldv, const zd* w, long n, float4* part, zd* h, zd* Hc, int add,
                          unsigned* ticket, cudaStream_t s) {
-  const int nchunk = (int)ceil_div(n, (long)KDOT_CHUNK);
+  const int nchunk = kdots_chunks(n);
   k_kdots<<<dim3(nchunk, kdots_groups(m)), 256, 0, s>>>(V, m, ldv, w, n, part, h, Hc, add, ticket);
   return cudaGetLastError();
 }
@@ -2543,7 +2544,7 @@ __global__ void __launch_bounds__(256) k_bkscale(const KStep* __restrict__ tab, 
 }
 cudaError_t launch_batch_arnoldi_step(const KStep* d_tab, int nprob, int j, int mr_max, long n_max, cudaStream_t s) {
   const int m_max = mr_max + j + 1;
-  const int nchunk = (int)ceil_div(n_max, (long)KDOT_CHUNK), ntile = kupdate_blocks(n_max);
+  const int nchunk = kdots_chunks(n_max), ntile = kupdate_blocks(n_max);
   for (int pass = 0; pass < 2; ++pass) {
     k_bkdots<<<dim3(nchunk, kdots_groups(m_max), nprob), 256, 0, s>>>(d_tab, j, pass);
     k_bkupdate<<<dim3(ntile, nprob), dim3(32, 8), 0, s>>>(d_tab, j, pass);

@@ -53,7 +53,7 @@ def test_solves_reach_residual_and_energy_balance(name, make, eps_max, relres_ma
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_solve_residual_with_ragged_krylov_tiles(prec):
-    """GMRES with its float-float Arnoldi kernels on N = 1200 (ragged 512-element chunks and
+    """GMRES with its float-float Arnoldi kernels on N = 1200 (ragged 256-element chunks and
     32-element tiles): the solution's residual b - A x, recomputed with a separate application of
     the FP64 operator, matches the reported relative residual and the 1e-12 target."""
     par = I.wl_sinusoid_dirichlet(N=1200)
