@@ -10,10 +10,85 @@
 __host__ __device__ __forceinline__ int spad(int e) { return e + (e >> 4); }
 __host__ __device__ __forceinline__ int splen(int n) { return n + (n >> 4) + 1; }
 
-// Radix-R DFT in registers, R in {2, 3, 4, 8}; dir = -1 forward, +1 inverse.
+// v * e^{dir i t} for t with cos t = c, sin t = sn (dir = -1: the forward DFT's twiddle)
+template <typename T>
+__device__ __forceinline__ cplx<T> rot(cplx<T> v, T c, T sn, int dir) {
+  return dir < 0 ? cplx<T>(v.re * c + v.im * sn, v.im * c - v.re * sn)
+                 : cplx<T>(v.re * c - v.im * sn, v.im * c + v.re * sn);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(cplx<T>* a, int dir);
+
+// Radix-9 and radix-16 DFTs as 3 x 3 and 4 x 4 (Cooley-Tukey with m = 3 or 4: element n = m n1 + n2;
+// length-m transforms over n1 for each n2, the twiddles w^{n2 k1} of the full length, length-m
+// transforms over n2; output k1 + m k2, in natural order).
+template <typename T>
+__device__ __forceinline__ void dft9_reg(cplx<T>* a, int dir) {
+  // cos and sin of 2 pi m / 9 for m = 1, 2, 4
+  const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;
+  const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;
+  const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;
+  cplx<T> b[3][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    b[n2][0] = a[n2];
+    b[n2][1] = a[n2 + 3];
+    b[n2][2] = a[n2 + 6];
+    dft_reg<T, 3>(b[n2], dir);
+  }
+  b[1][1] = rot(b[1][1], c1, s1, dir);
+  b[1][2] = rot(b[1][2], c2, s2, dir);
+  b[2][1] = rot(b[2][1], c2, s2, dir);
+  b[2][2] = rot(b[2][2], c4, s4, dir);
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    cplx<T> t[3] = {b[0][k1], b[1][k1], b[2][k1]};
+    dft_reg<T, 3>(t, dir);
+    a[k1] = t[0];
+    a[k1 + 3] = t[1];
+    a[k1 + 6] = t[2];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void dft16_reg(cplx<T>* a, int dir) {
+  // cos and sin of 2 pi m / 16 for m = 1, 2, 3 (m = 4, 6, 9 follow by symmetry)
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+  const T h = (T)0.70710678118654752440;
+  cplx<T> b[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) b[n2][n1] = a[4 * n1 + n2];
+    dft_reg<T, 4>(b[n2], dir);
+  }
+  // w^{n2 k1}, w = e^{dir 2 pi i / 16}
+  b[1][1] = rot(b[1][1], c1, s1, dir);
+  b[1][2] = rot(b[1][2], h, h, dir);
+  b[1][3] = rot(b[1][3], s1, c1, dir);
+  b[2][1] = rot(b[2][1], h, h, dir);
+  b[2][2] = rot(b[2][2], (T)0, (T)1, dir);
+  b[2][3] = rot(b[2][3], -h, h, dir);
+  b[3][1] = rot(b[3][1], s1, c1, dir);
+  b[3][2] = rot(b[3][2], -h, h, dir);
+  b[3][3] = rot(b[3][3], -c1, -s1, dir);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cplx<T> t[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+    dft_reg<T, 4>(t, dir);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+  }
+}
+
+// Radix-R DFT in registers, R in {2, 3, 4, 8, 9, 16}; dir = -1 forward, +1 inverse.
 template <typename T, int R>
 __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
-  if (R == 3) {
+  if (R == 9) {
+    dft9_reg<T>(a, dir);
+  } else if (R == 16) {
+    dft16_reg<T>(a, dir);
+  } else if (R == 3) {
     const T h = (T)0.86602540378443864676;  // sqrt(3)/2
     cplx<T> t1 = a[1] + a[2], df = a[1] - a[2];
     cplx<T> t2 = a[0] - (T)0.5 * t1;
@@ -63,10 +138,12 @@ __device__ __forceinline__ void dft_reg(cplx<T>* a, int dir) {
   }
 }
 
-// Butterflies per thread of a radix-R stage when a thread may hold VPT values (at least one).
+// Butterflies per thread of a radix-R stage when a thread may hold VPT values (at least one). A
+// block has at least n / VPT threads (n / 15 and n / 6 when n has a factor 3, for VPT = 16 and 8),
+// so that items * threads covers the n / R butterflies: radix 9 takes two per thread when VPT = 16.
 template <int VPT, int R>
 struct StageItems {
-  static constexpr int value = VPT / R > 0 ? VPT / R : 1;
+  static constexpr int value = R == 9 ? (VPT + R - 1) / R : (VPT / R > 0 ? VPT / R : 1);
 };
 
 // One Stockham radix-R stage (self-sorting, in place through registers) over `batch` sequences;
@@ -144,18 +221,28 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* s, int n, int lognR, int
 }
 
 // In-place FFT of `batch` sequences of length n = 2^la 3^lb held in shared memory; element i of
-// sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 8 (then 4 or 2), then
-// radix 3. tw[k] = e^{-2 pi i k / twlen} over the full circle, n dividing twlen. dir = -1 forward,
+// sequence b sits at s[b*bs + i*es]. Self-sorting Stockham stages of radix 16 and 8 (then 4 or 2),
+// then radix 9 (then 3). tw[k] = e^{-2 pi i k / twlen} over the full circle, n dividing twlen. dir = -1 forward,
 // +1 inverse (unnormalised). All threads of the block must call it. Each stage exchanges through
 // registers in place, so every thread holds all of its items at once: with VPT = 16 the caller
 // must keep batch * n <= 16 * blockDim.x (<= 15 * blockDim.x when lb > 0); with VPT = 8,
 // batch * n <= 8 * blockDim.x (<= 6 * blockDim.x when lb > 0).
-template <typename T, int VPT = 16>
+// R16: radix-16 stages allowed (the 16-value kernels and the X passes; in the 8-value Y
+// convolution its sixteen values would raise the register count past what 768-thread blocks hold).
+template <typename T, int VPT = 16, bool R16 = (VPT >= 16)>
 __device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, int bs,
                           const cplx<T>* __restrict__ tw, int twlen, int dir) {
   int ns2 = 0, ns3 = 0, rem = la;
   // log2(n / R) for the power-of-two lengths (lb = 0), -1 otherwise
   auto lognR = [&](int logR) { return lb == 0 ? la - logR : -1; };
+  // fewest stages: ceil(la / 4) radix-16/8 stages for 2^la (radix 16 where radix 8 would need one
+  // more stage), one radix-9 stage per 3^2 (radix 8 then 4 or 2, and radix 3, without R16)
+  const int nst = (la + 3) / 4;
+  for (int n16 = R16 ? la - 3 * nst : 0; n16 > 0; --n16) {
+    stockham_stage<T, 16, StageItems<VPT, 16>::value>(s, n, lognR(4), ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns2 += 4;
+    rem -= 4;
+  }
   while (rem >= 3) {
     stockham_stage<T, 8, StageItems<VPT, 8>::value>(s, n, lognR(3), ns2, ns3, es, batch, bs, tw, twlen, dir);
     ns2 += 3;
@@ -169,7 +256,12 @@ __device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, 
     stockham_stage<T, 2, StageItems<VPT, 2>::value>(s, n, lognR(1), ns2, ns3, es, batch, bs, tw, twlen, dir);
     ns2 += 1;
   }
-  for (int t = 0; t < lb; ++t) {
+  // radix 9 only where a thread already holds 15 values (the 8-value kernels keep radix 3)
+  for (int t = 0; VPT >= 16 && t + 1 < lb; t += 2) {
+    stockham_stage<T, 9, StageItems<VPT, 9>::value>(s, n, -1, ns2, ns3, es, batch, bs, tw, twlen, dir);
+    ns3 += 2;
+  }
+  while (ns3 < lb) {
     stockham_stage<T, 3, StageItems<VPT, 3>::value>(s, n, -1, ns2, ns3, es, batch, bs, tw, twlen, dir);
     ns3 += 1;
   }
@@ -180,7 +272,7 @@ __device__ void smem_fftn(cplx<T>* s, int n, int la, int lb, int es, int batch, 
 template <typename T, int VPT = 16>
 __device__ void smem_fft(cplx<T>* s, int logn, int es, int batch, int bs, const cplx<T>* __restrict__ tw,
                          int twlog, int dir) {
-  smem_fftn<T, VPT>(s, 1 << logn, logn, 0, es, batch, bs, tw, 1 << twlog, dir);
+  smem_fftn<T, VPT, true>(s, 1 << logn, logn, 0, es, batch, bs, tw, 1 << twlog, dir);
 }
 
 // FFT along X (the strided dimension) of arrays laid out g[ix * nrow + iy], ix < Px = 2^logPx,
