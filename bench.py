@@ -164,7 +164,7 @@ LAUNCHES = {"project": 1, "fft_x": 2, "conv_y": 2, "ifft_x": 2, "near": 1, "inte
 # stages give the mean of their H and V launches. Each kernel's writes stay in the 129 MB L2 while it
 # runs (ncu reports 0 bytes written), so these are the reads. None where no capture of the current
 # kernel exists.
-DRAM_BYTES_PER_LAUNCH = {"project": 12.703e6, "fft_x": 4.263e6, "conv_y": 13.743e6, "ifft_x": 2.152e6,
+DRAM_BYTES_PER_LAUNCH = {"project": 12.708e6, "fft_x": 4.274e6, "conv_y": 13.743e6, "ifft_x": 2.163e6,
                          "near": 36.591e6, "interp": 5.438e6}
 
 
