@@ -981,10 +981,12 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     return SGF_OK;
   };
   // The Arnoldi steps run on the device without host round trips: CGS2 projections and updates in
-  // float-float arithmetic, the Hessenberg column, the norm and the normalisation. Every kCheck
-  // steps the host reads the new Hessenberg columns, applies the Givens rotations to them (FP64,
+  // float-float arithmetic, the Hessenberg column, the norm and the normalisation. After each group
+  // of steps the host reads the new Hessenberg columns, applies the Givens rotations to them (FP64,
   // on the host) and takes the residual estimates; steps taken after the estimate reached tol
-  // within such a group are counted as applications and otherwise discarded.
+  // within a group are counted as applications and otherwise discarded. A group holds the steps
+  // that the last group's per-step reduction predicts to tol (at least 1, at most kCheck); a solve
+  // that deflates with a recycled space starts with 2, as it converges within a few steps.
   constexpr int kCheck = 8;
   const long ldh = mr + m + 1;  // column: mr coefficients against C, then the Hessenberg column
   const int nparts = kupdate_blocks(N);
@@ -1020,8 +1022,10 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
     int j = 0;
     jdone = 0;
     bool stop = false;
+    int group = mr > 0 ? 2 : kCheck;
     while (!stop && j < m && total < maxit) {
-      const int j0 = j, jend = std::min({m, j + kCheck, j + (maxit - total)});
+      const int j0 = j, jend = std::min({m, j + group, j + (maxit - total)});
+      const double res0 = res;  // the estimate before this group
       for (; j < jend; ++j) {
         zd* vj = K.V + (size_t)j * N;
         zd* w = K.V + (size_t)(j + 1) * N;
@@ -1067,6 +1071,13 @@ static sgf_status gmres(sgf_ctx* ctx, Krylov& K, int prec, bool adj, const zd* b
           stop = true;
           break;
         }
+      }
+      // next group: the steps to tol at this group's geometric reduction per step
+      const double rate = res0 > 0 && res > 0 ? std::pow(res / res0, 1.0 / (jend - j0)) : 1.0;
+      group = kCheck;
+      if (rate < 1.0) {
+        const double need = std::ceil(std::log(tol * bn / res) / std::log(rate));
+        if (need < kCheck) group = std::max(1, (int)need);
       }
     }
     // back-substitution with the rotated triangle R (columns 0..jdone-1, rows 0..jdone-1)
