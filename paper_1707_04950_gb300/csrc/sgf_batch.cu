@@ -743,8 +743,13 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
     for (int p = 0; p < n; ++p) live[p] = !done[p];
     int j = 0;
     bool any_live = true;
+    // group sizes as in sgf_solve: the steps the slowest live problem's last reduction per step
+    // predicts to its tolerance (1..kCheck); 2 first when deflating with recycled spaces
+    int group = mr > 0 ? 2 : kCheck;
+    std::vector<double> res0(n);
     while (any_live && j < m && total < maxit) {
-      const int j0 = j, jend = std::min({m, j + kCheck, j + (maxit - total)});
+      const int j0 = j, jend = std::min({m, j + group, j + (maxit - total)});
+      for (int p = 0; p < n; ++p) res0[p] = res[p];
       for (; j < jend; ++j) {
         BTRY(bapply(B, slot, W.d_V, j, W.d_V, j + 1));
         ++total;
@@ -792,6 +797,14 @@ static sgf_status bgmres(sgf_batch* B, BWork& W, int slot, zd** bt, zd** xt, con
         }
         any_live = any_live || live[p];
       }
+      int need_max = 1;
+      for (int p = 0; p < n && need_max < kCheck; ++p) {
+        if (!live[p]) continue;
+        const double rate = res0[p] > 0 && res[p] > 0 ? std::pow(res[p] / res0[p], 1.0 / (jend - j0)) : 1.0;
+        const double need = rate < 1.0 ? std::ceil(std::log(tolv[p] * bn[p] / res[p]) / std::log(rate)) : kCheck;
+        need_max = need >= kCheck ? kCheck : std::max(need_max, (int)need);
+      }
+      group = need_max;
     }
     // x_p += V_p y_p - U_p B_p y_p (back substitution per problem; coefficients zero past jdone_p)
     int mm = 0;
