@@ -311,6 +311,7 @@ def run_ours(args):
     solves = run_solves(sgf, par, dev, stream, 1e-12, 4000) if args.solve and rank == 0 else None
     shifted = run_shifted(sgf, dev, stream, flush, args) if args.shifted and rank == 0 else None
     multi = run_multi_rhs(sgf, dev, stream, flush, args) if args.multi and rank == 0 else None
+    periods = run_periods(sgf, dev, stream, flush, args.periods) if args.periods > 1 and rank == 0 else None
     sweep = run_sweep(sgf, dev, stream, flush, args) if args.sweep and rank == 0 else None
     batch = run_batch(args, dev, stream, flush) if args.batch > 0 and rank == 0 else None
     grad = run_gradient(dev, stream) if args.gradient and rank == 0 else None
@@ -376,6 +377,8 @@ def run_ours(args):
         line["solve"] = solves
     if shifted is not None:
         line["shifted_j8"] = shifted
+    if periods is not None:
+        line["periods"] = periods
     if multi is not None:
         line["multi_rhs"] = multi
     if sweep is not None:
@@ -478,6 +481,28 @@ def run_sweep(sgf, dev, stream, flush, args):
             "solve": {"value": n / t_solve, "unit": "solves/s", "s": t_solve, "tol": 1e-8, "status": st_all,
                       "applications": its_all, "max_relres": rr_max},
             "l2": "flushed (256 MiB write) before each timed step"}
+
+
+def run_periods(sgf, dev, stream, flush, r):
+    """The headline forward map on r repetitions of the same corrugation (N = 16384 r): what the
+    kernels reach when the application is r times longer than the latency-bound N = 16384 case."""
+    import torch
+
+    par = inputs.wl_deep_corrugation_neumann_periods(r)
+    op = sgf.Operator(par, device=dev.index, stream=stream.cuda_stream, precision=32)
+    info = op.info
+    hbm, kind = peaks()
+    mu = torch.from_numpy(inputs.random_density(par["N"], 7)).to(dev)
+    out = torch.empty_like(mu)
+    ms = time_applies(sgf, op, mu, out, stream, flush, 100, 10)
+    sb = stage_bytes(info, 8)
+    stg = stage_times(sgf, op, mu, out, flush, 20)
+    op.close()
+    return {"workload": f"deep corrugation repeated {r} times, period {10 * r}, N = {par['N']}, {128 * r} cell columns",
+            "N": int(par["N"]), "ms_per_step": ms, "value": 1000.0 / ms, "unit": "matvecs/s",
+            "unknowns_per_s": par["N"] * 1000.0 / ms, "algorithmic_bytes": sum(sb.values()),
+            "stages_ms": stg, "stage_hbm_frac": {k: sb[k] / (stg[k] * 1e-3) / 1e9 / hbm for k in STAGES if stg[k] > 0},
+            "peak_kind": kind}
 
 
 def run_multi_rhs(sgf, dev, stream, flush, args):
@@ -1026,6 +1051,8 @@ def main():
     ap.add_argument("--solve", type=int, default=1, help="1: time the headline FP64 and mixed solves")
     ap.add_argument("--shifted", type=int, default=1, help="1: time the j = 8 shifted kernel on the same geometry")
     ap.add_argument("--multi", type=int, default=1, help="1: time several densities per call (nrhs 1, 8, 64)")
+    ap.add_argument("--periods", type=int, default=0,
+                    help="R > 1: also time the forward map on the corrugation repeated R times (N = 16384 R; R <= 4)")
     ap.add_argument("--sweep", type=int, default=1, help="1: the batched angle/Wood sweep over four surfaces")
     ap.add_argument("--gradient", type=int, default=1, help="1: time the 128-coefficient gradient block")
     ap.add_argument("--tables", type=int, default=0,

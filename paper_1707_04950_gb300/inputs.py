@@ -178,6 +178,18 @@ def wl_deep_corrugation_neumann(N=16384, nx=128, **kw):
     return make_params(prof, 2 * math.pi, 45.0, NEUMANN, N, nx=nx, **kw)
 
 
+def wl_deep_corrugation_neumann_periods(r, **kw):
+    """The deep corrugation repeated r times in one period of 10 r (N = 16384 r nodes, 128 r cell
+    columns: the same shape, cell size and points per wavelength, r times the surface)."""
+    a = np.zeros(r + 1)
+    a[r] = 10.0
+    prof = {"d": 10.0 * r, "a": a, "b": np.zeros(r + 1)}
+    kw.setdefault("j", 0)
+    kw.setdefault("n_per", 2048)
+    kw.setdefault("ls_reg", 1e-8)
+    return make_params(prof, 2 * math.pi, 45.0, NEUMANN, 16384 * r, nx=128 * r, **kw)
+
+
 def wl_deep_corrugation_neumann_small(N=1024, nx=32, **kw):
     """Same shape as the deep corrugation (depth/period = 2) at period 2: the small parity case."""
     prof = sinusoid(2.0, 2.0)
