@@ -57,3 +57,21 @@ def test_composite_rows_read_as_printed(wood):
         assert (_min_beta_over_k(par) < 1e-12) == wood
         if wood:
             assert par["j"] == 8 and par["h"] == 0.16 and par["h"] > par["a_s"] * np.max(np.abs(f1))
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_repeated_corrugation_is_the_benchmark_shape(r):
+    """The longer-surface workload repeats the benchmark corrugation: the same profile values at the
+    same abscissae, node spacing, cell size and box, r times the period and the nodes, and no mode
+    of the longer period sits at a Wood anomaly."""
+    base = I.wl_deep_corrugation_neumann()
+    rep = I.wl_deep_corrugation_neumann_periods(r)
+    assert rep["N"] == r * base["N"] and rep["nx"] == r * base["nx"] and rep["d"] == r * base["d"]
+    x = np.linspace(0.0, base["d"], 257)
+    f0 = I.profile_eval_host({"d": base["d"], "a": base["a"], "b": base["b"]}, x)
+    f1 = I.profile_eval_host({"d": rep["d"], "a": rep["a"], "b": rep["b"]}, x)
+    assert np.max(np.abs(f1 - f0)) < 1e-12
+    assert rep["d"] / rep["N"] == pytest.approx(base["d"] / base["N"])
+    assert rep["d"] / rep["nx"] == pytest.approx(base["d"] / base["nx"])
+    assert rep["ny"] == base["ny"] and rep["hmin"] == pytest.approx(base["hmin"])
+    assert _min_beta_over_k(rep) > 1e-3
