@@ -116,10 +116,13 @@ sgf_status sgf_apply_host(sgf_ctx* ctx, const void* mu_host, void* out_host, int
 sgf_status sgf_rhs(sgf_ctx* ctx, void* out_dev);
 
 /* Algorithm 1: GMRES (restarted after min(1000, maxit) vectors, fewer if the basis would exceed
- * 2 GiB; zero initial guess, CGS2 Arnoldi in FP64) on the system with
- * the right-hand side of sgf_rhs; with precision 32 an FP64 residual-refinement loop wraps inner
- * GMRES solves on the mixed operator. Writes the solution to mu_dev; *iters = operator
- * applications, *relres = final ||b - A mu|| / ||b|| with the FP64 operator. Synchronises. */
+ * 2 GiB; zero initial guess; CGS2 Arnoldi on FP64 vectors with float-float projections, about 48
+ * significant bits; Givens rotations on the host every 1 to 8 steps) on the system with the
+ * right-hand side of sgf_rhs; with precision 32 an FP64 residual-refinement loop wraps inner GMRES
+ * solves on the mixed operator, the later ones deflated with the first one's Krylov space (GCRO
+ * form, up to 256 vectors). Writes the solution to mu_dev; *iters = operator applications,
+ * *relres = final ||b - A mu|| / ||b|| with the FP64 operator. Allocates its Krylov storage on the
+ * device for the call. Synchronises. */
 sgf_status sgf_solve(sgf_ctx* ctx, double tol, int maxit, void* mu_dev, int* iters, double* relres);
 
 /* Algorithm 1 on a caller's right-hand side: GMRES (as in sgf_solve, same precision handling) on
@@ -255,9 +258,11 @@ const char* sgf_batch_last_error(const sgf_batch* batch);
 sgf_status sgf_batch_apply(sgf_batch* batch, const void* const* mu_devs, void* const* out_devs);
 
 /* Algorithm 1 for every problem on its incident-wave right-hand side (as sgf_solve): restarted GMRES
- * (restart length as sgf_solve, bases within 4 GiB for the batch; CGS2) in lockstep, one graph launch per Arnoldi step for all problems, one batched
- * kernel per Gram-Schmidt pass. If any context uses precision 32, every problem runs FP64 residual
- * refinement around inner solves (tolerance 1e-6) on its own operator. Solutions go to mu_devs[p];
+ * (restart length as sgf_solve, bases within 4 GiB for the batch; CGS2 as in sgf_solve) in
+ * lockstep: one graph launch per Arnoldi step for all problems, one batched kernel per
+ * Gram-Schmidt pass. If any context uses precision 32, every problem runs FP64 residual refinement
+ * around inner solves (tolerance 1e-6) on its own operator, the later ones deflated with the first
+ * one's Krylov spaces. Solutions go to mu_devs[p];
  * host iters[n] and relres[n] (may be NULL) receive operator applications and the final FP64
  * relative residual of each problem. SGF_ENOCONV names the first problem above tol. Synchronises. */
 sgf_status sgf_batch_solve(sgf_batch* batch, double tol, int maxit, void* const* mu_devs, int* iters,
