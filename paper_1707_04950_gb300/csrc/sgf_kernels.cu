@@ -897,8 +897,11 @@ __device__ __forceinline__ void mode_partial(int n, int chunk, int MB, long N, c
 // monopole/dipole, source) of P_q mu_q (P stored [node][output]), scattered with the quasi-periodic
 // twist into the X-major grids. The grid tail (nm * MB blocks) computes the mode-sum partials. For
 // the mixed path the cell blocks also write the float-float copy of mu used by the near field.
+// FP64: six blocks per SM (78 registers, no spills) so that the ~790 work items of the N = 16384
+// workload run in one wave; FP32: five (96 registers: its 32 staged P values spill under six, and
+// a one-block bound lets the compiler take 123).
 template <typename T>
-__global__ void k_project(int n_occ, int neq, int nm, long N, const int* __restrict__ cell_start,
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 6 : 5) k_project(int n_occ, int neq, int nm, long N, const int* __restrict__ cell_start,
                           const int* __restrict__ node_idx, const zd* __restrict__ mu, const cplx<T>* __restrict__ P,
                           const int* __restrict__ src_gidx, const cplx<T>* __restrict__ src_tw,
                           cplx<T>* __restrict__ gH, long gH_stride, cplx<T>* __restrict__ gV, long gV_stride,
